@@ -1,0 +1,231 @@
+"""FP64 CPU oracle for the linear lasso / elastic-net path (test infrastructure).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package.  The CUDA library never uses it.
+
+Thin ctypes wrapper around ``oracle.c`` (plain C, IEEE FP64, compiled with
+``-ffp-contract=off`` so no fused multiply-adds change its rounding).  Inputs
+are raw stored values promoted exactly to FP64 and laid out column-major as a
+NumPy array of shape (p, n) (column j is row j of the array).
+
+Every function cites the passage of the paper it restates; the pins that tie
+each one to something other than itself are in ``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_ARG, ERR_OOM, ERR_NOT_CONVERGED = 0, -1, -3, -4
+
+_dp = C.POINTER(C.c_double)
+_i64p = C.POINTER(C.c_int64)
+_u8p = C.POINTER(C.c_uint8)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into _build/liboracle.so (gcc, -O2, no FP contraction)."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        tmp = _OUT + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+                               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            i64 = C.c_int64
+            L.orc_standardize.argtypes = [_dp, i64, i64, i64, _dp, _dp, _u8p]
+            L.orc_center.argtypes = [_dp, i64, _dp]
+            L.orc_center.restype = C.c_double
+            L.orc_standardized_matrix.argtypes = [_dp, i64, i64, i64, _dp, _dp, _u8p, _dp]
+            L.orc_xtv.argtypes = [_dp, i64, i64, _dp, _dp]
+            L.orc_z.argtypes = [_dp, i64, i64, _dp, _dp]
+            L.orc_lambda_max.argtypes = [_dp, _u8p, i64, i64, C.c_double, _dp, _i64p]
+            L.orc_lambda_grid.argtypes = [C.c_double, C.c_double, C.c_int, _dp]
+            L.orc_bedpp_init.argtypes = [_dp, i64, i64, i64, _dp, _dp]
+            L.orc_bedpp_init.restype = C.c_double
+            L.orc_bedpp_safe.argtypes = [_dp, _dp, _u8p, i64, i64, C.c_double, i64, C.c_double,
+                                         C.c_double, C.c_double, _u8p]
+            L.orc_strong.argtypes = [_dp, _u8p, _dp, i64, C.c_double, C.c_double, C.c_double, _u8p]
+            L.orc_cd.argtypes = [_dp, i64, _i64p, i64, C.c_double, C.c_double, C.c_double, i64,
+                                 _dp, _dp, _i64p]
+            L.orc_objective.argtypes = [_dp, i64, i64, _dp, _dp, C.c_double, C.c_double]
+            L.orc_objective.restype = C.c_double
+            L.orc_fit_path.argtypes = [_dp, i64, i64, i64, _dp, C.c_double, _dp, C.c_int, C.c_int,
+                                       C.c_double, i64, _dp, _dp, _dp, _dp, _i64p]
+            _lib = L
+    return _lib
+
+
+def _p(a, t=_dp):
+    return a.ctypes.data_as(t)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def standardize(X):
+    """Column means c, population sds s and keep flags (Sec. 3.1). X: (p, n) FP64."""
+    X = _f64(X)
+    p, n = X.shape
+    c, s = np.empty(p), np.empty(p)
+    keep = np.empty(p, dtype=np.uint8)
+    st = lib().orc_standardize(_p(X), n, p, n, _p(c), _p(s), _p(keep, _u8p))
+    assert st == OK
+    return c, s, keep
+
+
+def center(y):
+    y = _f64(y)
+    yc = np.empty_like(y)
+    ybar = lib().orc_center(_p(y), y.size, _p(yc))
+    return yc, ybar
+
+
+def standardized_matrix(X, c, s, keep):
+    """Explicit cell-wise standardized matrix (Sec. 3.1), shape (p, n)."""
+    X = _f64(X)
+    p, n = X.shape
+    Xt = np.empty((p, n))
+    lib().orc_standardized_matrix(_p(X), n, p, n, _p(_f64(c)), _p(_f64(s)),
+                                  _p(np.ascontiguousarray(keep, dtype=np.uint8), _u8p), _p(Xt))
+    return Xt
+
+
+def xtv(Xt, v):
+    """xt_j' v for every column (simplifications (1)-(3) of Sec. 3.1.1 written
+    out without the c/s factoring)."""
+    Xt = _f64(Xt)
+    p, n = Xt.shape
+    out = np.empty(p)
+    lib().orc_xtv(_p(Xt), n, p, _p(_f64(v)), _p(out))
+    return out
+
+
+def z(Xt, r):
+    """z_j = xt_j' r / n: the post-convergence KKT quantity (Sec. 2.2, 3.1.1 (3))."""
+    Xt = _f64(Xt)
+    p, n = Xt.shape
+    out = np.empty(p)
+    lib().orc_z(_p(Xt), n, p, _p(_f64(r)), _p(out))
+    return out
+
+
+def lambda_max(xty, keep, n, alpha):
+    """lambda_max = max_j |xt_j' yc| / (n alpha), lowest index on ties."""
+    xty = _f64(xty)
+    lm = C.c_double()
+    js = C.c_int64()
+    st = lib().orc_lambda_max(_p(xty), _p(np.ascontiguousarray(keep, dtype=np.uint8), _u8p),
+                              xty.size, n, alpha, C.byref(lm), C.byref(js))
+    if st != OK:
+        raise ValueError("alpha must be in (0, 1]")
+    return lm.value, js.value
+
+
+def lambda_grid(lmax, ratio, K):
+    """Log-spaced grid from lambda_max to ratio * lambda_max (Sec. 4)."""
+    out = np.empty(K)
+    lib().orc_lambda_grid(lmax, ratio, K, _p(out))
+    return out
+
+
+def bedpp_init(Xt, jstar, yc):
+    """x_j~' x_*~ for every j (simplification (1), Sec. 3.1.1) and ||yc||^2."""
+    Xt = _f64(Xt)
+    p, n = Xt.shape
+    out = np.empty(p)
+    yy = lib().orc_bedpp_init(_p(Xt), n, p, jstar, _p(_f64(yc)), _p(out))
+    return out, yy
+
+
+def bedpp_safe(xty, xtxstar, keep, n, lmax, jstar, ynorm2, lam, alpha):
+    """BEDPP safe set at lam (Sec. 2.2): 1 = not discarded."""
+    xty = _f64(xty)
+    p = xty.size
+    safe = np.empty(p, dtype=np.uint8)
+    lib().orc_bedpp_safe(_p(xty), _p(_f64(xtxstar)),
+                         _p(np.ascontiguousarray(keep, dtype=np.uint8), _u8p), p, n, lmax, jstar,
+                         ynorm2, lam, alpha, _p(safe, _u8p))
+    return safe
+
+
+def strong(zprev, safe, beta_prev, lam, lam_prev, alpha):
+    """Sequential strong rule within the safe set (SSR-BEDPP, Sec. 2.2)."""
+    zprev = _f64(zprev)
+    out = np.empty(zprev.size, dtype=np.uint8)
+    lib().orc_strong(_p(zprev), _p(np.ascontiguousarray(safe, dtype=np.uint8), _u8p),
+                     _p(_f64(beta_prev)), zprev.size, lam, lam_prev, alpha, _p(out, _u8p))
+    return out
+
+
+def cd(Xt, idx, lam, alpha, eps, beta, r, max_sweeps=100_000):
+    """Coordinate descent at one lambda over coordinates ``idx`` (in order),
+    from (beta, r); returns (beta, r, sweeps, status).  beta is dense (p)."""
+    Xt = _f64(Xt)
+    p, n = Xt.shape
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    beta = _f64(beta).copy()
+    r = _f64(r).copy()
+    sw = C.c_int64()
+    st = lib().orc_cd(_p(Xt), n, _p(idx, _i64p), idx.size, lam, alpha, eps, max_sweeps,
+                      _p(beta), _p(r), C.byref(sw))
+    return beta, r, sw.value, st
+
+
+def objective(Xt, yc, beta, lam, alpha):
+    Xt = _f64(Xt)
+    p, n = Xt.shape
+    return lib().orc_objective(_p(Xt), n, p, _p(_f64(yc)), _p(_f64(beta)), lam, alpha)
+
+
+def fit_path(X, y, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, lambdas=None,
+             max_sweeps=100_000):
+    """Whole path (no screening).  X: (p, n) raw values promoted to FP64.
+
+    Returns a dict with lambdas, beta (K x p, standardized scale), beta_orig,
+    intercept, loss, sweeps, status, lmax, jstar, c, s, keep."""
+    X = _f64(X)
+    p, n = X.shape
+    y = _f64(y)
+    c, s, keep = standardize(X)
+    yc, ybar = center(y)
+    grid_from_lmax = 0
+    Xt = standardized_matrix(X, c, s, keep)
+    xty = xtv(Xt, yc)
+    del Xt
+    lmax, jstar = lambda_max(xty, keep, n, alpha)
+    if lambdas is None:
+        lambdas = lambda_grid(lmax, ratio, nlambda)
+        grid_from_lmax = 1
+    lambdas = _f64(lambdas)
+    K = lambdas.size
+    beta = np.empty((K, p))
+    beta_orig = np.empty((K, p))
+    icpt, loss = np.empty(K), np.empty(K)
+    sweeps = np.empty(K, dtype=np.int64)
+    st = lib().orc_fit_path(_p(X), n, p, n, _p(y), alpha, _p(lambdas), K, grid_from_lmax, eps,
+                            max_sweeps, _p(beta), _p(beta_orig), _p(icpt), _p(loss),
+                            _p(sweeps, _i64p))
+    if st == ERR_ARG:
+        raise ValueError("invalid arguments to the oracle path")
+    return dict(lambdas=lambdas, beta=beta, beta_orig=beta_orig, intercept=icpt, loss=loss,
+                sweeps=sweeps, status=st, lmax=lmax, jstar=jstar, c=c, s=s, keep=keep,
+                ybar=ybar, xty=xty)

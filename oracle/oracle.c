@@ -1,0 +1,388 @@
+/*
+ * oracle.c -- plain, slow, FP64 CPU reference for the linear lasso /
+ * elastic-net solution path of "The biglasso Package" (Zeng & Breheny).
+ *
+ * TEST INFRASTRUCTURE. Only the test suite, the package smoke check and the
+ * benchmark's CPU-baseline leg may load this library. The CUDA path never
+ * links, imports or calls it, and it shares no code, header or constant with
+ * the CUDA path.
+ *
+ * What it computes (all in IEEE FP64, no screening, no blocking, no fusion):
+ *
+ *   Standardization (Sec. 3.1, "cell-wise standardization"): c_j is the column
+ *   mean, s_j the population standard deviation (divisor n, so that the
+ *   standardized column satisfies (1/n) sum_i xt_ij^2 = 1, Sec. 2 notation),
+ *   and xt_ij = (x_ij - c_j) / s_j is formed explicitly.  A column whose
+ *   entries are all equal has no standard deviation; it is flagged keep=0 and
+ *   its coefficient is held at 0.
+ *
+ *   Objective (the paper compares objective values Q in Sec. 4.4 but never
+ *   writes Q out; the reading used here is the usual one for pathwise CD):
+ *       Q(b; lam) = (1/2n) ||yc - Xt b||^2 + lam*alpha*||b||_1
+ *                   + lam*(1-alpha)/2 * ||b||^2,
+ *   with yc = y - mean(y) (the unpenalized intercept absorbs the mean).
+ *
+ *   lambda_max = max_j |xt_j' yc| / (n alpha)  (the smallest lambda at which the
+ *   solution is 0; its argmax column is the x_* of simplification (1), Sec. 3.1.1);
+ *   ties resolve to the lowest index.
+ *
+ *   Pathwise coordinate descent with warm starts and active-set cycling
+ *   (Sec. 1 and Sec. 3.1.1, following the pathwise CD of Friedman et al.):
+ *   for lambda_k, starting from b(lambda_{k-1}), repeat
+ *     (i)  one full cyclic sweep over all kept j in index order with
+ *            zt_j = xt_j' r / n + b_j,
+ *            b_j <- S(zt_j, lam*alpha) / (1 + lam*(1-alpha)),
+ *            r   <- r - (b_j_new - b_j_old) xt_j,
+ *     (ii) then sweeps over {j : b_j != 0} until max |delta b_j| < eps,
+ *   until a full sweep (i) moves no coordinate by eps or more and makes no
+ *   zero coordinate nonzero.  S(z,t) = sign(z) max(|z|-t, 0).
+ *   At lambda >= lambda_max the solution is exactly 0 and no sweep is run.
+ *
+ *   BEDPP (Sec. 2.2, the basic EDPP safe rule of Wang, Wonka and Ye, with the
+ *   reference point fixed at lambda_max; the paper defers the formula to its
+ *   companion work).  Restated for the 1/(2n) scaling with standardized
+ *   columns (||xt_j||^2 = n) and s* = sign(xt_*' yc): feature j is discarded at
+ *   lambda (alpha = 1) when
+ *     |(lmax+lam) xt_j'yc - (lmax-lam) s* lmax xt_j'xt_*|
+ *         < 2 n lam lmax - (lmax-lam) sqrt(n ||yc||^2 - n^2 lmax^2).
+ *   x_* itself is never discarded (its left side is identically 2 n lam lmax).
+ *   For alpha < 1 no feature is discarded.
+ *
+ *   Sequential strong rule (Sec. 2.2, Tibshirani et al. 2012): keep j at
+ *   lambda_k when |z_j(lambda_{k-1})| >= alpha (2 lambda_k - lambda_{k-1}), or when
+ *   b_j(lambda_{k-1}) != 0.
+ *
+ * Parity pins for every function live in tests/test_oracle_pins.py
+ * (closed forms, brute-force support enumeration, KKT conditions, safety).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef int64_t i64;
+
+#define ORC_OK 0
+#define ORC_ERR_ARG (-1)
+#define ORC_ERR_OOM (-3)
+#define ORC_ERR_NOT_CONVERGED (-4)
+
+static const double *col(const double *X, i64 ldx, i64 j) { return X + (size_t)j * (size_t)ldx; }
+
+static double soft(double z, double t)
+{
+    if (z > t) return z - t;
+    if (z < -t) return z + t;
+    return 0.0;
+}
+
+/* Column mean, population standard deviation, and the keep flag (Sec. 3.1). */
+int orc_standardize(const double *X, i64 n, i64 p, i64 ldx, double *c, double *s, uint8_t *keep)
+{
+    if (n < 1 || p < 0 || ldx < n) return ORC_ERR_ARG;
+    for (i64 j = 0; j < p; ++j) {
+        const double *x = col(X, ldx, j);
+        int varies = 0;
+        double sum = 0.0;
+        for (i64 i = 0; i < n; ++i) {
+            sum += x[i];
+            if (x[i] != x[0]) varies = 1;
+        }
+        double mean = sum / (double)n;
+        double ss = 0.0;
+        for (i64 i = 0; i < n; ++i) {
+            double d = x[i] - mean;
+            ss += d * d;
+        }
+        c[j] = mean;
+        s[j] = varies ? sqrt(ss / (double)n) : 0.0;
+        keep[j] = (uint8_t)(varies && s[j] > 0.0);
+        if (!keep[j]) s[j] = 0.0;
+    }
+    return ORC_OK;
+}
+
+/* yc = y - mean(y); returns the mean. */
+double orc_center(const double *y, i64 n, double *yc)
+{
+    double sum = 0.0;
+    for (i64 i = 0; i < n; ++i) sum += y[i];
+    double ybar = sum / (double)n;
+    for (i64 i = 0; i < n; ++i) yc[i] = y[i] - ybar;
+    return ybar;
+}
+
+/* Xt (p x n, column j contiguous) = (x_ij - c_j)/s_j for kept columns, 0 otherwise. */
+int orc_standardized_matrix(const double *X, i64 n, i64 p, i64 ldx, const double *c,
+                            const double *s, const uint8_t *keep, double *Xt)
+{
+    for (i64 j = 0; j < p; ++j) {
+        const double *x = col(X, ldx, j);
+        double *t = Xt + (size_t)j * (size_t)n;
+        if (keep[j]) {
+            for (i64 i = 0; i < n; ++i) t[i] = (x[i] - c[j]) / s[j];
+        } else {
+            for (i64 i = 0; i < n; ++i) t[i] = 0.0;
+        }
+    }
+    return ORC_OK;
+}
+
+/* out_j = xt_j' v  (plain dot products of the explicit standardized columns). */
+void orc_xtv(const double *Xt, i64 n, i64 p, const double *v, double *out)
+{
+    for (i64 j = 0; j < p; ++j) {
+        const double *t = Xt + (size_t)j * (size_t)n;
+        double acc = 0.0;
+        for (i64 i = 0; i < n; ++i) acc += t[i] * v[i];
+        out[j] = acc;
+    }
+}
+
+/* z_j = xt_j' r / n, the quantity the KKT check and the strong rule test. */
+void orc_z(const double *Xt, i64 n, i64 p, const double *r, double *z)
+{
+    orc_xtv(Xt, n, p, r, z);
+    for (i64 j = 0; j < p; ++j) z[j] /= (double)n;
+}
+
+/* lambda_max = max_j |xty_j| / (n alpha) over kept columns; lowest index wins ties. */
+int orc_lambda_max(const double *xty, const uint8_t *keep, i64 p, i64 n, double alpha,
+                   double *lmax, i64 *jstar)
+{
+    if (!(alpha > 0.0 && alpha <= 1.0)) return ORC_ERR_ARG;
+    double best = 0.0;
+    i64 arg = -1;
+    for (i64 j = 0; j < p; ++j) {
+        if (!keep[j]) continue;
+        double a = fabs(xty[j]);
+        if (arg < 0 || a > best) {
+            best = a;
+            arg = j;
+        }
+    }
+    *lmax = (arg < 0) ? 0.0 : best / ((double)n * alpha);
+    *jstar = arg;
+    return ORC_OK;
+}
+
+/* lambda_k = lmax * ratio^(k/(K-1)), k = 0..K-1 (log-spaced; lambda_0 = lmax). */
+void orc_lambda_grid(double lmax, double ratio, int K, double *lam)
+{
+    for (int k = 0; k < K; ++k) {
+        double e = (K > 1) ? (double)k / (double)(K - 1) : 0.0;
+        lam[k] = lmax * pow(ratio, e);
+    }
+}
+
+/* BEDPP precomputation (Sec. 3.1.1 simplification (1) and ||yc||^2), done with
+ * the explicit standardized columns. */
+double orc_bedpp_init(const double *Xt, i64 n, i64 p, i64 jstar, const double *yc,
+                      double *xtxstar)
+{
+    const double *ts = Xt + (size_t)jstar * (size_t)n;
+    orc_xtv(Xt, n, p, ts, xtxstar);
+    double yy = 0.0;
+    for (i64 i = 0; i < n; ++i) yy += yc[i] * yc[i];
+    return yy;
+}
+
+/* safe_j = 1 when BEDPP does not discard j at lam (see header). */
+void orc_bedpp_safe(const double *xty, const double *xtxstar, const uint8_t *keep, i64 p, i64 n,
+                    double lmax, i64 jstar, double ynorm2, double lam, double alpha,
+                    uint8_t *safe)
+{
+    if (alpha < 1.0 || jstar < 0) {
+        for (i64 j = 0; j < p; ++j) safe[j] = keep[j];
+        return;
+    }
+    double nn = (double)n;
+    double sstar = (xty[jstar] >= 0.0) ? 1.0 : -1.0;
+    double rad = nn * ynorm2 - nn * nn * lmax * lmax;
+    if (rad < 0.0) rad = 0.0;
+    double rhs = 2.0 * nn * lam * lmax - (lmax - lam) * sqrt(rad);
+    for (i64 j = 0; j < p; ++j) {
+        if (!keep[j]) {
+            safe[j] = 0;
+            continue;
+        }
+        if (j == jstar) {
+            /* For x_* the left side equals 2 n lam lmax identically, which is at
+             * least the right side, so x_* is never discarded; the FP64 values of
+             * the two sides tie at lam = lmax and must not be compared. */
+            safe[j] = 1;
+            continue;
+        }
+        double lhs = fabs((lmax + lam) * xty[j] - (lmax - lam) * sstar * lmax * xtxstar[j]);
+        safe[j] = (uint8_t)!(lhs < rhs);
+    }
+}
+
+/* Sequential strong rule restricted to the safe set (SSR-BEDPP, Sec. 2.2). */
+void orc_strong(const double *zprev, const uint8_t *safe, const double *beta_prev, i64 p,
+                double lam, double lam_prev, double alpha, uint8_t *strong)
+{
+    double t = alpha * (2.0 * lam - lam_prev);
+    for (i64 j = 0; j < p; ++j)
+        strong[j] = (uint8_t)(safe[j] && (beta_prev[j] != 0.0 || fabs(zprev[j]) >= t));
+}
+
+/* One coordinate update; returns the change in b_j. */
+static double cd_update(const double *Xt, i64 n, i64 j, double thr, double den, double *beta,
+                        double *r, int *became_nonzero)
+{
+    const double *t = Xt + (size_t)j * (size_t)n;
+    double acc = 0.0;
+    for (i64 i = 0; i < n; ++i) acc += t[i] * r[i];
+    double old = beta[j];
+    double zt = acc / (double)n + old;
+    double nb = soft(zt, thr) / den;
+    double d = nb - old;
+    if (d != 0.0) {
+        for (i64 i = 0; i < n; ++i) r[i] -= d * t[i];
+        beta[j] = nb;
+        if (old == 0.0 && nb != 0.0) *became_nonzero = 1;
+    }
+    return d;
+}
+
+/* Coordinate descent at one lambda over the coordinates idx[0..m) (in that
+ * order), starting from (beta, r) with r = yc - Xt beta.  beta is dense (p). */
+int orc_cd(const double *Xt, i64 n, const i64 *idx, i64 m, double lam, double alpha, double eps,
+           i64 max_sweeps, double *beta, double *r, i64 *sweeps_out)
+{
+    double thr = lam * alpha, den = 1.0 + lam * (1.0 - alpha);
+    i64 sweeps = 0;
+    i64 *act = (i64 *)malloc((size_t)(m > 0 ? m : 1) * sizeof(i64));
+    if (!act) return ORC_ERR_OOM;
+    int status = ORC_OK;
+    for (;;) {
+        double maxd = 0.0;
+        int newnz = 0;
+        for (i64 t = 0; t < m; ++t) {
+            double d = fabs(cd_update(Xt, n, idx[t], thr, den, beta, r, &newnz));
+            if (d > maxd) maxd = d;
+        }
+        ++sweeps;
+        if (maxd < eps && !newnz) break;
+        if (sweeps >= max_sweeps) {
+            status = ORC_ERR_NOT_CONVERGED;
+            break;
+        }
+        i64 na = 0;
+        for (i64 t = 0; t < m; ++t)
+            if (beta[idx[t]] != 0.0) act[na++] = idx[t];
+        for (;;) {
+            double md = 0.0;
+            int dummy = 0;
+            for (i64 a = 0; a < na; ++a) {
+                double d = fabs(cd_update(Xt, n, act[a], thr, den, beta, r, &dummy));
+                if (d > md) md = d;
+            }
+            ++sweeps;
+            if (md < eps) break;
+            if (sweeps >= max_sweeps) {
+                status = ORC_ERR_NOT_CONVERGED;
+                break;
+            }
+        }
+        if (status != ORC_OK) break;
+    }
+    free(act);
+    *sweeps_out = sweeps;
+    return status;
+}
+
+/* Q(b; lam) with the residual recomputed from scratch. */
+double orc_objective(const double *Xt, i64 n, i64 p, const double *yc, const double *beta,
+                     double lam, double alpha)
+{
+    double *r = (double *)malloc((size_t)n * sizeof(double));
+    if (!r) return NAN;
+    memcpy(r, yc, (size_t)n * sizeof(double));
+    double l1 = 0.0, l2 = 0.0;
+    for (i64 j = 0; j < p; ++j) {
+        double b = beta[j];
+        if (b == 0.0) continue;
+        const double *t = Xt + (size_t)j * (size_t)n;
+        for (i64 i = 0; i < n; ++i) r[i] -= b * t[i];
+        l1 += fabs(b);
+        l2 += b * b;
+    }
+    double rss = 0.0;
+    for (i64 i = 0; i < n; ++i) rss += r[i] * r[i];
+    free(r);
+    return rss / (2.0 * (double)n) + lam * alpha * l1 + 0.5 * lam * (1.0 - alpha) * l2;
+}
+
+/* Full path from raw FP64 data (column-major, leading dimension ldx).
+ * lambdas: K values, strictly decreasing; when grid_from_lmax != 0 the first
+ * value is taken to be lambda_max itself and the solution there is set to 0.
+ * Outputs (any may be NULL except beta): beta K x p on the standardized scale,
+ * beta_orig K x p (b_j / s_j), intercept[K], loss[K] (= Q), sweeps[K]. */
+int orc_fit_path(const double *X, i64 n, i64 p, i64 ldx, const double *y, double alpha,
+                 const double *lambdas, int K, int grid_from_lmax, double eps, i64 max_sweeps,
+                 double *beta_out, double *beta_orig, double *intercept, double *loss,
+                 i64 *sweeps)
+{
+    if (n < 1 || p < 1 || ldx < n || K < 1 || !(alpha > 0.0 && alpha <= 1.0) || !(eps > 0.0))
+        return ORC_ERR_ARG;
+    for (int k = 1; k < K; ++k)
+        if (!(lambdas[k] < lambdas[k - 1])) return ORC_ERR_ARG;
+    double *c = malloc((size_t)p * sizeof(double));
+    double *s = malloc((size_t)p * sizeof(double));
+    uint8_t *keep = malloc((size_t)p);
+    double *yc = malloc((size_t)n * sizeof(double));
+    double *Xt = malloc((size_t)n * (size_t)p * sizeof(double));
+    double *xty = malloc((size_t)p * sizeof(double));
+    double *beta = calloc((size_t)p, sizeof(double));
+    double *r = malloc((size_t)n * sizeof(double));
+    i64 *idx = malloc((size_t)p * sizeof(i64));
+    int status = ORC_OK;
+    if (!c || !s || !keep || !yc || !Xt || !xty || !beta || !r || !idx) {
+        status = ORC_ERR_OOM;
+        goto done;
+    }
+    orc_standardize(X, n, p, ldx, c, s, keep);
+    double ybar = orc_center(y, n, yc);
+    orc_standardized_matrix(X, n, p, ldx, c, s, keep, Xt);
+    orc_xtv(Xt, n, p, yc, xty);
+    double lmax;
+    i64 jstar;
+    orc_lambda_max(xty, keep, p, n, alpha, &lmax, &jstar);
+    i64 m = 0;
+    for (i64 j = 0; j < p; ++j)
+        if (keep[j]) idx[m++] = j;
+    memcpy(r, yc, (size_t)n * sizeof(double));
+    for (int k = 0; k < K; ++k) {
+        double lam = lambdas[k];
+        i64 sw = 0;
+        int at_max = (grid_from_lmax && k == 0) || lam >= lmax;
+        if (!at_max) {
+            int st = orc_cd(Xt, n, idx, m, lam, alpha, eps, max_sweeps, beta, r, &sw);
+            if (st != ORC_OK && status == ORC_OK) status = st;
+        }
+        double *bk = beta_out + (size_t)k * (size_t)p;
+        memcpy(bk, beta, (size_t)p * sizeof(double));
+        double icpt = ybar;
+        for (i64 j = 0; j < p; ++j) {
+            double bo = (beta[j] != 0.0) ? beta[j] / s[j] : 0.0;
+            if (beta_orig) beta_orig[(size_t)k * (size_t)p + (size_t)j] = bo;
+            icpt -= c[j] * bo;
+        }
+        if (intercept) intercept[k] = icpt;
+        if (loss) loss[k] = orc_objective(Xt, n, p, yc, beta, lam, alpha);
+        if (sweeps) sweeps[k] = sw;
+    }
+done:
+    free(c);
+    free(s);
+    free(keep);
+    free(yc);
+    free(Xt);
+    free(xty);
+    free(beta);
+    free(r);
+    free(idx);
+    return status;
+}

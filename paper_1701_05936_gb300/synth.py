@@ -1,0 +1,180 @@
+"""Seeded synthetic inputs for the linear lasso / elastic-net path.
+
+This module only draws raw data (X, y) and the true coefficient vector. It
+holds none of the solver's arithmetic (no standardization, no lambda grid, no
+screening, no descent), so both the CUDA path and the FP64 oracle can consume
+the same stored values without sharing any of the method.
+
+Random numbers come from NumPy's Philox-4x32-10 counter-based generator
+(Salmon et al., SC'11), keyed by (20170120, workload * 1000 + replicate).
+
+Layout: X is column-major n x p with leading dimension ``ldx`` (elements),
+stored as a NumPy array of shape (p, ldx); column j is ``X[j, :n]``.  ``ldx`` is
+padded so that every column starts on a 128-byte boundary.  The padding rows
+(``X[:, n:]``) hold ``pad_value`` and are never part of the problem.
+
+Workload recipes (the synthetic stand-ins for the paper's benchmark shapes,
+Sec. 4.2 simulated data and Table 2's real-data shapes):
+
+* ``gaussian_iid``  -- X_ij iid N(0,1); k nonzero beta = +-1 (random sign);
+  y = X beta + N(0, noise_sd^2).                      (200 x 1000, FP64)
+* ``gaussian_ar1``  -- x_1 ~ N(0,I), x_j = rho x_{j-1} + sqrt(1-rho^2) e_j;
+  k nonzero beta ~ U[lo,hi] with random sign; noise sd set so that the sample
+  variance of X beta over sigma^2 equals the SNR.    (1000 x 100,000, FP32)
+* ``genotype``      -- x_ij ~ Binomial(2, MAF_j), MAF_j ~ U[0.05, 0.5], int8;
+  k causal effects N(0, 0.3^2); sigma^2 = Var(g)(1-h2)/h2.  (5000 x 500,000)
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+SEED_BASE = 20170120
+
+_ELEM = {"f64": 8, "f32": 4, "bf16": 2, "i8": 1}
+_NP_DTYPE = {"f64": np.float64, "f32": np.float32, "i8": np.int8}
+
+
+def padded_ld(n: int, dtype: str) -> int:
+    """Leading dimension (elements) rounding each column up to 128 bytes."""
+    per = 128 // _ELEM[dtype]
+    return max(per, ((n + per - 1) // per) * per)
+
+
+def rng_for(workload: int, replicate: int) -> np.random.Generator:
+    key = np.array([SEED_BASE, workload * 1000 + replicate], dtype=np.uint64)
+    return np.random.Generator(np.random.Philox(key=key))
+
+
+@dataclass
+class Problem:
+    """One synthetic regression problem (raw, unstandardized data)."""
+    name: str
+    X: np.ndarray            # shape (p, ldx), storage dtype; column j = X[j, :n]
+    y: np.ndarray            # float64[n]
+    n: int
+    p: int
+    ldx: int
+    dtype: str               # "f64" | "f32" | "i8"
+    beta_true: np.ndarray    # float64[p], on the raw scale
+    alpha: float = 1.0
+    ratio: float = 0.1       # lambda_min / lambda_max
+    nlambda: int = 100
+    eps: float = 1e-7
+    meta: dict = field(default_factory=dict)
+
+    def dense_f64(self) -> np.ndarray:
+        """Stored values promoted exactly to FP64, as a (p, n) C-contiguous array
+        (column-major n x p with ldx = n)."""
+        return np.ascontiguousarray(self.X[:, : self.n], dtype=np.float64)
+
+
+def _alloc_x(n: int, p: int, dtype: str, pad_value: float) -> tuple[np.ndarray, int]:
+    ldx = padded_ld(n, dtype)
+    X = np.empty((p, ldx), dtype=_NP_DTYPE[dtype])
+    if ldx > n:
+        X[:, n:] = pad_value
+    return X, ldx
+
+
+def gaussian_iid(n=200, p=1000, k=10, noise_sd=1.0, dtype="f64", workload=1,
+                 replicate=0, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7,
+                 pad_value=0.0, name=None) -> Problem:
+    g = rng_for(workload, replicate)
+    X, ldx = _alloc_x(n, p, dtype, pad_value)
+    Xf = g.standard_normal((p, n))
+    X[:, :n] = Xf
+    beta = np.zeros(p)
+    k = min(k, p)
+    idx = g.choice(p, size=k, replace=False)
+    beta[idx] = np.where(g.random(k) < 0.5, -1.0, 1.0)
+    xs = X[:, :n].astype(np.float64)
+    y = xs.T @ beta + noise_sd * g.standard_normal(n)
+    return Problem(name or f"iid_{n}x{p}_{dtype}", X, y, n, p, ldx, dtype, beta,
+                   alpha, ratio, nlambda, eps, {"k": k, "noise_sd": noise_sd})
+
+
+def gaussian_ar1(n=1000, p=100_000, rho=0.5, k=20, lo=0.5, hi=1.5, snr=3.0,
+                 dtype="f32", workload=2, replicate=0, alpha=1.0, ratio=0.05,
+                 nlambda=100, eps=1e-7, pad_value=0.0, name=None) -> Problem:
+    g = rng_for(workload, replicate)
+    X, ldx = _alloc_x(n, p, dtype, pad_value)
+    E = g.standard_normal((p, n))
+    a = np.sqrt(1.0 - rho * rho)
+    prev = E[0]
+    X[0, :n] = prev
+    for j in range(1, p):
+        prev = rho * prev + a * E[j]
+        X[j, :n] = prev
+    del E
+    beta = np.zeros(p)
+    k = min(k, p)
+    idx = g.choice(p, size=k, replace=False)
+    mag = g.uniform(lo, hi, size=k)
+    sgn = np.where(g.random(k) < 0.5, -1.0, 1.0)
+    beta[idx] = sgn * mag
+    xs = X[idx, :n].astype(np.float64)
+    signal = xs.T @ beta[idx]
+    var_sig = float(np.var(signal))
+    sigma = np.sqrt(var_sig / snr) if var_sig > 0 else 1.0
+    y = signal + sigma * g.standard_normal(n)
+    return Problem(name or f"ar1_{n}x{p}_{dtype}", X, y, n, p, ldx, dtype, beta,
+                   alpha, ratio, nlambda, eps,
+                   {"rho": rho, "k": k, "snr": snr, "sigma": sigma})
+
+
+def genotype(n=5000, p=500_000, k=50, effect_sd=0.3, h2=0.3, workload=3,
+             replicate=0, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7,
+             pad_value=0, name=None) -> Problem:
+    g = rng_for(workload, replicate)
+    X, ldx = _alloc_x(n, p, "i8", pad_value)
+    maf = g.uniform(0.05, 0.5, size=p)
+    chunk = max(1, (1 << 24) // max(n, 1))
+    for j0 in range(0, p, chunk):
+        j1 = min(p, j0 + chunk)
+        X[j0:j1, :n] = g.binomial(2, maf[j0:j1, None], size=(j1 - j0, n)).astype(np.int8)
+    beta = np.zeros(p)
+    k = min(k, p)
+    idx = g.choice(p, size=k, replace=False)
+    beta[idx] = effect_sd * g.standard_normal(k)
+    gvals = X[idx, :n].astype(np.float64).T @ beta[idx]
+    vg = float(np.var(gvals))
+    sigma = np.sqrt(vg * (1.0 - h2) / h2) if vg > 0 else 1.0
+    y = gvals + sigma * g.standard_normal(n)
+    return Problem(name or f"geno_{n}x{p}", X, y, n, p, ldx, "i8", beta, alpha,
+                   ratio, nlambda, eps, {"k": k, "h2": h2, "sigma": sigma})
+
+
+def workload(index: int, replicate: int = 0, scale: Optional[float] = None,
+             pad_value=0.0) -> Problem:
+    """The benchmark workloads by number, optionally shrunk in p (and n) by
+    ``scale`` for oracle-sized parity cases.
+
+    1: 200 x 1000 iid Gaussian, FP64, 10 nonzero +-1, unit noise, ratio 0.1.
+    2: 1000 x 100,000 AR(1) rho=0.5, FP32, 20 nonzero U[0.5,1.5], SNR 3, ratio 0.05.
+    3: 5000 x 500,000 genotype int8, 50 causal, h2 0.3, ratio 0.1.
+    """
+    if index == 1:
+        n, p = 200, 1000
+        if scale:
+            p = max(8, int(p * scale))
+        return gaussian_iid(n, p, 10, 1.0, "f64", 1, replicate, 1.0, 0.1, 100,
+                            1e-7, pad_value, name=f"w1_iid_{n}x{p}_f64")
+    if index == 2:
+        n, p = 1000, 100_000
+        if scale:
+            n = max(16, int(n * min(1.0, scale * 10)))
+            p = max(16, int(p * scale))
+        return gaussian_ar1(n, p, 0.5, 20, 0.5, 1.5, 3.0, "f32", 2, replicate,
+                            1.0, 0.05, 100, 1e-7, pad_value,
+                            name=f"w2_ar1_{n}x{p}_f32")
+    if index == 3:
+        n, p = 5000, 500_000
+        if scale:
+            n = max(16, int(n * min(1.0, scale * 10)))
+            p = max(16, int(p * scale))
+        return genotype(n, p, 50, 0.3, 0.3, 3, replicate, 1.0, 0.1, 100, 1e-7,
+                        int(pad_value), name=f"w3_geno_{n}x{p}_i8")
+    raise ValueError(f"unknown workload {index}")

@@ -1,0 +1,433 @@
+"""Pins for the FP64 oracle: each check ties it to something other than itself.
+
+* a hand-worked example (tests/golden/hand_path_4x2.txt, derived on paper);
+* standardization invariants (Sec. 3.1: mean 0, (1/n) sum xt^2 = 1);
+* the closed-form soft-threshold solution on an orthonormal design;
+* brute-force enumeration of supports and signs for p <= 8 (lasso and
+  elastic net), which solves the optimality conditions directly;
+* the KKT conditions at every lambda of a correlated path, in NumPy;
+* BEDPP against an independent vector-form EDPP evaluation, its safety
+  against the oracle's active sets, and its power near lambda_max;
+* a planted mistake in a copy of the oracle's source must break a pin.
+"""
+import ctypes as C
+import itertools
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from conftest import read_golden
+from paper_1701_05936_gb300 import synth
+
+
+# ----------------------------------------------------------------- helpers ---
+def np_standardize(X):
+    """NumPy library routines: mean and population std (ddof=0)."""
+    c = X.mean(axis=1)
+    s = X.std(axis=1)
+    Xt = (X - c[:, None]) / s[:, None]
+    return Xt, c, s
+
+
+def brute_force(Xt, yc, lam, alpha):
+    """Unique minimizer by enumerating supports S and sign vectors sigma_S.
+
+    For each (S, sigma) solve (G_SS + lam(1-alpha) I) b_S = g_S - lam alpha sigma_S
+    with G = Xt Xt'/n, g = Xt yc/n; accept when sign(b_S) = sigma_S and
+    |g_j - G_jS b_S| <= lam alpha off S.  Returns (beta, number accepted)."""
+    p, n = Xt.shape
+    G = Xt @ Xt.T / n
+    g = Xt @ yc / n
+    t = lam * alpha
+    found, count = np.zeros(p), 0
+    tol = 1e-11 * max(1.0, t)
+    for m in range(0, p + 1):
+        for S in itertools.combinations(range(p), m):
+            S = list(S)
+            off = [j for j in range(p) if j not in S]
+            if m == 0:
+                if np.all(np.abs(g) <= t + tol):
+                    found, count = np.zeros(p), count + 1
+                continue
+            A = G[np.ix_(S, S)] + lam * (1 - alpha) * np.eye(m)
+            Ainv = np.linalg.inv(A)
+            signs = np.array(list(itertools.product([-1.0, 1.0], repeat=m)))  # (2^m, m)
+            B = (Ainv @ (g[S][:, None] - t * signs.T))  # (m, 2^m)
+            ok = np.all(np.sign(B) == signs.T, axis=0)
+            for col in np.nonzero(ok)[0]:
+                b = B[:, col]
+                zoff = g[off] - G[np.ix_(off, S)] @ b
+                if np.all(np.abs(zoff) <= t + tol):
+                    found = np.zeros(p)
+                    found[S] = b
+                    count += 1
+    return found, count
+
+
+def corr_design(n, p, rho, rng):
+    X = np.empty((p, n))
+    X[0] = rng.standard_normal(n)
+    for j in range(1, p):
+        X[j] = rho * X[j - 1] + np.sqrt(1 - rho * rho) * rng.standard_normal(n)
+    return X
+
+
+# ------------------------------------------------------ hand-worked example ---
+def test_hand_worked_example(golden_dir):
+    gd = read_golden(os.path.join(golden_dir, "hand_path_4x2.txt"))
+    rows = {r[0]: r[1:] for r in gd["data"]}
+    n, p = int(rows["n"][0]), int(rows["p"][0])
+    X = np.array([[float(v) for v in rows[f"x{j}"]] for j in range(p)])
+    y = np.array([float(v) for v in rows["y"]])
+    st = {r[0]: [float(v) for v in r[1:]] for r in gd["standardize"]}
+    c, s, keep = oracle.standardize(X)
+    np.testing.assert_allclose(c, st["c"], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(s, st["s"], rtol=0, atol=1e-15)
+    assert list(keep) == [int(v) for v in st["keep"]]
+    yc, ybar = oracle.center(y)
+    Xt = oracle.standardized_matrix(X, c, s, keep)
+    xty = oracle.xtv(Xt, yc)
+    lm = {r[0]: (float(r[1]), int(r[2])) for r in gd["lambda_max"]}
+    for key, alpha in (("alpha1", 1.0), ("alpha0.5", 0.5)):
+        lmax, js = oracle.lambda_max(xty, keep, n, alpha)
+        assert lmax == pytest.approx(lm[key][0], abs=1e-15) and js == lm[key][1]
+    for row in gd["solutions"]:
+        alpha, lam, b0, b1, b2, Q, icpt = map(float, row)
+        lmax, _ = oracle.lambda_max(xty, keep, n, alpha)
+        res = oracle.fit_path(X, y, alpha=alpha, lambdas=[lmax, lam], eps=1e-14)
+        np.testing.assert_allclose(res["beta"][1], [b0, b1, b2], atol=1e-14)
+        assert np.all(res["beta"][0] == 0.0)
+        assert res["loss"][1] == pytest.approx(Q, abs=1e-14)
+        assert res["intercept"][1] == pytest.approx(icpt, abs=1e-14)
+    lmax, js = oracle.lambda_max(xty, keep, n, 1.0)
+    xtxs, yy = oracle.bedpp_init(Xt, js, yc)
+    assert yy == pytest.approx(13.0, abs=1e-14)
+    for row in gd["bedpp"]:
+        lam = float(row[0])
+        safe = oracle.bedpp_safe(xty, xtxs, keep, n, lmax, js, yy, lam, 1.0)
+        assert list(safe) == [int(v) for v in row[1:]]
+
+
+# --------------------------------------------------------- standardization ---
+def test_standardize_invariants_and_constant_columns():
+    rng = np.random.default_rng(1)
+    n, p = 37, 50
+    X = rng.standard_normal((p, n)) * rng.uniform(0.01, 100, size=(p, 1)) + rng.uniform(-50, 50, (p, 1))
+    X[3] = 7.25                      # constant column
+    X[11] = 0.0                      # all-zero column
+    X[20] = 0.0
+    X[20, 5] = 1.0                   # one nonzero: not constant
+    c, s, keep = oracle.standardize(X)
+    assert keep[3] == 0 and keep[11] == 0 and keep[20] == 1
+    assert s[3] == 0.0 and s[11] == 0.0
+    k = keep.astype(bool)
+    np.testing.assert_allclose(c, X.mean(axis=1), rtol=1e-14, atol=1e-12)
+    np.testing.assert_allclose(s[k], X[k].std(axis=1), rtol=1e-13)
+    Xt = oracle.standardized_matrix(X, c, s, keep)
+    np.testing.assert_allclose(Xt[k].mean(axis=1), 0.0, atol=1e-13)
+    np.testing.assert_allclose((Xt[k] ** 2).mean(axis=1), 1.0, rtol=1e-13)
+    assert np.all(Xt[~k] == 0.0)
+
+
+def test_z_matches_blas_product():
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((40, 23)) + 3.0
+    r = rng.standard_normal(23)
+    c, s, keep = oracle.standardize(X)
+    Xt = oracle.standardized_matrix(X, c, s, keep)
+    Xt_np, _, _ = np_standardize(X)
+    np.testing.assert_allclose(oracle.z(Xt, r), Xt_np @ r / 23, rtol=1e-12, atol=1e-14)
+
+
+# --------------------------------------------------------------- closed form ---
+@pytest.mark.parametrize("alpha", [1.0, 0.5])
+def test_orthonormal_design_soft_threshold(alpha):
+    rng = np.random.default_rng(3)
+    n, p = 60, 25
+    A = rng.standard_normal((n, p))
+    A -= A.mean(axis=0)                       # project out the intercept
+    Q, _ = np.linalg.qr(A)
+    X = (np.sqrt(n) * Q).T                    # (p, n): xt'xt/n = I, 1'xt = 0
+    beta_true = np.zeros(p)
+    beta_true[:5] = [3, -2, 1.5, 0.7, -0.4]
+    y = X.T @ beta_true + 0.5 * rng.standard_normal(n) + 2.0
+    res = oracle.fit_path(X, y, alpha=alpha, ratio=0.01, nlambda=100, eps=1e-14)
+    yc = y - y.mean()
+    zj = X @ yc / n
+    for k, lam in enumerate(res["lambdas"]):
+        t = lam * alpha
+        exact = np.sign(zj) * np.maximum(np.abs(zj) - t, 0) / (1 + lam * (1 - alpha))
+        np.testing.assert_allclose(res["beta"][k], exact, atol=1e-12)
+    assert res["lmax"] == pytest.approx(np.max(np.abs(zj)) / alpha, rel=1e-13)
+
+
+# ------------------------------------------------------------- brute force ---
+@pytest.mark.parametrize("alpha,rho,seed", [(1.0, 0.0, 4), (1.0, 0.6, 5), (0.5, 0.3, 6)])
+def test_brute_force_support_enumeration(alpha, rho, seed):
+    rng = np.random.default_rng(seed)
+    n, p = 40, 8
+    X = corr_design(n, p, rho, rng) * 2.0 + 1.0
+    b = np.zeros(p)
+    b[[1, 4, 6]] = [1.0, -0.8, 0.5]
+    y = X.T @ b + 0.7 * rng.standard_normal(n)
+    res = oracle.fit_path(X, y, alpha=alpha, ratio=0.02, nlambda=100, eps=1e-13)
+    assert res["status"] == 0
+    Xt, _, _ = np_standardize(X)
+    yc = y - y.mean()
+    assert np.all(res["beta"][0] == 0)        # lambda_0 = lambda_max (pinned below)
+    for k in range(1, 100, 3):
+        lam = res["lambdas"][k]
+        bf, cnt = brute_force(Xt, yc, lam, alpha)
+        assert cnt == 1, (k, cnt)
+        np.testing.assert_allclose(res["beta"][k], bf, atol=1e-9)
+        assert np.array_equal(res["beta"][k] != 0, bf != 0)
+
+
+def test_lambda_max_is_the_entry_point():
+    """Just above lambda_max the solution is 0; just below, only x_* is active
+    with b_* = S(z_*, lam alpha)/(1 + lam(1-alpha)) (checked by brute force)."""
+    rng = np.random.default_rng(7)
+    n, p = 30, 7
+    X = rng.standard_normal((p, n))
+    y = 1.3 * X[2] + rng.standard_normal(n)
+    for alpha in (1.0, 0.7):
+        res = oracle.fit_path(X, y, alpha=alpha, ratio=0.5, nlambda=5, eps=1e-14)
+        lmax, js = res["lmax"], res["jstar"]
+        Xt, _, _ = np_standardize(X)
+        yc = y - y.mean()
+        bf_hi, _ = brute_force(Xt, yc, lmax * (1 + 1e-9), alpha)
+        assert np.all(bf_hi == 0)
+        lam = lmax * 0.999
+        bf_lo, cnt = brute_force(Xt, yc, lam, alpha)
+        assert cnt == 1 and np.count_nonzero(bf_lo) == 1 and bf_lo[js] != 0
+        zs = Xt[js] @ yc / n
+        expect = np.sign(zs) * (abs(zs) - lam * alpha) / (1 + lam * (1 - alpha))
+        assert bf_lo[js] == pytest.approx(expect, rel=1e-9)
+        res2 = oracle.fit_path(X, y, alpha=alpha, lambdas=[lmax, lam], eps=1e-14)
+        np.testing.assert_allclose(res2["beta"][1], bf_lo, atol=1e-12)
+
+
+# ---------------------------------------------------------------- KKT ---
+@pytest.mark.parametrize("alpha", [1.0, 0.6])
+def test_kkt_conditions_at_every_lambda(alpha):
+    rng = np.random.default_rng(8)
+    n, p = 80, 300
+    X = corr_design(n, p, 0.5, rng)
+    b = np.zeros(p)
+    b[rng.choice(p, 8, replace=False)] = rng.uniform(0.5, 1.5, 8) * rng.choice([-1, 1], 8)
+    y = X.T @ b + rng.standard_normal(n)
+    res = oracle.fit_path(X, y, alpha=alpha, ratio=0.05, nlambda=100, eps=1e-11)
+    assert res["status"] == 0
+    Xt, _, _ = np_standardize(X)
+    yc = y - y.mean()
+    for k, lam in enumerate(res["lambdas"]):
+        bk = res["beta"][k]
+        zk = Xt @ (yc - Xt.T @ bk) / n
+        nz = bk != 0
+        assert np.all(np.abs(zk[~nz]) <= lam * alpha + 1e-9)
+        stat = zk[nz] - lam * alpha * np.sign(bk[nz]) - lam * (1 - alpha) * bk[nz]
+        assert np.all(np.abs(stat) <= 1e-8), (k, np.abs(stat).max())
+        # objective: numpy restatement on the same beta agrees
+        Qnp = np.sum((yc - Xt.T @ bk) ** 2) / (2 * n) + lam * alpha * np.abs(bk).sum() \
+            + 0.5 * lam * (1 - alpha) * np.sum(bk ** 2)
+        assert res["loss"][k] == pytest.approx(Qnp, rel=1e-12)
+
+
+def test_objective_is_minimal_along_random_directions():
+    rng = np.random.default_rng(9)
+    n, p = 50, 40
+    X = rng.standard_normal((p, n))
+    y = X[:3].sum(axis=0) + rng.standard_normal(n)
+    res = oracle.fit_path(X, y, ratio=0.05, nlambda=20, eps=1e-13)
+    c, s, keep = oracle.standardize(X)
+    Xt = oracle.standardized_matrix(X, c, s, keep)
+    yc, _ = oracle.center(y)
+    for k in (5, 12, 19):
+        lam, bk = res["lambdas"][k], res["beta"][k]
+        q0 = oracle.objective(Xt, yc, bk, lam, 1.0)
+        for _ in range(20):
+            d = rng.standard_normal(p)
+            for t in (1e-3, 1e-5):
+                assert oracle.objective(Xt, yc, bk + t * d, lam, 1.0) >= q0 - 1e-14
+
+
+# ----------------------------------------------------------------- BEDPP ---
+def edpp_vector_form(Xt, yc, lam, n):
+    """Basic EDPP (Wang, Wonka & Ye) evaluated with explicit dual vectors in the
+    1/2||y - Xb||^2 + lam' ||b||_1 scaling (lam' = n lam), reference lam_max."""
+    corr = Xt @ yc
+    js = int(np.argmax(np.abs(corr)))
+    lmp = abs(corr[js])
+    lp = n * lam
+    theta0 = yc / lmp
+    v1 = np.sign(corr[js]) * Xt[js]
+    v2 = yc / lp - theta0
+    v2p = v2 - (v1 @ v2) / (v1 @ v1) * v1
+    lhs = np.abs(Xt @ (theta0 + 0.5 * v2p))
+    rhs = 1.0 - 0.5 * np.linalg.norm(v2p) * np.linalg.norm(Xt, axis=1)
+    return lhs < rhs, lhs, rhs
+
+
+def test_bedpp_matches_vector_form_edpp():
+    rng = np.random.default_rng(10)
+    disagree = 0
+    for trial in range(30):
+        n, p = int(rng.integers(5, 60)), int(rng.integers(2, 150))
+        X = corr_design(n, p, rng.uniform(0, 0.8), rng) if trial % 2 else rng.standard_normal((p, n))
+        y = X[: min(3, p)].T @ rng.standard_normal(min(3, p)) + rng.standard_normal(n)
+        c, s, keep = oracle.standardize(X)
+        Xt = oracle.standardized_matrix(X, c, s, keep)
+        yc, _ = oracle.center(y)
+        xty = oracle.xtv(Xt, yc)
+        lmax, js = oracle.lambda_max(xty, keep, n, 1.0)
+        xtxs, yy = oracle.bedpp_init(Xt, js, yc)
+        for frac in (0.999, 0.95, 0.8, 0.6, 0.4, 0.2, 0.05):
+            lam = lmax * frac
+            safe = oracle.bedpp_safe(xty, xtxs, keep, n, lmax, js, yy, lam, 1.0)
+            disc_v, lhs, rhs = edpp_vector_form(Xt, yc, lam, n)
+            clear = np.abs(lhs - rhs) > 1e-9 * np.maximum(1.0, np.abs(rhs))
+            disagree += int(np.sum(((safe == 0) != disc_v) & clear))
+    assert disagree == 0
+
+
+def test_bedpp_is_safe_on_random_paths():
+    rng = np.random.default_rng(11)
+    checked = 0
+    for trial in range(120):
+        n, p = int(rng.integers(8, 50)), int(rng.integers(5, 200))
+        rho = [0.0, 0.5, 0.9][trial % 3]
+        X = corr_design(n, p, rho, rng)
+        k = int(rng.integers(1, 6))
+        b = np.zeros(p)
+        b[rng.choice(p, min(k, p), replace=False)] = rng.standard_normal(min(k, p)) * 2
+        y = X.T @ b + rng.uniform(0.1, 2.0) * rng.standard_normal(n)
+        res = oracle.fit_path(X, y, ratio=0.05, nlambda=30, eps=1e-10)
+        Xt = oracle.standardized_matrix(X, res["c"], res["s"], res["keep"])
+        yc, _ = oracle.center(y)
+        xtxs, yy = oracle.bedpp_init(Xt, res["jstar"], yc)
+        for kk, lam in enumerate(res["lambdas"]):
+            safe = oracle.bedpp_safe(res["xty"], xtxs, res["keep"], n, res["lmax"],
+                                     res["jstar"], yy, lam, 1.0)
+            active = res["beta"][kk] != 0
+            assert not np.any(active & (safe == 0)), (trial, kk)
+            assert safe[res["jstar"]] == 1
+            checked += 1
+    assert checked == 120 * 30
+
+
+def test_bedpp_power_and_nesting():
+    """Near lambda_max BEDPP discards most features of an iid design, and the
+    safe set only grows as lambda decreases on this example."""
+    rng = np.random.default_rng(12)
+    n, p = 100, 2000
+    X = rng.standard_normal((p, n))
+    y = X[0] * 2 + rng.standard_normal(n)
+    c, s, keep = oracle.standardize(X)
+    Xt = oracle.standardized_matrix(X, c, s, keep)
+    yc, _ = oracle.center(y)
+    xty = oracle.xtv(Xt, yc)
+    lmax, js = oracle.lambda_max(xty, keep, n, 1.0)
+    xtxs, yy = oracle.bedpp_init(Xt, js, yc)
+    prev = None
+    sizes = []
+    for frac in np.linspace(1.0, 0.3, 30):
+        safe = oracle.bedpp_safe(xty, xtxs, keep, n, lmax, js, yy, lmax * frac, 1.0)
+        if prev is not None:
+            assert np.all(safe >= prev)
+        prev = safe
+        sizes.append(int(safe.sum()))
+    assert sizes[0] == 1                  # at lambda_max only x_* survives
+    assert sizes[3] < 0.2 * p             # 0.93 lambda_max: most discarded
+    safe_en = oracle.bedpp_safe(xty, xtxs, keep, n, lmax, js, yy, lmax * 0.9, 0.5)
+    assert np.array_equal(safe_en, keep)  # no safe rule for alpha < 1
+
+
+def test_strong_rule_definition():
+    z = np.array([0.9, 0.5, 0.79, -0.81, 0.0])
+    safe = np.array([1, 1, 1, 1, 0], dtype=np.uint8)
+    bprev = np.array([0, 0.2, 0, 0, 0.0])
+    # lam = 0.9, lam_prev = 1.0, alpha = 1: threshold 2*0.9 - 1.0 = 0.8
+    st = oracle.strong(z, safe, bprev, 0.9, 1.0, 1.0)
+    assert list(st) == [1, 1, 0, 1, 0]
+
+
+def test_cd_on_subset_matches_brute_force_on_subdesign():
+    rng = np.random.default_rng(13)
+    n, p = 30, 20
+    X = corr_design(n, p, 0.4, rng)
+    y = X[[2, 5, 9]].T @ np.array([1.0, -1.0, 0.6]) + 0.5 * rng.standard_normal(n)
+    c, s, keep = oracle.standardize(X)
+    Xt = oracle.standardized_matrix(X, c, s, keep)
+    yc, _ = oracle.center(y)
+    W = np.array([1, 2, 5, 7, 9, 13])
+    for alpha in (1.0, 0.5):
+        lam = 0.08
+        beta, r, sw, st = oracle.cd(Xt, W, lam, alpha, 1e-13, np.zeros(p), yc)
+        assert st == 0
+        bf, cnt = brute_force(Xt[W], yc, lam, alpha)
+        assert cnt == 1
+        np.testing.assert_allclose(beta[W], bf, atol=1e-10)
+        assert np.all(np.delete(beta, W) == 0)
+        np.testing.assert_allclose(r, yc - Xt.T @ beta, atol=1e-12)
+
+
+# ------------------------------------------------------- planted mistakes ---
+_MUTATIONS = {
+    "dropped_ridge_term": ("den = 1.0 + lam * (1.0 - alpha);", "den = 1.0;"),
+    "wrong_sign_warm_start": ("double zt = acc / (double)n + old;", "double zt = acc / (double)n - old;"),
+    "sample_sd_divisor": ("s[j] = varies ? sqrt(ss / (double)n) : 0.0;",
+                          "s[j] = varies ? sqrt(ss / (double)(n - 1)) : 0.0;"),
+    "bedpp_sign_flip": ("- (lmax - lam) * sstar * lmax * xtxstar[j]",
+                        "+ (lmax - lam) * sstar * lmax * xtxstar[j]"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(_MUTATIONS))
+def test_planted_mistake_in_oracle_copy_is_caught(name, monkeypatch):
+    """Compile a copy of the oracle with one plausible mistake; a pin must fail."""
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "oracle.c")).read()
+    old, new = _MUTATIONS[name]
+    assert old in src
+    with tempfile.TemporaryDirectory() as td:
+        cpath, so = os.path.join(td, "m.c"), os.path.join(td, "libm_orc.so")
+        open(cpath, "w").write(src.replace(old, new))
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-o", so, cpath, "-lm"])
+        good = oracle.lib()
+        monkeypatch.setattr(oracle, "_lib", None)
+        monkeypatch.setattr(oracle, "build", lambda force=False: so)
+        caught = False
+        try:
+            if name == "bedpp_sign_flip":
+                test_bedpp_matches_vector_form_edpp()
+            elif name == "sample_sd_divisor":
+                test_standardize_invariants_and_constant_columns()
+            else:
+                test_brute_force_support_enumeration(0.5, 0.3, 6)
+        except AssertionError:
+            caught = True
+        finally:
+            monkeypatch.setattr(oracle, "_lib", good)
+        assert caught, f"mutation {name} was not detected"
+
+
+# --------------------------------------------------------- input generator ---
+def test_synthetic_inputs_are_seeded_and_padded():
+    a = synth.workload(2, scale=0.002, pad_value=np.nan)
+    b = synth.workload(2, scale=0.002, pad_value=np.nan)
+    assert a.X.shape == (a.p, a.ldx) and a.ldx % 32 == 0 and a.ldx >= a.n
+    assert np.array_equal(a.X[:, : a.n], b.X[:, : b.n]) and np.array_equal(a.y, b.y)
+    assert np.all(np.isnan(a.X[:, a.n:]))
+    c = synth.workload(2, replicate=1, scale=0.002)
+    assert not np.array_equal(a.y, c.y)
+    g = synth.genotype(n=64, p=100, k=5)
+    assert g.X.dtype == np.int8 and set(np.unique(g.X[:, :64])) <= {0, 1, 2}
+    # AR(1) neighbour correlation close to rho on a larger draw
+    w = synth.gaussian_ar1(n=2000, p=50, rho=0.5, k=3, dtype="f64")
+    xs = w.X[:, : w.n]
+    r = np.mean([np.corrcoef(xs[j], xs[j + 1])[0, 1] for j in range(49)])
+    assert abs(r - 0.5) < 0.05
