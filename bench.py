@@ -1,0 +1,314 @@
+#!/usr/bin/env python
+"""Benchmark: 100-lambda lasso paths per second on one or more GB300s.
+
+Workload (the path the headline metric is quoted on): a 1000 x 100,000 FP32
+design with AR(1) column correlation rho = 0.5, 20 nonzero coefficients
+U[0.5, 1.5] with random signs, noise for SNR 3, 100 log-spaced lambdas down
+to 0.05 lambda_max, alpha = 1, SSR-BEDPP screening, CD tolerance 1e-7.
+One step = one whole path through ``bl_fit_path`` (standardization,
+lambda_max, BEDPP init, and all 100 lambdas) with X and y already in HBM.
+The 400 MB design is larger than the 129 MB L2, so no extra flush is done.
+
+Under torchrun each rank fits its own replicate (a different seed) -- the
+path has no data-path exchange, so scaling is weak and there is no
+collective besides the timing barrier and the max over ranks.
+
+``--impl reference`` times the FP64 oracle on the host cores instead: each
+step runs 10 consecutive lambdas of one warm-started oracle path (ten steps
+make one path); the value is paths/s extrapolated from lambdas done.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "100-λ lasso paths/s and Xᵀr GB/s vs HBM peak; chosen vs plain form at 1e-5"
+WORKLOAD_NAME = "ar1_1000x100000_f32_rho0.5_k20_snr3_ratio0.05_alpha1_ssr-bedpp_eps1e-7"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", action="store_true", help="a small workload for profiling runs")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_problem(rank: int, small: bool):
+    from paper_1701_05936_gb300 import synth
+    if small:
+        return synth.gaussian_ar1(n=1000, p=40_000, rho=0.5, k=20, snr=3.0, dtype="f32", workload=2,
+                                  replicate=rank, ratio=0.05)
+    return synth.workload(2, replicate=rank)
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.lines: list[str] = []
+        self.proc = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def zpass_traffic():
+    """Per-launch DRAM bytes of the z pass from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "zpass_traffic.json")
+    src = os.path.join(ROOT, "paper_1701_05936_gb300", "csrc", "bl_zpass.cu")
+    try:
+        meta = json.load(open(path))
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if meta.get("source_sha256") == h:
+            return meta
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def cpu_baseline(prob):
+    """The FP64 oracle as it stands, one full 100-lambda path, single thread."""
+    import oracle
+    X = prob.dense_f64()
+    t0 = time.perf_counter()
+    runner = oracle.PathRunner(X, prob.y, prob.alpha, prob.ratio, prob.nlambda, prob.eps)
+    while not runner.done:
+        runner.advance(10)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": "paths/s", "cores": 1, "kind": "oracle",
+            "sample": f"one full 100-lambda path of the same {prob.n}x{prob.p} workload (replicate 0), "
+                      f"FP64 oracle, no screening, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    import oracle  # noqa: F401
+    prob = make_problem(0, args.small)
+    X = prob.dense_f64()
+    import oracle as orc
+
+    def fresh():
+        return orc.PathRunner(X, prob.y, prob.alpha, prob.ratio, prob.nlambda, prob.eps)
+
+    runner = fresh()
+    for _ in range(args.warmup):
+        runner.advance(1)
+    runner = fresh()
+    lam_done = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        if runner.done:
+            runner = fresh()
+        lam_done += runner.advance(10)
+    dt = time.perf_counter() - t0
+    value = (lam_done / prob.nlambda) / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config(prob),
+        "cpu_baseline": {"value": value, "unit": "paths/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} steps x 10 consecutive lambdas of a warm-started 100-lambda "
+                                   f"oracle path ({lam_done} lambdas)"},
+        "e2e": {"value": value, "unit": "paths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config(prob):
+    return {"workload": WORKLOAD_NAME if prob.p == 100_000 else f"ar1_{prob.n}x{prob.p}_f32_small",
+            "n": prob.n, "p": prob.p, "ldx": prob.ldx, "nlambda": prob.nlambda, "lambda_min_ratio": prob.ratio,
+            "alpha": prob.alpha, "eps": prob.eps, "screen": "SSR-BEDPP",
+            "l2": "inputs larger than L2 (400 MB design vs 129 MB L2); no flush"}
+
+
+def run_ours(args):
+    import torch
+    from paper_1701_05936_gb300 import bl
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    prob = make_problem(rank, args.small)
+    X = torch.from_numpy(prob.X).to(dev)
+    y = torch.from_numpy(prob.y).to(dev)
+    ctx = bl.Context(local)
+    kw = dict(alpha=prob.alpha, ratio=prob.ratio, nlambda=prob.nlambda, eps=prob.eps)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(max(args.warmup, 0)):
+        res = bl.bl_fit_path(ctx, X, prob.n, y, **kw)
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    clocks = ClockSampler(f"GPU-{uuid}" if uuid else None)
+    stream = ctx.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0.record(stream)
+    for _ in range(args.steps):
+        res = bl.bl_fit_path(ctx, X, prob.n, y, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    tim = ctx.timing()
+    ms_all = ms
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_all = float(t.item())
+    value = world * args.steps / (ms_all / 1e3)
+
+    # end to end through the public API from pinned host buffers
+    Xh = torch.from_numpy(prob.X).pin_memory()
+    yh = torch.from_numpy(prob.y).pin_memory()
+    e2e_steps = max(1, args.e2e_steps)
+    barrier()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    d2h = 0
+    for _ in range(e2e_steps):
+        out = bl.fit_path(Xh, prob.n, yh, device=local, ctx=ctx, **kw)
+        d2h = sum(out[k].numel() * out[k].element_size()
+                  for k in ("lambdas", "col_ptr", "row_idx", "val", "val_orig", "intercept", "loss"))
+    f1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = f0.elapsed_time(f1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * e2e_steps / (e2e_ms / 1e3)
+
+    z = tim["zpass"]
+    peaks, which = measured_peaks()
+    achieved = (z["bytes"] / 1e9) / (z["ms"] / 1e3) if z["ms"] > 0 else 0.0
+    traffic = zpass_traffic()
+    roofline = {"bound": "hbm", "kernel": "k_zpass (X'r z pass + KKT check)", "achieved": achieved,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "peak_source": f"{which} hbm_gbs (copy bandwidth)",
+                "frac_nominal_8TBs": achieved / 8000.0,
+                "traffic": (traffic["dram_bytes_per_launch"] if traffic else None),
+                "algorithmic_bytes_per_launch": z["bytes"] / max(1, z["launches"]),
+                "launches": z["launches"], "avg_launch_us": 1e3 * z["ms"] / max(1, z["launches"])}
+    breakdown = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps}
+                 for k, v in tim.items() if isinstance(v, dict)}
+    line = {
+        "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(prob),
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": "paths/s", "h2d_bytes_per_step": int(prob.X.nbytes + prob.y.nbytes),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(tim["kernel_launches"]), "clocks": clk,
+        "kernel_ms_per_step": breakdown, "status": res["status"],
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(prob)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

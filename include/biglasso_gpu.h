@@ -1,0 +1,257 @@
+/*
+ * biglasso_gpu.h -- C ABI of the GB300 (sm_103a) hot path of the pathwise
+ * lasso / elastic-net solver with hybrid safe-strong (SSR-BEDPP) screening
+ * described in "The biglasso Package: A Memory- and Computation-Efficient
+ * Solver for Lasso Model Fitting with Big Data in R" (Zeng & Breheny).
+ *
+ * Problem (linear regression, unpenalized intercept), for a raw n x p design X
+ * and response y:
+ *     minimize_b  (1/2n) ||yc - Xt b||^2 + lam*alpha*||b||_1 + lam*(1-alpha)/2*||b||^2
+ * where yc = y - mean(y) and Xt is the cell-wise standardized design
+ * xt_ij = (x_ij - c_j)/s_j, with c_j the column mean and s_j the population
+ * standard deviation (Sec. 3.1; the 1/n normalization of the Sec. 2 notation).
+ * The paper does not print the objective; this is the standard form that its
+ * Sec. 4.4 objective comparison refers to.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every function returns a bl_status (0 = BL_OK).  On failure the message is
+ *   available from bl_last_error(ctx).  No C++ exception crosses the ABI.
+ * - Arrays documented as "device" must be device memory of the ctx's GPU;
+ *   "host" arrays are ordinary CPU memory.  The caller owns every array it
+ *   passes.  The library owns only the workspace inside a bl_ctx, which it
+ *   allocates and grows itself (cudaMalloc) and frees in bl_ctx_destroy.
+ * - Work is enqueued on the ctx stream.  Calls that return host scalars
+ *   (documented below) synchronize that stream before returning; the others
+ *   are asynchronous.  A ctx is used by one host thread at a time.
+ * - Design matrix arguments "X, dtype, n, p, ldx": X is a device pointer to a
+ *   column-major n x p matrix with leading dimension ldx (elements), so column
+ *   j starts at element j*ldx.  dtype is a bl_dtype.  Requirements (else
+ *   BL_ERR_ARG before any launch): n >= 1, p >= 1, ldx >= n,
+ *   ldx*sizeof(elem) a multiple of 16 bytes, X 16-byte aligned.  The rows
+ *   n..ldx-1 of each column are never read for arithmetic.
+ *   Indices are 64-bit, so n*ldx may exceed 2^31.
+ * - Per-feature vectors are length p, per-observation vectors length n.
+ */
+#ifndef BIGLASSO_GPU_H
+#define BIGLASSO_GPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BL_OK = 0,
+    BL_ERR_ARG = -1,           /* invalid argument; nothing was launched */
+    BL_ERR_CUDA = -2,          /* a CUDA runtime call failed */
+    BL_ERR_OOM = -3,           /* workspace allocation failed */
+    BL_ERR_NOT_CONVERGED = -4, /* sweep cap reached; outputs hold the last iterate */
+    BL_ERR_TIMEOUT = -5,       /* a bounded device-side wait gave up */
+    BL_ERR_UNSUPPORTED = -6,   /* valid input beyond this build's limits */
+    BL_ERR_CAPACITY = -7       /* output buffer too small; needed size reported */
+} bl_status;
+
+typedef enum { BL_F64 = 0, BL_F32 = 1, BL_BF16 = 2, BL_I8 = 3 } bl_dtype;
+
+typedef enum {
+    BL_SCREEN_NONE = 0,      /* every kept feature is scanned and enters CD */
+    BL_SCREEN_SSR = 1,       /* strong rule + KKT check over all features */
+    BL_SCREEN_SSR_BEDPP = 2  /* hybrid rule of Sec. 2.2 (default) */
+} bl_screen_rule;
+
+typedef struct bl_ctx bl_ctx;
+
+/* Largest working set (features entering coordinate descent at one lambda)
+ * and largest n that the coordinate-descent kernel of this build accepts. */
+#define BL_MAX_WORKING 12288
+#define BL_MAX_N 16384
+
+/* Options of bl_fit_path. */
+typedef struct {
+    double alpha;            /* elastic-net mixing, 0 < alpha <= 1 (1 = lasso) */
+    double eps;              /* convergence: max |delta b_j| over a sweep < eps */
+    double lambda_min_ratio; /* grid end lambda_min/lambda_max, 0 < ratio < 1 */
+    int64_t max_sweeps;      /* cap on CD sweeps per lambda (e.g. 100000) */
+    int32_t screen;          /* bl_screen_rule */
+    int32_t reserved;
+} bl_options;
+
+/* Outputs of bl_fit_path.  Pointers marked device are caller-allocated device
+ * memory; pointers marked host are caller-allocated host memory; any pointer
+ * marked nullable may be NULL.  The coefficient path is stored sparse, one
+ * compressed column per lambda (the sparse coding of Sec. 3.1): the nonzero
+ * coefficients of lambda_k are val[col_ptr[k] .. col_ptr[k+1]) at feature
+ * indices row_idx[...] (ascending). */
+typedef struct {
+    double *lambdas;       /* device [K]: the lambda sequence used */
+    int64_t *col_ptr;      /* device [K+1] */
+    int32_t *row_idx;      /* device [nnz_capacity] */
+    double *val;           /* device [nnz_capacity]: b_j on the standardized scale */
+    double *val_orig;      /* device [nnz_capacity], nullable: b_j / s_j (raw scale) */
+    int64_t nnz_capacity;  /* in: capacity of row_idx/val/val_orig */
+    int64_t nnz_needed;    /* out (host): total nonzeros of the path */
+    double *intercept;     /* device [K]: mean(y) - sum_j c_j b_j / s_j */
+    double *loss;          /* device [K]: objective Q(b(lam_k); lam_k), FP64 */
+    int64_t *sweeps;       /* host [K], nullable: CD sweeps at each lambda */
+    int64_t *n_safe;       /* host [K], nullable: |S_k|, features BEDPP keeps */
+    int64_t *n_strong;     /* host [K], nullable: strong-set size */
+    int64_t *kkt_rounds;   /* host [K], nullable: KKT passes (1 = no violation) */
+    int64_t *cols_scanned; /* host [K], nullable: columns read by the z passes */
+    int64_t *n_active;     /* host [K], nullable: nonzero coefficients */
+    double lambda_max;     /* out (host) */
+    int64_t jstar;         /* out (host): column attaining lambda_max, -1 if none */
+    double ybar;           /* out (host): mean(y) */
+} bl_path;
+
+/* Per-kernel timing collected with CUDA events on the ctx stream while timing
+ * is enabled (bl_ctx_set_timing).  Kinds: 0 standardize, 1 lambda_max,
+ * 2 bedpp_init, 3 screen, 4 compact, 5 cd, 6 residual, 7 zpass, 8 record. */
+#define BL_NUM_KINDS 9
+typedef struct {
+    int64_t launches[BL_NUM_KINDS];
+    double ms[BL_NUM_KINDS];         /* summed device time */
+    double bytes[BL_NUM_KINDS];      /* summed algorithmic bytes: the stored
+                                        design elements the pass reads */
+    int64_t kernel_launches;         /* CUDA kernels launched since the ctx was
+                                        created or timing was last enabled
+                                        (counted whether or not timing is on) */
+} bl_timing;
+
+/* ---------------------------------------------------------------- context -- */
+
+/* Create a context on CUDA device `device` that enqueues on `stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  No workspace is allocated
+ * until a call needs it.  Errors: BL_ERR_ARG (ctx NULL), BL_ERR_CUDA. */
+int bl_ctx_create(bl_ctx **ctx, int device, void *stream);
+
+/* Free the workspace (after synchronizing the stream) and the context. */
+int bl_ctx_destroy(bl_ctx *ctx);
+
+/* Replace the stream used by later calls. */
+int bl_ctx_set_stream(bl_ctx *ctx, void *stream);
+
+/* Message of the last failing call on this ctx ("" if none).  The string is
+ * owned by the ctx and valid until its next call. */
+const char *bl_last_error(const bl_ctx *ctx);
+
+/* Enable (1) or disable (0) per-kernel event timing; enabling clears totals. */
+int bl_ctx_set_timing(bl_ctx *ctx, int enable);
+
+/* Copy the timing totals (synchronizes the stream). */
+int bl_ctx_get_timing(bl_ctx *ctx, bl_timing *out);
+
+/* Library version string, e.g. "1.0.0 sm_103a". */
+const char *bl_version(void);
+
+/* -------------------------------------------------------- one-time passes -- */
+
+/* Cell-wise standardization statistics (Sec. 3.1): center[j] = mean of
+ * column j, scale[j] = population standard deviation (divisor n),
+ * xnorm[j] = ||x_j||_2 of the raw column (used for rounding bounds),
+ * keep[j] = 0 when all n entries of column j are equal (then scale[j] = 0).
+ * Outputs: device FP64 [p] (xnorm nullable), device uint8 [p].  One pass over X.
+ * Asynchronous. */
+int bl_standardize(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx,
+                   double *center, double *scale, double *xnorm, uint8_t *keep);
+
+/* lambda_max and the correlations xt_j' yc (simplification (2) of Sec. 3.1.1:
+ * xt_j'y = (sum_i x_ij y_i - c_j sum_i y_i)/s_j).  y: device FP64 [n];
+ * center/scale/keep: outputs of bl_standardize.  Outputs: yc device FP64 [n]
+ * (y - mean y), xty device FP64 [p] (0 for keep=0 columns), host scalars
+ * *lambda_max = max_j |xty_j|/(n alpha) over kept columns, *jstar = its
+ * column (lowest index on ties; -1 and lambda_max 0 if no column is kept),
+ * *ybar = mean(y).  Synchronizes.  Errors: BL_ERR_ARG if alpha not in (0,1]. */
+int bl_lambda_max(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx,
+                  const double *center, const double *scale, const uint8_t *keep,
+                  const double *y, double alpha, double *yc, double *xty,
+                  double *lambda_max, int64_t *jstar, double *ybar);
+
+/* BEDPP precomputation (Sec. 2.2 with simplification (1) of Sec. 3.1.1):
+ * xtxstar[j] = xt_j' xt_* = (sum_i x_ij x_i* - n c_j c_*)/(s_j s_*) for the
+ * column jstar of lambda_max, and *ynorm2 = ||yc||^2 (host).  yc: device FP64
+ * [n] from bl_lambda_max.  xtxstar: device FP64 [p].  Synchronizes. */
+int bl_bedpp_init(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx,
+                  const double *center, const double *scale, const uint8_t *keep,
+                  const double *yc, int64_t jstar, double *xtxstar, double *ynorm2);
+
+/* ------------------------------------------------------------ per lambda -- */
+
+/* Screening at lam (Sec. 2.2).  safe[j] = 1 unless BEDPP (reference point
+ * lambda_max, alpha = 1 only; for alpha < 1 every kept feature is safe)
+ * discards j; BEDPP's discard test is tightened by a relative 1e-10 margin so
+ * FP64 rounding can never discard a feature the exact test keeps, and x_* is
+ * never discarded.  strong[j] = safe[j] && (beta_prev[j] != 0 ||
+ * |z_prev[j]| >= alpha (2 lam - lam_prev)) -- the sequential strong rule on
+ * z_prev = xt'r/n at the previous solution.  Inputs: xty/xtxstar device FP64
+ * [p], keep device uint8 [p], z_prev device FP32 [p], beta_prev device FP32
+ * [p] (nullable: treated as 0).  Outputs: safe/strong device uint8 [p];
+ * host counts *n_safe and *n_strong (nullable; when either is given the call
+ * synchronizes).  Errors: BL_ERR_ARG if lam >= lam_prev or lam <= 0. */
+int bl_screen(bl_ctx *ctx, int64_t n, int64_t p, const double *xty, const double *xtxstar,
+              const uint8_t *keep, double lambda_max, int64_t jstar, double ynorm2, double lam,
+              double lam_prev, double alpha, const float *z_prev, const float *beta_prev,
+              uint8_t *safe, uint8_t *strong, int64_t *n_safe, int64_t *n_strong);
+
+/* Full-feature correlation pass and post-convergence KKT check (Sec. 2.2 and
+ * simplification (3) of Sec. 3.1.1): for every column j with scan[j] != 0,
+ *     z[j] = xt_j' r / n = (sum_i x_ij r_i - c_j sum_i r_i) / (n s_j),
+ * and j is a violator when safe[j] && !working[j] && |z_j| > lam*alpha - tau_j,
+ * tau_j being a rigorous bound on the FP32 rounding error of z_j (so no true
+ * violation is missed).  Violators get working[j] = 1.  r: device FP32 [n]
+ * (FP64 when dtype is BL_F64).  z: device FP32 [p] (entries with scan[j] = 0
+ * are left unchanged).  xnorm from bl_standardize.  *n_viol (host, nullable:
+ * then asynchronous) = number of violators.  Reads n*|scan| elements of X. */
+int bl_kkt_check(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx,
+                 const double *center, const double *scale, const double *xnorm,
+                 const uint8_t *keep, const void *r, double lam, double alpha,
+                 const uint8_t *scan, const uint8_t *safe, uint8_t *working, float *z,
+                 int64_t *n_viol);
+
+/* Cyclic coordinate descent at one lambda over the working set (Sec. 1 and
+ * Sec. 3.1.1: pathwise CD with residual updates and active-set cycling):
+ * repeat { one sweep over work_idx in order; then sweeps over its nonzero
+ * coordinates until max |delta b| < eps } until a full sweep moves no
+ * coordinate by eps and creates no new nonzero.  Update of coordinate j:
+ *     zt = xt_j' r / n + b_j;  b_j' = S(zt, lam alpha)/(1 + lam (1-alpha));
+ *     r -= (b_j' - b_j) xt_j,   xt_ij = (x_ij - c_j)/s_j formed in registers.
+ * In FP32 a change below 2^-20 |b_j| also counts as converged (FP32 rounding
+ * floor).  work_idx: device int32 [n_work], ascending, kept features only,
+ * n_work <= BL_MAX_WORKING.  beta: device dense [p] (FP32; FP64 for BL_F64),
+ * only entries in work_idx change.  r: device [n] (same type), in/out, must
+ * equal yc - Xt b on entry.  *sweeps (host, nullable) = sweeps run.
+ * Synchronizes.  Errors: BL_ERR_NOT_CONVERGED after max_sweeps sweeps,
+ * BL_ERR_UNSUPPORTED when n > BL_MAX_N or n_work > BL_MAX_WORKING. */
+int bl_cd_active(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx,
+                 const double *center, const double *scale, const int32_t *work_idx,
+                 int64_t n_work, double lam, double alpha, void *beta, void *r, double eps,
+                 int64_t max_sweeps, int64_t *sweeps);
+
+/* ---------------------------------------------------------------- the path -- */
+
+/* The whole solution path over a decreasing lambda sequence with SSR-BEDPP
+ * screening (Sec. 2.2), warm starts and active-set cycling, all on the GPU:
+ * standardize, lambda_max, BEDPP init; then per lambda_k: screen, CD over
+ * the working set, residual recomputation in FP64, the z pass over S_k and
+ * S_{k+1} (KKT check for lambda_k and strong-rule input for lambda_{k+1});
+ * violators join the working set and CD repeats until the KKT check is
+ * clean.  X: device design; y: device FP64 [n].  lambdas_in: host FP64
+ * [nlambda], nullable -> the grid lambda_k = lambda_max * ratio^(k/(K-1)); when
+ * given it must be strictly decreasing and positive.  At lambda >= lambda_max
+ * (and at lambda_0 of the generated grid) the solution is exactly 0.  A
+ * response with no variation gives lambda_max = 0 and an all-zero path with
+ * BL_OK (lambdas all 0 when generated).  Synchronizes once per KKT pass and at
+ * the end.  Errors: BL_ERR_ARG (shapes, alpha, eps <= 0, ratio, non-decreasing
+ * lambdas), BL_ERR_CAPACITY (nnz_capacity < nnz_needed: col_ptr and the
+ * counters are complete, row_idx/val hold the first nnz_capacity entries),
+ * BL_ERR_NOT_CONVERGED, BL_ERR_UNSUPPORTED (see bl_cd_active). */
+int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx,
+                const double *y, const bl_options *opt, const double *lambdas_in, int nlambda,
+                bl_path *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BIGLASSO_GPU_H */

@@ -229,3 +229,39 @@ def fit_path(X, y, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, lambdas=None,
     return dict(lambdas=lambdas, beta=beta, beta_orig=beta_orig, intercept=icpt, loss=loss,
                 sweeps=sweeps, status=st, lmax=lmax, jstar=jstar, c=c, s=s, keep=keep,
                 ybar=ybar, xty=xty)
+
+
+class PathRunner:
+    """The oracle path advanced a few lambdas at a time (for timing bounded samples).
+
+    The same steps as ``fit_path``: standardize, form Xt, lambda_max, the grid,
+    then for each lambda the oracle's coordinate descent over every kept column
+    from the previous solution.  ``advance(m)`` runs the next m lambdas and
+    returns how many it ran; ``done`` is set after the last one."""
+
+    def __init__(self, X, y, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, max_sweeps=100_000):
+        X = _f64(X)
+        self.p, self.n = X.shape
+        c, s, keep = standardize(X)
+        self.yc, _ = center(y)
+        self.Xt = standardized_matrix(X, c, s, keep)
+        xty = xtv(self.Xt, self.yc)
+        self.lmax, _ = lambda_max(xty, keep, self.n, alpha)
+        self.lambdas = lambda_grid(self.lmax, ratio, nlambda)
+        self.idx = np.nonzero(keep)[0].astype(np.int64)
+        self.alpha, self.eps, self.max_sweeps = alpha, eps, max_sweeps
+        self.beta = np.zeros(self.p)
+        self.r = self.yc.copy()
+        self.k = 0
+        self.done = False
+
+    def advance(self, m):
+        ran = 0
+        while ran < m and self.k < len(self.lambdas):
+            if self.k > 0:          # lambda_0 = lambda_max: the solution is 0
+                self.beta, self.r, _, _ = cd(self.Xt, self.idx, self.lambdas[self.k], self.alpha,
+                                             self.eps, self.beta, self.r, self.max_sweeps)
+            self.k += 1
+            ran += 1
+        self.done = self.k >= len(self.lambdas)
+        return ran

@@ -1,0 +1,291 @@
+"""ctypes binding of libbl (``include/biglasso_gpu.h``).
+
+Argument marshalling only: the ``bl_*`` functions below take torch tensors,
+pass their device pointers and sizes to the C ABI, and raise ``BLError`` on a
+non-zero status.  Every step of the path runs in libbl's CUDA kernels; there
+is no CPU or PyTorch fallback -- without the built library or a GPU these
+functions raise.
+
+Design matrices are torch tensors of shape (p, ldx): row j of the tensor is
+column j of the column-major n x p design (only its first n entries are data),
+dtype float64, float32 or int8.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+from typing import Optional
+
+import torch
+
+from . import build as _build
+
+BL_OK, BL_ERR_ARG, BL_ERR_CUDA, BL_ERR_OOM = 0, -1, -2, -3
+BL_ERR_NOT_CONVERGED, BL_ERR_TIMEOUT, BL_ERR_UNSUPPORTED, BL_ERR_CAPACITY = -4, -5, -6, -7
+BL_F64, BL_F32, BL_BF16, BL_I8 = 0, 1, 2, 3
+BL_SCREEN_NONE, BL_SCREEN_SSR, BL_SCREEN_SSR_BEDPP = 0, 1, 2
+KINDS = ["standardize", "lambda_max", "bedpp_init", "screen", "compact", "cd", "residual", "zpass", "record"]
+
+_STATUS = {0: "BL_OK", -1: "BL_ERR_ARG", -2: "BL_ERR_CUDA", -3: "BL_ERR_OOM", -4: "BL_ERR_NOT_CONVERGED",
+           -5: "BL_ERR_TIMEOUT", -6: "BL_ERR_UNSUPPORTED", -7: "BL_ERR_CAPACITY"}
+_DTYPE = {torch.float64: BL_F64, torch.float32: BL_F32, torch.int8: BL_I8}
+
+
+class BLError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class bl_options(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("eps", C.c_double), ("lambda_min_ratio", C.c_double),
+                ("max_sweeps", C.c_int64), ("screen", C.c_int32), ("reserved", C.c_int32)]
+
+
+class bl_path(C.Structure):
+    _fields_ = [("lambdas", C.c_void_p), ("col_ptr", C.c_void_p), ("row_idx", C.c_void_p),
+                ("val", C.c_void_p), ("val_orig", C.c_void_p), ("nnz_capacity", C.c_int64),
+                ("nnz_needed", C.c_int64), ("intercept", C.c_void_p), ("loss", C.c_void_p),
+                ("sweeps", C.c_void_p), ("n_safe", C.c_void_p), ("n_strong", C.c_void_p),
+                ("kkt_rounds", C.c_void_p), ("cols_scanned", C.c_void_p), ("n_active", C.c_void_p),
+                ("lambda_max", C.c_double), ("jstar", C.c_int64), ("ybar", C.c_double)]
+
+
+class bl_timing(C.Structure):
+    _fields_ = [("launches", C.c_int64 * 9), ("ms", C.c_double * 9), ("bytes", C.c_double * 9),
+                ("kernel_launches", C.c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp, _i64, _int, _dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libbl.so, building it first when it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(_build.build())
+            X = [_vp, _int, _i64, _i64, _i64]
+            sig = {
+                "bl_ctx_create": [C.POINTER(_vp), _int, _vp],
+                "bl_ctx_destroy": [_vp],
+                "bl_ctx_set_stream": [_vp, _vp],
+                "bl_ctx_set_timing": [_vp, _int],
+                "bl_ctx_get_timing": [_vp, C.POINTER(bl_timing)],
+                "bl_standardize": [_vp, *X, _vp, _vp, _vp, _vp],
+                "bl_lambda_max": [_vp, *X, _vp, _vp, _vp, _vp, _dbl, _vp, _vp, C.POINTER(_dbl),
+                                  C.POINTER(_i64), C.POINTER(_dbl)],
+                "bl_bedpp_init": [_vp, *X, _vp, _vp, _vp, _vp, _i64, _vp, C.POINTER(_dbl)],
+                "bl_screen": [_vp, _i64, _i64, _vp, _vp, _vp, _dbl, _i64, _dbl, _dbl, _dbl, _dbl, _vp, _vp,
+                              _vp, _vp, C.POINTER(_i64), C.POINTER(_i64)],
+                "bl_kkt_check": [_vp, *X, _vp, _vp, _vp, _vp, _vp, _dbl, _dbl, _vp, _vp, _vp, _vp,
+                                 C.POINTER(_i64)],
+                "bl_cd_active": [_vp, *X, _vp, _vp, _vp, _i64, _dbl, _dbl, _vp, _vp, _dbl, _i64,
+                                 C.POINTER(_i64)],
+                "bl_fit_path": [_vp, *X, _vp, C.POINTER(bl_options), C.POINTER(_dbl), _int,
+                                C.POINTER(bl_path)],
+            }
+            for name, args in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = _int
+            L.bl_last_error.argtypes = [_vp]
+            L.bl_last_error.restype = C.c_char_p
+            L.bl_version.argtypes = []
+            L.bl_version.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+def header_symbols() -> list[str]:
+    """Names of every function the public header declares."""
+    path = os.path.join(os.path.dirname(_build.HERE), "include", "biglasso_gpu.h")
+    text = open(path).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(bl_\w+)\s*\(", text, flags=re.M)))
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """A bl_ctx bound to one CUDA device and (by default) torch's current stream."""
+
+    def __init__(self, device: int = 0, stream: Optional[torch.cuda.Stream] = None):
+        if not torch.cuda.is_available():
+            raise BLError(BL_ERR_CUDA, "no CUDA device: libbl has no CPU path")
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        h = C.c_void_p()
+        st = lib().bl_ctx_create(C.byref(h), device, C.c_void_p(self.stream.cuda_stream))
+        if st != BL_OK:
+            raise BLError(st, "bl_ctx_create failed")
+        self.h = h
+
+    def check(self, st: int, allow=()):
+        if st != BL_OK and st not in allow:
+            raise BLError(st, lib().bl_last_error(self.h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().bl_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_timing(self, on: bool):
+        self.check(lib().bl_ctx_set_timing(self.h, 1 if on else 0))
+
+    def timing(self) -> dict:
+        t = bl_timing()
+        self.check(lib().bl_ctx_get_timing(self.h, C.byref(t)))
+        out = {k: {"launches": int(t.launches[i]), "ms": float(t.ms[i]), "bytes": float(t.bytes[i])}
+               for i, k in enumerate(KINDS)}
+        out["kernel_launches"] = int(t.kernel_launches)
+        return out
+
+
+def design_args(X: torch.Tensor, n: int):
+    if X.dim() != 2 or X.dtype not in _DTYPE:
+        raise BLError(BL_ERR_ARG, "X must be a 2-D (p, ldx) float64/float32/int8 tensor")
+    if X.stride(1) != 1:
+        raise BLError(BL_ERR_ARG, "X rows (design columns) must be contiguous")
+    return [C.c_void_p(X.data_ptr()), _DTYPE[X.dtype], int(n), int(X.shape[0]), int(X.stride(0))]
+
+
+# ------------------------------------------------------------ C ABI wrappers
+def bl_standardize(ctx, X, n, center, scale, xnorm, keep):
+    return ctx.check(lib().bl_standardize(ctx.h, *design_args(X, n), _ptr(center), _ptr(scale), _ptr(xnorm),
+                                          _ptr(keep)))
+
+
+def bl_lambda_max(ctx, X, n, center, scale, keep, y, alpha, yc, xty):
+    lm, js, yb = C.c_double(), C.c_int64(), C.c_double()
+    ctx.check(lib().bl_lambda_max(ctx.h, *design_args(X, n), _ptr(center), _ptr(scale), _ptr(keep), _ptr(y),
+                                  float(alpha), _ptr(yc), _ptr(xty), C.byref(lm), C.byref(js), C.byref(yb)))
+    return lm.value, js.value, yb.value
+
+
+def bl_bedpp_init(ctx, X, n, center, scale, keep, yc, jstar, xtxstar):
+    yy = C.c_double()
+    ctx.check(lib().bl_bedpp_init(ctx.h, *design_args(X, n), _ptr(center), _ptr(scale), _ptr(keep), _ptr(yc),
+                                  int(jstar), _ptr(xtxstar), C.byref(yy)))
+    return yy.value
+
+
+def bl_screen(ctx, n, p, xty, xtxstar, keep, lambda_max, jstar, ynorm2, lam, lam_prev, alpha, z_prev,
+              beta_prev, safe, strong):
+    ns, ng = C.c_int64(), C.c_int64()
+    ctx.check(lib().bl_screen(ctx.h, int(n), int(p), _ptr(xty), _ptr(xtxstar), _ptr(keep), float(lambda_max),
+                              int(jstar), float(ynorm2), float(lam), float(lam_prev), float(alpha), _ptr(z_prev),
+                              _ptr(beta_prev), _ptr(safe), _ptr(strong), C.byref(ns), C.byref(ng)))
+    return ns.value, ng.value
+
+
+def bl_kkt_check(ctx, X, n, center, scale, xnorm, keep, r, lam, alpha, scan, safe, working, z):
+    nv = C.c_int64()
+    ctx.check(lib().bl_kkt_check(ctx.h, *design_args(X, n), _ptr(center), _ptr(scale), _ptr(xnorm), _ptr(keep),
+                                 _ptr(r), float(lam), float(alpha), _ptr(scan), _ptr(safe), _ptr(working), _ptr(z),
+                                 C.byref(nv)))
+    return nv.value
+
+
+def bl_cd_active(ctx, X, n, center, scale, work_idx, lam, alpha, beta, r, eps, max_sweeps=100_000):
+    sw = C.c_int64()
+    st = lib().bl_cd_active(ctx.h, *design_args(X, n), _ptr(center), _ptr(scale), _ptr(work_idx),
+                            int(work_idx.numel()), float(lam), float(alpha), _ptr(beta), _ptr(r), float(eps),
+                            int(max_sweeps), C.byref(sw))
+    ctx.check(st, allow=(BL_ERR_NOT_CONVERGED,))
+    return sw.value, st
+
+
+def bl_fit_path(ctx, X, n, y, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, lambdas=None,
+                screen=BL_SCREEN_SSR_BEDPP, max_sweeps=100_000, nnz_capacity=None):
+    """The whole path on the GPU.  X (p, ldx) and y (n, float64) on the ctx's
+    device.  Returns a dict of device tensors (lambdas, col_ptr, row_idx, val,
+    val_orig, intercept, loss) and host tensors (per-lambda counters)."""
+    dev = X.device
+    p = int(X.shape[0])
+    K = int(nlambda if lambdas is None else len(lambdas))
+    if nnz_capacity is None:
+        nnz_capacity = K * min(p, int(n) + 64)
+    o = torch.zeros
+    res = {
+        "lambdas": o(K, dtype=torch.float64, device=dev),
+        "col_ptr": o(K + 1, dtype=torch.int64, device=dev),
+        "row_idx": o(max(1, nnz_capacity), dtype=torch.int32, device=dev),
+        "val": o(max(1, nnz_capacity), dtype=torch.float64, device=dev),
+        "val_orig": o(max(1, nnz_capacity), dtype=torch.float64, device=dev),
+        "intercept": o(K, dtype=torch.float64, device=dev),
+        "loss": o(K, dtype=torch.float64, device=dev),
+    }
+    host = {k: o(K, dtype=torch.int64) for k in ("sweeps", "n_safe", "n_strong", "kkt_rounds", "cols_scanned",
+                                                   "n_active")}
+    path = bl_path()
+    for k in ("lambdas", "col_ptr", "row_idx", "val", "val_orig", "intercept", "loss"):
+        setattr(path, k, res[k].data_ptr())
+    for k, t in host.items():
+        setattr(path, k, t.data_ptr())
+    path.nnz_capacity = nnz_capacity
+    opt = bl_options(float(alpha), float(eps), float(ratio), int(max_sweeps), int(screen), 0)
+    lam_arr = None
+    if lambdas is not None:
+        lam_arr = (C.c_double * K)(*[float(v) for v in lambdas])
+    st = lib().bl_fit_path(ctx.h, *design_args(X, n), _ptr(y), C.byref(opt), lam_arr, K, C.byref(path))
+    ctx.check(st, allow=(BL_ERR_NOT_CONVERGED,))
+    res.update(host)
+    res.update(status=st, nnz=path.nnz_needed, lambda_max=path.lambda_max, jstar=path.jstar, ybar=path.ybar)
+    return res
+
+
+def path_dense(res: dict, p: int, key: str = "val") -> torch.Tensor:
+    """Expand the CSC path into a dense (K, p) FP64 tensor (output conversion)."""
+    cp = res["col_ptr"].cpu()
+    K = cp.numel() - 1
+    nnz = int(cp[-1])
+    out = torch.zeros(K, p, dtype=torch.float64, device=res["val"].device)
+    if nnz:
+        counts = (cp[1:] - cp[:-1]).to(res["val"].device)
+        rows = torch.repeat_interleave(torch.arange(K, device=out.device), counts)
+        out[rows, res["row_idx"][:nnz].long()] = res[key][:nnz]
+    return out
+
+
+def fit_path(X: torch.Tensor, n: int, y: torch.Tensor, device: int = 0, ctx: Optional[Context] = None, **kw):
+    """Public entry: accepts host or device tensors.  Host inputs are copied to
+    the device (pinned, non-blocking) before the C call and the result's small
+    vectors are read back; the returned dict then holds host tensors."""
+    own = ctx is None
+    ctx = ctx or Context(device)
+    try:
+        on_host = not X.is_cuda
+        Xd = X.to(f"cuda:{device}", non_blocking=True) if on_host else X
+        yd = y.to(f"cuda:{device}", dtype=torch.float64, non_blocking=True) if not y.is_cuda else y
+        res = bl_fit_path(ctx, Xd, n, yd, **kw)
+        if on_host:
+            nnz = res["nnz"]
+            for k in ("lambdas", "col_ptr", "intercept", "loss"):
+                res[k] = res[k].cpu()
+            for k in ("row_idx", "val", "val_orig"):
+                res[k] = res[k][:nnz].cpu()
+        return res
+    finally:
+        if own:
+            ctx.close()
+
+
+def version() -> str:
+    return lib().bl_version().decode()

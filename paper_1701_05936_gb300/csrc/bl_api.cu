@@ -1,0 +1,706 @@
+// bl_api.cu -- the C ABI of libbl (declared in include/biglasso_gpu.h):
+// context and workspace management, argument checking, per-kernel event
+// timing, and the host orchestration of the solution path.
+#include "biglasso_gpu.h"
+#include "bl_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace bl;
+
+namespace {
+
+struct TimedLaunch {
+    cudaEvent_t a, b;
+    int kind;
+    double bytes;
+};
+
+struct Workspace {
+    void *base = nullptr;
+    size_t size = 0;
+    int64_t n = 0, p = 0;
+    double *center, *scale, *inv_scale, *xnorm, *xty, *xtxstar;
+    float *c32, *is32, *z;
+    void *beta;
+    uint8_t *keep, *safe, *working, *scan;
+    int32_t *idx;
+    double *yc, *xcs, *partial, *part_val;
+    long long *part_idx;
+    void *r;
+    DevScalars *sc;
+};
+
+}  // namespace
+
+struct bl_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    std::string err;
+    Workspace ws;
+    DevScalars *sc_host = nullptr;  // pinned mirror
+    bool timing = false;
+    std::vector<TimedLaunch> launches;
+    std::vector<cudaEvent_t> pool;
+    bl_timing totals{};
+    int64_t kernels = 0;
+};
+
+namespace {
+
+int fail(bl_ctx *ctx, int code, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int cuda_fail(bl_ctx *ctx, cudaError_t e, const char *what)
+{
+    if (ctx) ctx->err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? BL_ERR_OOM : BL_ERR_CUDA;
+}
+
+#define CK(call)                                                 \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+// Launch through a bl::launch_* helper that starts `nk` kernels.
+#define LAUNCH(nk, call)        \
+    do {                        \
+        CK(call);               \
+        ctx->kernels += (nk);   \
+    } while (0)
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+int ensure_ws(bl_ctx *ctx, int64_t n, int64_t p)
+{
+    Workspace &w = ctx->ws;
+    if (w.base && n <= w.n && p <= w.p) return BL_OK;
+    const int64_t N = (n > w.n) ? n : w.n;
+    const int64_t P = (p > w.p) ? p : w.p;
+    const size_t p8 = align256((size_t)P * 8), p4 = align256((size_t)P * 4), p1 = align256((size_t)P + 16);
+    const size_t n8 = align256((size_t)N * 8);
+    const size_t idxb = align256((size_t)MAX_WORKING * 4);
+    const size_t total = 6 * p8 + 3 * p4 + p8 + 4 * p1 + idxb + 3 * n8 + (size_t)RESID_GROUPS * n8 +
+                         2 * align256(1024 * 8) + align256(sizeof(DevScalars));
+    if (w.base) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(w.base);
+        w.base = nullptr;
+        w.size = 0;
+    }
+    void *base = nullptr;
+    cudaError_t e = cudaMalloc(&base, total);
+    if (e != cudaSuccess) {
+        w.n = w.p = 0;
+        return cuda_fail(ctx, e, "workspace cudaMalloc");
+    }
+    char *q = (char *)base;
+    auto take = [&](size_t bytes) {
+        char *r = q;
+        q += bytes;
+        return (void *)r;
+    };
+    w.center = (double *)take(p8);
+    w.scale = (double *)take(p8);
+    w.inv_scale = (double *)take(p8);
+    w.xnorm = (double *)take(p8);
+    w.xty = (double *)take(p8);
+    w.xtxstar = (double *)take(p8);
+    w.c32 = (float *)take(p4);
+    w.is32 = (float *)take(p4);
+    w.z = (float *)take(p4);
+    w.beta = take(p8);
+    w.keep = (uint8_t *)take(p1);
+    w.safe = (uint8_t *)take(p1);
+    w.working = (uint8_t *)take(p1);
+    w.scan = (uint8_t *)take(p1);
+    w.idx = (int32_t *)take(idxb);
+    w.yc = (double *)take(n8);
+    w.r = take(n8);
+    w.xcs = (double *)take(n8);
+    w.partial = (double *)take((size_t)RESID_GROUPS * n8);
+    w.part_val = (double *)take(align256(1024 * 8));
+    w.part_idx = (long long *)take(align256(1024 * 8));
+    w.sc = (DevScalars *)take(align256(sizeof(DevScalars)));
+    w.base = base;
+    w.size = total;
+    w.n = N;
+    w.p = P;
+    return BL_OK;
+}
+
+int check_design(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx)
+{
+    if (!ctx) return BL_ERR_ARG;
+    if (dtype == BL_BF16) return fail(ctx, BL_ERR_UNSUPPORTED, "BF16 designs are not supported by this build");
+    if (dtype != BL_F64 && dtype != BL_F32 && dtype != BL_I8) return fail(ctx, BL_ERR_ARG, "unknown dtype");
+    if (!X) return fail(ctx, BL_ERR_ARG, "X is NULL");
+    if (n < 1 || p < 1) return fail(ctx, BL_ERR_ARG, "n and p must be >= 1");
+    if (ldx < n) return fail(ctx, BL_ERR_ARG, "ldx must be >= n");
+    const size_t es = elem_size(dtype);
+    if (((size_t)ldx * es) % 16 != 0) return fail(ctx, BL_ERR_ARG, "ldx * element size must be a multiple of 16 bytes");
+    if (((uintptr_t)X) % 16 != 0) return fail(ctx, BL_ERR_ARG, "X must be 16-byte aligned");
+    if (p > 2147483647LL) return fail(ctx, BL_ERR_UNSUPPORTED, "p must fit in int32");
+    return BL_OK;
+}
+
+int64_t max_n_for(int dtype) { return dtype == BL_F64 ? MAX_N_F64 : MAX_N_F32; }
+int64_t max_w_for(int dtype) { return dtype == BL_F64 ? MAX_WORKING_F64 : MAX_WORKING; }
+
+cudaEvent_t get_event(bl_ctx *ctx)
+{
+    if (!ctx->pool.empty()) {
+        cudaEvent_t e = ctx->pool.back();
+        ctx->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Begin a timed launch; returns its slot (or -1 when timing is off).
+int tbegin(bl_ctx *ctx, int kind)
+{
+    if (!ctx->timing) return -1;
+    TimedLaunch t{get_event(ctx), get_event(ctx), kind, 0.0};
+    cudaEventRecord(t.a, ctx->stream);
+    ctx->launches.push_back(t);
+    return (int)ctx->launches.size() - 1;
+}
+
+void tend(bl_ctx *ctx, int slot, double bytes)
+{
+    if (slot < 0) return;
+    ctx->launches[slot].bytes = bytes;
+    cudaEventRecord(ctx->launches[slot].b, ctx->stream);
+}
+
+// Fold finished launches into the totals (the stream must be idle).
+void fold_timing(bl_ctx *ctx)
+{
+    for (auto &t : ctx->launches) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+            ctx->totals.launches[t.kind] += 1;
+            ctx->totals.ms[t.kind] += ms;
+            ctx->totals.bytes[t.kind] += t.bytes;
+        }
+        ctx->pool.push_back(t.a);
+        ctx->pool.push_back(t.b);
+    }
+    ctx->launches.clear();
+}
+
+int sync_sc(bl_ctx *ctx)
+{
+    CK(cudaMemcpyAsync(ctx->sc_host, ctx->ws.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return BL_OK;
+}
+
+int reset_counters(bl_ctx *ctx)
+{
+    const size_t off = offsetof(DevScalars, n_viol);
+    const size_t len = offsetof(DevScalars, nnz_total) - off;
+    CK(cudaMemsetAsync((char *)ctx->ws.sc + off, 0, len, ctx->stream));
+    return BL_OK;
+}
+
+int reset_round(bl_ctx *ctx)
+{
+    const size_t off = offsetof(DevScalars, n_viol);
+    CK(cudaMemsetAsync((char *)ctx->ws.sc + off, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    return BL_OK;
+}
+
+double gamma_for(int dtype, int64_t n)
+{
+    const double u = (dtype == BL_F64) ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
+    const double m = (double)zpass_depth(dtype, n);
+    return m * u / (1.0 - m * u);
+}
+
+}  // namespace
+
+// =================================================================== context
+extern "C" int bl_ctx_create(bl_ctx **out, int device, void *stream)
+{
+    if (!out) return BL_ERR_ARG;
+    *out = nullptr;
+    bl_ctx *ctx = new (std::nothrow) bl_ctx();
+    if (!ctx) return BL_ERR_OOM;
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->sc_host, sizeof(DevScalars));
+    if (e != cudaSuccess) {
+        delete ctx;
+        return BL_ERR_CUDA;
+    }
+    *out = ctx;
+    return BL_OK;
+}
+
+extern "C" int bl_ctx_destroy(bl_ctx *ctx)
+{
+    if (!ctx) return BL_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &t : ctx->launches) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    for (auto e : ctx->pool) cudaEventDestroy(e);
+    if (ctx->ws.base) cudaFree(ctx->ws.base);
+    if (ctx->sc_host) cudaFreeHost(ctx->sc_host);
+    delete ctx;
+    return BL_OK;
+}
+
+extern "C" int bl_ctx_set_stream(bl_ctx *ctx, void *stream)
+{
+    if (!ctx) return BL_ERR_ARG;
+    ctx->stream = (cudaStream_t)stream;
+    return BL_OK;
+}
+
+extern "C" const char *bl_last_error(const bl_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" int bl_ctx_set_timing(bl_ctx *ctx, int enable)
+{
+    if (!ctx) return BL_ERR_ARG;
+    cudaStreamSynchronize(ctx->stream);
+    fold_timing(ctx);
+    ctx->timing = enable != 0;
+    ctx->totals = bl_timing{};
+    ctx->kernels = 0;
+    return BL_OK;
+}
+
+extern "C" int bl_ctx_get_timing(bl_ctx *ctx, bl_timing *out)
+{
+    if (!ctx || !out) return BL_ERR_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    fold_timing(ctx);
+    *out = ctx->totals;
+    out->kernel_launches = ctx->kernels;
+    return BL_OK;
+}
+
+extern "C" const char *bl_version(void) { return "1.0.0 sm_103a"; }
+
+// ===================================================== one-time passes (ABI)
+extern "C" int bl_standardize(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx,
+                              double *center, double *scale, double *xnorm, uint8_t *keep)
+{
+    int st = check_design(ctx, X, dtype, n, p, ldx);
+    if (st) return st;
+    if (!center || !scale || !keep) return fail(ctx, BL_ERR_ARG, "center/scale/keep must not be NULL");
+    ctx->err.clear();
+    CK(cudaSetDevice(ctx->device));
+    if ((st = ensure_ws(ctx, n, p))) return st;
+    Workspace &w = ctx->ws;
+    int slot = tbegin(ctx, 0);
+    LAUNCH(1, launch_standardize(dtype, X, n, p, ldx, true, false, nullptr, w.sc, center, scale, w.inv_scale, w.c32,
+                          w.is32, xnorm, keep, nullptr, ctx->num_sms, ctx->stream));
+    tend(ctx, slot, (double)n * p * elem_size(dtype));
+    return BL_OK;
+}
+
+extern "C" int bl_lambda_max(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx,
+                             const double *center, const double *scale, const uint8_t *keep, const double *y,
+                             double alpha, double *yc, double *xty, double *lambda_max, int64_t *jstar,
+                             double *ybar)
+{
+    int st = check_design(ctx, X, dtype, n, p, ldx);
+    if (st) return st;
+    if (!center || !scale || !keep || !y || !yc || !xty || !lambda_max || !jstar)
+        return fail(ctx, BL_ERR_ARG, "NULL argument");
+    if (!(alpha > 0.0 && alpha <= 1.0)) return fail(ctx, BL_ERR_ARG, "alpha must be in (0, 1]");
+    ctx->err.clear();
+    CK(cudaSetDevice(ctx->device));
+    if ((st = ensure_ws(ctx, n, p))) return st;
+    Workspace &w = ctx->ws;
+    int slot = tbegin(ctx, 1);
+    LAUNCH(1, launch_center_y(y, n, yc, w.sc, ctx->stream));
+    LAUNCH(1, launch_standardize(dtype, X, n, p, ldx, false, true, yc, w.sc, (double *)center, (double *)scale, nullptr,
+                          nullptr, nullptr, nullptr, (uint8_t *)keep, xty, ctx->num_sms, ctx->stream));
+    LAUNCH(2, launch_absmax(xty, keep, p, w.part_val, w.part_idx, w.sc, ctx->stream));
+    tend(ctx, slot, (double)n * p * elem_size(dtype));
+    if ((st = sync_sc(ctx))) return st;
+    const DevScalars &h = *ctx->sc_host;
+    *jstar = h.jstar;
+    *lambda_max = (h.jstar < 0) ? 0.0 : h.absmax / ((double)n * alpha);
+    if (ybar) *ybar = h.ybar;
+    return BL_OK;
+}
+
+extern "C" int bl_bedpp_init(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx,
+                             const double *center, const double *scale, const uint8_t *keep, const double *yc,
+                             int64_t jstar, double *xtxstar, double *ynorm2)
+{
+    int st = check_design(ctx, X, dtype, n, p, ldx);
+    if (st) return st;
+    if (!center || !scale || !keep || !yc || !xtxstar || !ynorm2) return fail(ctx, BL_ERR_ARG, "NULL argument");
+    if (jstar < 0 || jstar >= p) return fail(ctx, BL_ERR_ARG, "jstar out of range");
+    ctx->err.clear();
+    CK(cudaSetDevice(ctx->device));
+    if ((st = ensure_ws(ctx, n, p))) return st;
+    Workspace &w = ctx->ws;
+    int slot = tbegin(ctx, 2);
+    LAUNCH(1, launch_rstats(BL_F64, yc, n, w.sc, ctx->stream));
+    LAUNCH(2, launch_xtxstar(dtype, X, n, p, ldx, center, scale, keep, jstar, w.xcs, w.sc, xtxstar, ctx->num_sms,
+                      ctx->stream));
+    tend(ctx, slot, (double)n * p * elem_size(dtype));
+    if ((st = sync_sc(ctx))) return st;
+    *ynorm2 = ctx->sc_host->rss;
+    return BL_OK;
+}
+
+// ======================================================== per lambda (ABI)
+extern "C" int bl_screen(bl_ctx *ctx, int64_t n, int64_t p, const double *xty, const double *xtxstar,
+                         const uint8_t *keep, double lambda_max, int64_t jstar, double ynorm2, double lam,
+                         double lam_prev, double alpha, const float *z_prev, const float *beta_prev,
+                         uint8_t *safe, uint8_t *strong, int64_t *n_safe, int64_t *n_strong)
+{
+    if (!ctx) return BL_ERR_ARG;
+    if (n < 1 || p < 1 || !xty || !keep || !z_prev || !safe || !strong) return fail(ctx, BL_ERR_ARG, "NULL argument or bad size");
+    if (!(lam > 0.0) || !(lam < lam_prev)) return fail(ctx, BL_ERR_ARG, "need 0 < lam < lam_prev");
+    if (!(alpha > 0.0 && alpha <= 1.0)) return fail(ctx, BL_ERR_ARG, "alpha must be in (0, 1]");
+    const bool bedpp = alpha >= 1.0 && jstar >= 0;
+    if (bedpp && (!xtxstar || jstar >= p)) return fail(ctx, BL_ERR_ARG, "xtxstar/jstar required for BEDPP");
+    ctx->err.clear();
+    CK(cudaSetDevice(ctx->device));
+    int st;
+    if ((st = ensure_ws(ctx, n, p))) return st;
+    Workspace &w = ctx->ws;
+    double sstar = 1.0;
+    if (bedpp) {
+        double xs = 0.0;
+        CK(cudaMemcpyAsync(&xs, xty + jstar, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        sstar = xs >= 0.0 ? 1.0 : -1.0;
+    }
+    double rad = (double)n * ynorm2 - (double)n * (double)n * lambda_max * lambda_max;
+    ScreenArgs a{};
+    a.n = n;
+    a.p = p;
+    a.xty = xty;
+    a.xtxstar = xtxstar;
+    a.keep = keep;
+    a.lmax = lambda_max;
+    a.sstar = sstar;
+    a.radius = rad > 0.0 ? std::sqrt(rad) : 0.0;
+    a.jstar = jstar;
+    a.lam = lam;
+    a.lam_prev = lam_prev;
+    a.lam_next = -1.0;
+    a.alpha = alpha;
+    a.rule = BL_SCREEN_SSR_BEDPP;
+    a.z_prev = z_prev;
+    a.beta_prev = beta_prev;
+    a.beta_f64 = 0;
+    a.safe = safe;
+    a.strong = strong;
+    a.scan = nullptr;
+    if ((st = reset_counters(ctx))) return st;
+    int slot = tbegin(ctx, 3);
+    LAUNCH(1, launch_screen(a, w.sc, ctx->stream));
+    tend(ctx, slot, (double)p * (8 + 8 + 1 + 4 + 4 + 3));
+    if (n_safe || n_strong) {
+        if ((st = sync_sc(ctx))) return st;
+        if (n_safe) *n_safe = (int64_t)ctx->sc_host->n_safe;
+        if (n_strong) *n_strong = (int64_t)ctx->sc_host->n_strong;
+    }
+    return BL_OK;
+}
+
+extern "C" int bl_kkt_check(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx,
+                            const double *center, const double *scale, const double *xnorm, const uint8_t *keep,
+                            const void *r, double lam, double alpha, const uint8_t *scan, const uint8_t *safe,
+                            uint8_t *working, float *z, int64_t *n_viol)
+{
+    int st = check_design(ctx, X, dtype, n, p, ldx);
+    if (st) return st;
+    if (!center || !scale || !xnorm || !keep || !r || !scan || !working || !z)
+        return fail(ctx, BL_ERR_ARG, "NULL argument");
+    if (!(lam > 0.0) || !(alpha > 0.0 && alpha <= 1.0)) return fail(ctx, BL_ERR_ARG, "bad lam or alpha");
+    ctx->err.clear();
+    CK(cudaSetDevice(ctx->device));
+    if ((st = ensure_ws(ctx, n, p))) return st;
+    Workspace &w = ctx->ws;
+    LAUNCH(1, launch_rstats(dtype == BL_F64 ? BL_F64 : BL_F32, r, n, w.sc, ctx->stream));
+    if ((st = reset_round(ctx))) return st;
+    ZpassArgs za{X, n, p, ldx, center, scale, xnorm, r, lam, alpha, gamma_for(dtype, n),
+                 scan, safe ? safe : scan, working, z};
+    (void)keep;
+    int slot = tbegin(ctx, 7);
+    LAUNCH(1, launch_zpass(dtype, za, w.sc, zpass_grid(dtype, n, ctx->num_sms), ctx->stream));
+    tend(ctx, slot, 0.0);
+    if (n_viol || slot >= 0) {
+        if ((st = sync_sc(ctx))) return st;
+        if (n_viol) *n_viol = (int64_t)ctx->sc_host->n_viol;
+        if (slot >= 0) ctx->launches[slot].bytes = (double)ctx->sc_host->n_cols * n * elem_size(dtype);
+    }
+    return BL_OK;
+}
+
+extern "C" int bl_cd_active(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx,
+                            const double *center, const double *scale, const int32_t *work_idx, int64_t n_work,
+                            double lam, double alpha, void *beta, void *r, double eps, int64_t max_sweeps,
+                            int64_t *sweeps)
+{
+    int st = check_design(ctx, X, dtype, n, p, ldx);
+    if (st) return st;
+    if (!center || !scale || !beta || !r || (n_work > 0 && !work_idx) || n_work < 0)
+        return fail(ctx, BL_ERR_ARG, "NULL argument");
+    if (!(lam > 0.0) || !(alpha > 0.0 && alpha <= 1.0) || !(eps > 0.0) || max_sweeps < 1)
+        return fail(ctx, BL_ERR_ARG, "bad lam, alpha, eps or max_sweeps");
+    if (n > max_n_for(dtype)) return fail(ctx, BL_ERR_UNSUPPORTED, "n exceeds the CD kernel's limit");
+    if (n_work > max_w_for(dtype)) return fail(ctx, BL_ERR_UNSUPPORTED, "working set exceeds the CD kernel's limit");
+    ctx->err.clear();
+    CK(cudaSetDevice(ctx->device));
+    if ((st = ensure_ws(ctx, n, p))) return st;
+    Workspace &w = ctx->ws;
+    LAUNCH(1, launch_derive(center, scale, p, w.inv_scale, w.c32, w.is32, ctx->stream));
+    if ((st = reset_counters(ctx))) return st;
+    CK(cudaMemsetAsync(&w.sc->status, 0, sizeof(int), ctx->stream));
+    const void *cvec = (dtype == BL_F64) ? (const void *)center : (const void *)w.c32;
+    const void *isvec = (dtype == BL_F64) ? (const void *)w.inv_scale : (const void *)w.is32;
+    int slot = tbegin(ctx, 5);
+    if (n_work > 0)
+        LAUNCH(1, launch_cd(dtype, X, n, p, ldx, cvec, isvec, work_idx, n_work, lam, alpha, beta, r, eps,
+                            max_sweeps, CD_TIME_LIMIT_NS, w.sc, ctx->stream));
+    tend(ctx, slot, 0.0);
+    if ((st = sync_sc(ctx))) return st;
+    if (sweeps) *sweeps = (int64_t)ctx->sc_host->sweeps;
+    if (ctx->sc_host->status & ST_BAD_INDEX) return fail(ctx, BL_ERR_ARG, "work_idx holds an index outside [0, p)");
+    if (ctx->sc_host->status & ST_WORKING_TOO_BIG) return fail(ctx, BL_ERR_UNSUPPORTED, "working set too large");
+    if (ctx->sc_host->status & ST_TIMEOUT) return fail(ctx, BL_ERR_TIMEOUT, "CD reached its wall-clock limit");
+    if (ctx->sc_host->status & ST_NOT_CONVERGED) return fail(ctx, BL_ERR_NOT_CONVERGED, "sweep cap reached");
+    return BL_OK;
+}
+
+// ================================================================= the path
+extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx,
+                           const double *y, const bl_options *opt, const double *lambdas_in, int K,
+                           bl_path *out)
+{
+    int st = check_design(ctx, X, dtype, n, p, ldx);
+    if (st) return st;
+    if (!y || !opt || !out || K < 1) return fail(ctx, BL_ERR_ARG, "NULL argument or nlambda < 1");
+    const double alpha = opt->alpha, eps = opt->eps;
+    if (!(alpha > 0.0 && alpha <= 1.0)) return fail(ctx, BL_ERR_ARG, "alpha must be in (0, 1]");
+    if (!(eps > 0.0)) return fail(ctx, BL_ERR_ARG, "eps must be > 0");
+    if (opt->max_sweeps < 1) return fail(ctx, BL_ERR_ARG, "max_sweeps must be >= 1");
+    if (opt->screen < 0 || opt->screen > 2) return fail(ctx, BL_ERR_ARG, "unknown screening rule");
+    if (!lambdas_in && K > 1 && !(opt->lambda_min_ratio > 0.0 && opt->lambda_min_ratio < 1.0))
+        return fail(ctx, BL_ERR_ARG, "lambda_min_ratio must be in (0, 1)");
+    if (lambdas_in) {
+        for (int k = 0; k < K; ++k) {
+            if (!(lambdas_in[k] > 0.0)) return fail(ctx, BL_ERR_ARG, "lambdas must be positive");
+            if (k > 0 && !(lambdas_in[k] < lambdas_in[k - 1])) return fail(ctx, BL_ERR_ARG, "lambdas must be strictly decreasing");
+        }
+    }
+    if (!out->lambdas || !out->col_ptr || !out->intercept || !out->loss || out->nnz_capacity < 0 ||
+        (out->nnz_capacity > 0 && (!out->row_idx || !out->val)))
+        return fail(ctx, BL_ERR_ARG, "output arrays missing");
+    if (n > max_n_for(dtype)) return fail(ctx, BL_ERR_UNSUPPORTED, "n exceeds the CD kernel's limit");
+    ctx->err.clear();
+    CK(cudaSetDevice(ctx->device));
+    if ((st = ensure_ws(ctx, n, p))) return st;
+    Workspace &w = ctx->ws;
+    cudaStream_t s = ctx->stream;
+    const size_t es = elem_size(dtype);
+    const int beta_f64 = dtype == BL_F64;
+    const size_t rsz = beta_f64 ? 8 : 4;
+
+    CK(cudaMemsetAsync(w.sc, 0, sizeof(DevScalars), s));
+    CK(cudaMemsetAsync(w.beta, 0, (size_t)p * rsz, s));
+    CK(cudaMemsetAsync(out->col_ptr, 0, sizeof(int64_t), s));
+
+    // one-time passes: y centring, standardization fused with x~'y, lambda_max
+    int slot = tbegin(ctx, 0);
+    LAUNCH(1, launch_center_y(y, n, w.yc, w.sc, s));
+    LAUNCH(1, launch_standardize(dtype, X, n, p, ldx, true, true, w.yc, w.sc, w.center, w.scale, w.inv_scale, w.c32,
+                          w.is32, w.xnorm, w.keep, w.xty, ctx->num_sms, s));
+    tend(ctx, slot, (double)n * p * es);
+    slot = tbegin(ctx, 1);
+    LAUNCH(2, launch_absmax(w.xty, w.keep, p, w.part_val, w.part_idx, w.sc, s));
+    tend(ctx, slot, (double)p * 9);
+    if ((st = sync_sc(ctx))) return st;
+    const int64_t jstar = ctx->sc_host->jstar;
+    const double lmax = (jstar < 0) ? 0.0 : ctx->sc_host->absmax / ((double)n * alpha);
+    const double ynorm2 = ctx->sc_host->ynorm2;
+    out->lambda_max = lmax;
+    out->jstar = jstar;
+    out->ybar = ctx->sc_host->ybar;
+
+    std::vector<double> L(K);
+    const bool generated = (lambdas_in == nullptr);
+    for (int k = 0; k < K; ++k) {
+        if (generated) {
+            const double e = (K > 1) ? (double)k / (double)(K - 1) : 0.0;
+            L[k] = lmax * std::pow(opt->lambda_min_ratio, e);
+        } else {
+            L[k] = lambdas_in[k];
+        }
+    }
+    CK(cudaMemcpyAsync(out->lambdas, L.data(), (size_t)K * sizeof(double), cudaMemcpyHostToDevice, s));
+
+    const bool use_bedpp = opt->screen == BL_SCREEN_SSR_BEDPP && alpha >= 1.0 && jstar >= 0 && lmax > 0.0;
+    double sstar = 1.0, radius = 0.0;
+    if (use_bedpp) {
+        slot = tbegin(ctx, 2);
+        LAUNCH(2, launch_xtxstar(dtype, X, n, p, ldx, w.center, w.scale, w.keep, jstar, w.xcs, w.sc, w.xtxstar,
+                          ctx->num_sms, s));
+        tend(ctx, slot, (double)n * p * es);
+        double xs = 0.0;
+        CK(cudaMemcpyAsync(&xs, w.xty + jstar, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        sstar = xs >= 0.0 ? 1.0 : -1.0;
+        const double rad = (double)n * ynorm2 - (double)n * (double)n * lmax * lmax;
+        radius = rad > 0.0 ? std::sqrt(rad) : 0.0;
+    }
+    // state at lambda_max: b = 0, r = yc, z = xt'yc/n
+    LAUNCH(1, launch_init_z(w.xty, w.keep, p, n, w.z, s));
+    slot = tbegin(ctx, 6);
+    LAUNCH(1, launch_residual(dtype, X, n, ldx, w.center, w.inv_scale, w.idx, 0, w.sc, w.beta, w.yc, w.partial,
+                              w.r, w.sc, s));
+    tend(ctx, slot, (double)n * 16);
+
+    const void *cvec = beta_f64 ? (const void *)w.center : (const void *)w.c32;
+    const void *isvec = beta_f64 ? (const void *)w.inv_scale : (const void *)w.is32;
+    const double gamma = gamma_for(dtype, n);
+    const int zgrid = zpass_grid(dtype, n, ctx->num_sms);
+    const int64_t wcap = max_w_for(dtype);
+    bool not_converged = false;
+
+    RecordArgs ra{};
+    ra.idx = w.idx;
+    ra.beta = w.beta;
+    ra.beta_f64 = beta_f64;
+    ra.center = w.center;
+    ra.scale = w.scale;
+    ra.alpha = alpha;
+    ra.n = n;
+    ra.col_ptr = out->col_ptr;
+    ra.row_idx = out->row_idx;
+    ra.val = out->val;
+    ra.val_orig = out->val_orig;
+    ra.cap = out->nnz_capacity;
+    ra.intercept = out->intercept;
+    ra.loss = out->loss;
+
+    for (int k = 0; k < K; ++k) {
+        const double lam = L[k];
+        ra.k = k;
+        ra.lam = lam;
+        if (lmax <= 0.0 || lam >= lmax || (generated && k == 0)) {
+            ra.w_host = 0;
+            slot = tbegin(ctx, 8);
+            LAUNCH(1, launch_record(ra, w.sc, s));
+            tend(ctx, slot, 0.0);
+            if (out->sweeps) out->sweeps[k] = 0;
+            if (out->n_safe) out->n_safe[k] = 0;
+            if (out->n_strong) out->n_strong[k] = 0;
+            if (out->kkt_rounds) out->kkt_rounds[k] = 0;
+            if (out->cols_scanned) out->cols_scanned[k] = 0;
+            continue;
+        }
+        const double lam_prev = (k == 0) ? lmax : std::fmin(L[k - 1], lmax);
+        const double lam_next = (k + 1 < K) ? L[k + 1] : -1.0;
+        if ((st = reset_counters(ctx))) return st;
+        ScreenArgs sa{};
+        sa.n = n;
+        sa.p = p;
+        sa.xty = w.xty;
+        sa.xtxstar = w.xtxstar;
+        sa.keep = w.keep;
+        sa.lmax = lmax;
+        sa.sstar = sstar;
+        sa.radius = radius;
+        sa.jstar = jstar;
+        sa.lam = lam;
+        sa.lam_prev = lam_prev;
+        sa.lam_next = lam_next;
+        sa.alpha = alpha;
+        sa.rule = use_bedpp ? BL_SCREEN_SSR_BEDPP : (opt->screen == BL_SCREEN_NONE ? BL_SCREEN_NONE : BL_SCREEN_SSR);
+        sa.z_prev = w.z;
+        sa.beta_prev = w.beta;
+        sa.beta_f64 = beta_f64;
+        sa.safe = w.safe;
+        sa.strong = w.working;
+        sa.scan = w.scan;
+        slot = tbegin(ctx, 3);
+        LAUNCH(1, launch_screen(sa, w.sc, s));
+        tend(ctx, slot, (double)p * 40);
+        int64_t rounds = 0, cols = 0;
+        for (;;) {
+            slot = tbegin(ctx, 4);
+            LAUNCH(1, launch_compact(w.working, p, w.idx, wcap, w.sc, s));
+            tend(ctx, slot, (double)p);
+            slot = tbegin(ctx, 5);
+            LAUNCH(1, launch_cd(dtype, X, n, p, ldx, cvec, isvec, w.idx, -1, lam, alpha, w.beta, w.r, eps,
+                                opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc, s));
+            tend(ctx, slot, 0.0);
+            slot = tbegin(ctx, 6);
+            LAUNCH(2, launch_residual(dtype, X, n, ldx, w.center, w.inv_scale, w.idx, -1, w.sc, w.beta, w.yc,
+                                      w.partial, w.r, w.sc, s));
+            tend(ctx, slot, 0.0);
+            if ((st = reset_round(ctx))) return st;
+            ZpassArgs za{X, n, p, ldx, w.center, w.scale, w.xnorm, w.r, lam, alpha, gamma,
+                         w.scan, w.safe, w.working, w.z};
+            int zslot = tbegin(ctx, 7);
+            LAUNCH(1, launch_zpass(dtype, za, w.sc, zgrid, s));
+            tend(ctx, zslot, 0.0);
+            if ((st = sync_sc(ctx))) return st;
+            const DevScalars &h = *ctx->sc_host;
+            if (zslot >= 0) ctx->launches[zslot].bytes = (double)h.n_cols * n * es;
+            ++rounds;
+            cols += (int64_t)h.n_cols;
+            if (h.status & ST_WORKING_TOO_BIG)
+                return fail(ctx, BL_ERR_UNSUPPORTED, "working set exceeds the CD kernel's limit");
+            if (h.status & ST_TIMEOUT) return fail(ctx, BL_ERR_TIMEOUT, "CD reached its wall-clock limit");
+            if (h.status & ST_NOT_CONVERGED) not_converged = true;
+            if (h.n_viol == 0) break;
+            if (rounds > 100000) return fail(ctx, BL_ERR_NOT_CONVERGED, "KKT loop did not settle");
+        }
+        ra.w_host = -1;
+        slot = tbegin(ctx, 8);
+        LAUNCH(1, launch_record(ra, w.sc, s));
+        tend(ctx, slot, 0.0);
+        const DevScalars &h = *ctx->sc_host;
+        if (out->sweeps) out->sweeps[k] = (int64_t)h.sweeps;
+        if (out->n_safe) out->n_safe[k] = (int64_t)h.n_safe;
+        if (out->n_strong) out->n_strong[k] = (int64_t)h.n_strong;
+        if (out->kkt_rounds) out->kkt_rounds[k] = rounds;
+        if (out->cols_scanned) out->cols_scanned[k] = cols;
+    }
+    std::vector<int64_t> cp((size_t)K + 1);
+    CK(cudaMemcpyAsync(cp.data(), out->col_ptr, ((size_t)K + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if ((st = sync_sc(ctx))) return st;
+    out->nnz_needed = cp[K];
+    if (out->n_active)
+        for (int k = 0; k < K; ++k) out->n_active[k] = cp[k + 1] - cp[k];
+    if (ctx->sc_host->status & ST_CAPACITY || out->nnz_needed > out->nnz_capacity)
+        return fail(ctx, BL_ERR_CAPACITY, "nnz_capacity smaller than the path's nonzeros");
+    if (not_converged) return fail(ctx, BL_ERR_NOT_CONVERGED, "CD reached max_sweeps at some lambda");
+    return BL_OK;
+}

@@ -1,0 +1,106 @@
+// bl_device.cuh -- device-side building blocks shared by the kernels of libbl:
+// element traits for the stored design types, 16-byte vector loads, and warp
+// reductions.  Internal to the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bl {
+
+// Element traits.  VEC is the number of stored elements in one 16-byte load;
+// acc is the arithmetic type of the data-parallel passes (FP32 for FP32 and
+// int8 designs, FP64 for FP64 designs); res is the type of the residual and
+// the dense coefficient vector on the device.
+template <typename T> struct elem;
+template <> struct elem<float> {
+    using acc = float;
+    using res = float;
+    using vec = float4;
+    static constexpr int VEC = 4;
+};
+template <> struct elem<double> {
+    using acc = double;
+    using res = double;
+    using vec = double2;
+    static constexpr int VEC = 2;
+};
+template <> struct elem<int8_t> {
+    using acc = float;
+    using res = float;
+    using vec = int4;
+    static constexpr int VEC = 16;
+};
+
+// Unpack one 16-byte chunk into VEC values of type A.
+template <typename A> __device__ __forceinline__ void unpack(const float4 &v, A *o)
+{
+    o[0] = (A)v.x; o[1] = (A)v.y; o[2] = (A)v.z; o[3] = (A)v.w;
+}
+template <typename A> __device__ __forceinline__ void unpack(const double2 &v, A *o)
+{
+    o[0] = (A)v.x; o[1] = (A)v.y;
+}
+template <typename A> __device__ __forceinline__ void unpack(const int4 &v, A *o)
+{
+    const int w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) o[4 * k + b] = (A)(int8_t)((w[k] >> (8 * b)) & 0xff);
+    }
+}
+
+// Read-only 16-byte load through the non-coherent path.
+template <typename V> __device__ __forceinline__ V ldg16(const V *p) { return __ldg(p); }
+
+// Streaming 16-byte load for single-use data: does not allocate in L1.
+__device__ __forceinline__ float4 ld_stream(const float4 *p)
+{
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double2 ld_stream(const double2 *p)
+{
+    double2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];"
+                 : "=d"(v.x), "=d"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ int4 ld_stream(const int4 *p)
+{
+    int4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+
+template <typename A> __device__ __forceinline__ A warp_sum(A v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double to_f64(float v) { return (double)v; }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(int8_t v) { return (double)v; }
+
+// Nanosecond wall clock of the GPU.
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Soft-thresholding operator S(z, t) = sign(z) max(|z| - t, 0).
+template <typename A> __device__ __forceinline__ A soft_threshold(A z, A t)
+{
+    A a = fabs(z) - t;
+    return a > (A)0 ? copysign(a, z) : (A)0;
+}
+
+}  // namespace bl

@@ -1,0 +1,142 @@
+// bl_internal.h -- launchers of the libbl kernels and the device-resident
+// scalars they share.  Internal to the library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bl {
+
+// Status bits a kernel can raise in DevScalars::status.
+enum : int {
+    ST_NOT_CONVERGED = 1,  // CD reached its sweep cap
+    ST_WORKING_TOO_BIG = 2,  // working set larger than the CD kernel accepts
+    ST_CAPACITY = 4,       // CSC output capacity exceeded
+    ST_TIMEOUT = 8,        // CD stopped at its wall-clock limit
+    ST_BAD_INDEX = 16      // a working-set index outside [0, p)
+};
+
+// Scalars and counters that stay on the device during a path.  Integer
+// counters are only ever added to (atomically) and reset by the host.
+struct DevScalars {
+    // residual statistics of the rounded residual the z pass reads
+    double sum_r;   // sum_i r_i (FP64 sum of the stored values)
+    double rnorm;   // ||r||_2 of the stored values
+    double rss;     // ||yc - Xt b||^2 of the FP64 residual (objective)
+    // response statistics
+    double ybar, sum_yc, ynorm2;
+    // lambda_max search result
+    double absmax;  // max_j |xty_j| over kept columns
+    double sum_xcs; // sum_i (x_i* - c_*) (BEDPP init)
+    long long jstar;
+    // per-round counters (reset by the host)
+    unsigned long long n_viol, n_cols, n_safe, n_strong, n_scan, w, sweeps;
+    unsigned long long nnz_total;
+    int status;
+    int pad;
+};
+
+constexpr int CD_THREADS = 256;
+constexpr int MAX_WORKING = 8192;   // float/int8 designs
+constexpr int MAX_WORKING_F64 = 6144;
+constexpr int64_t MAX_N_F32 = 16384;
+constexpr int64_t MAX_N_F64 = 8192;
+constexpr int RESID_GROUPS = 64;
+constexpr uint64_t CD_TIME_LIMIT_NS = 20ull * 1000ull * 1000ull * 1000ull;  // 20 s per CD launch
+
+// dtype codes follow bl_dtype: 0 F64, 1 F32, 2 BF16, 3 I8.
+size_t elem_size(int dtype);
+
+cudaError_t launch_center_y(const double *y, int64_t n, double *yc, DevScalars *sc, cudaStream_t st);
+
+// STATS: write center/scale/inv_scale/c32/is32/xnorm/keep.  XTY: write xty
+// (needs yc and sc->sum_yc; without STATS, center/scale/keep are inputs).
+cudaError_t launch_standardize(int dtype, const void *X, int64_t n, int64_t p, int64_t ldx,
+                               bool stats, bool xty_mode, const double *yc, const DevScalars *sc,
+                               double *center, double *scale, double *inv_scale, float *c32,
+                               float *is32, double *xnorm, uint8_t *keep, double *xty,
+                               int num_sms, cudaStream_t st);
+
+// Derived per-feature vectors (1/s, FP32 copies) from given center/scale.
+cudaError_t launch_derive(const double *center, const double *scale, int64_t p, double *inv_scale,
+                          float *c32, float *is32, cudaStream_t st);
+
+cudaError_t launch_absmax(const double *xty, const uint8_t *keep, int64_t p, double *part_val,
+                          long long *part_idx, DevScalars *sc, cudaStream_t st);
+
+cudaError_t launch_xtxstar(int dtype, const void *X, int64_t n, int64_t p, int64_t ldx,
+                           const double *center, const double *scale, const uint8_t *keep,
+                           int64_t jstar, double *xcs, DevScalars *sc, double *xtxstar,
+                           int num_sms, cudaStream_t st);
+
+struct ScreenArgs {
+    int64_t n, p;
+    const double *xty, *xtxstar;
+    const uint8_t *keep;
+    double lmax, sstar, radius;  // radius = sqrt(n ||yc||^2 - n^2 lmax^2)
+    int64_t jstar;
+    double lam, lam_prev, lam_next;  // lam_next < 0: no next lambda
+    double alpha;
+    int rule;          // bl_screen_rule
+    const float *z_prev;
+    const void *beta_prev;  // nullable
+    int beta_f64;
+    uint8_t *safe, *strong, *scan;  // scan nullable
+};
+cudaError_t launch_screen(const ScreenArgs &a, DevScalars *sc, cudaStream_t st);
+
+cudaError_t launch_compact(const uint8_t *mask, int64_t p, int32_t *idx, int64_t cap,
+                           DevScalars *sc, cudaStream_t st);
+
+cudaError_t launch_init_z(const double *xty, const uint8_t *keep, int64_t p, int64_t n, float *z,
+                          cudaStream_t st);
+
+// Coordinate descent over idx[0..w), w = w_host if >= 0 else sc->w.
+cudaError_t launch_cd(int dtype, const void *X, int64_t n, int64_t p, int64_t ldx, const void *cvec,
+                      const void *isvec, const int32_t *idx, int64_t w_host, double lam,
+                      double alpha, void *beta, void *r, double eps, int64_t max_sweeps,
+                      uint64_t time_limit_ns, DevScalars *sc, cudaStream_t st);
+
+// r = yc - Xt b over the working set, in FP64, rounded into r_out; also the
+// residual statistics in sc.  partial: RESID_GROUPS * n doubles of scratch.
+cudaError_t launch_residual(int dtype, const void *X, int64_t n, int64_t ldx, const double *center,
+                            const double *inv_scale, const int32_t *idx, int64_t w_host,
+                            const DevScalars *sc_w, const void *beta, const double *yc,
+                            double *partial, void *r_out, DevScalars *sc, cudaStream_t st);
+
+// Statistics (sum, norm) of a caller-provided residual.
+cudaError_t launch_rstats(int dtype, const void *r, int64_t n, DevScalars *sc, cudaStream_t st);
+
+struct ZpassArgs {
+    const void *X;
+    int64_t n, p, ldx;
+    const double *center, *scale, *xnorm;
+    const void *r;
+    double lam, alpha, gamma;
+    const uint8_t *scan, *safe;
+    uint8_t *working;
+    float *z;
+};
+cudaError_t launch_zpass(int dtype, const ZpassArgs &a, DevScalars *sc, int grid, cudaStream_t st);
+int zpass_grid(int dtype, int64_t n, int num_sms);
+size_t zpass_smem(int dtype, int64_t n);
+int zpass_depth(int dtype, int64_t n);  // accumulation depth for the rounding bound
+
+struct RecordArgs {
+    const int32_t *idx;
+    int64_t w_host;  // < 0: sc->w
+    const void *beta;
+    int beta_f64;
+    const double *center, *scale;
+    int k;
+    double lam, alpha;
+    int64_t n;
+    int64_t *col_ptr;
+    int32_t *row_idx;
+    double *val, *val_orig;
+    int64_t cap;
+    double *intercept, *loss;
+};
+cudaError_t launch_record(const RecordArgs &a, DevScalars *sc, cudaStream_t st);
+
+}  // namespace bl
