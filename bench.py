@@ -283,6 +283,17 @@ def run_ours(args):
                 "launches": z["launches"], "avg_launch_us": 1e3 * z["ms"] / max(1, z["launches"])}
     breakdown = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps}
                  for k, v in tim.items() if isinstance(v, dict)}
+    cd = tim["cd"]
+    cd_info = {"bound": "latency (one CTA, sequential coordinates)",
+               "updates_per_step": tim["cd_updates"] / args.steps,
+               "ns_per_update": 1e6 * cd["ms"] / max(1, tim["cd_updates"])}
+    if rank == 0:
+        K = len(res["sweeps"])
+        for k in range(0, K, 5):
+            sys.stderr.write(f"lam[{k:3d}] sweeps={int(res['sweeps'][k]):6d} strong={int(res['n_strong'][k]):6d} "
+                             f"safe={int(res['n_safe'][k]):6d} active={int(res['n_active'][k]):5d} "
+                             f"kkt={int(res['kkt_rounds'][k])} cols={int(res['cols_scanned'][k])}\n")
+        sys.stderr.write(json.dumps(breakdown) + "\n")
     line = {
         "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
@@ -290,7 +301,7 @@ def run_ours(args):
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": "paths/s", "h2d_bytes_per_step": int(prob.X.nbytes + prob.y.nbytes),
                 "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": int(tim["kernel_launches"]), "clocks": clk,
+        "gpu_launches": int(tim["kernel_launches"]), "clocks": clk, "cd": cd_info,
         "kernel_ms_per_step": breakdown, "status": res["status"],
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -117,6 +117,7 @@ typedef struct {
     int64_t kernel_launches;         /* CUDA kernels launched since the ctx was
                                         created or timing was last enabled
                                         (counted whether or not timing is on) */
+    int64_t cd_updates;              /* coordinate updates run by CD, same span */
 } bl_timing;
 
 /* ---------------------------------------------------------------- context -- */

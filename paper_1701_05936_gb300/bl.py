@@ -55,7 +55,7 @@ class bl_path(C.Structure):
 
 class bl_timing(C.Structure):
     _fields_ = [("launches", C.c_int64 * 9), ("ms", C.c_double * 9), ("bytes", C.c_double * 9),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("cd_updates", C.c_int64)]
 
 
 _lib = None
@@ -155,6 +155,7 @@ class Context:
         out = {k: {"launches": int(t.launches[i]), "ms": float(t.ms[i]), "bytes": float(t.bytes[i])}
                for i, k in enumerate(KINDS)}
         out["kernel_launches"] = int(t.kernel_launches)
+        out["cd_updates"] = int(t.cd_updates)
         return out
 
 

@@ -53,6 +53,7 @@ struct bl_ctx {
     std::vector<cudaEvent_t> pool;
     bl_timing totals{};
     int64_t kernels = 0;
+    int64_t cd_updates = 0;
 };
 
 namespace {
@@ -289,6 +290,7 @@ extern "C" int bl_ctx_set_timing(bl_ctx *ctx, int enable)
     ctx->timing = enable != 0;
     ctx->totals = bl_timing{};
     ctx->kernels = 0;
+    ctx->cd_updates = 0;
     return BL_OK;
 }
 
@@ -300,6 +302,7 @@ extern "C" int bl_ctx_get_timing(bl_ctx *ctx, bl_timing *out)
     fold_timing(ctx);
     *out = ctx->totals;
     out->kernel_launches = ctx->kernels;
+    out->cd_updates = ctx->cd_updates;
     return BL_OK;
 }
 
@@ -447,7 +450,9 @@ extern "C" int bl_kkt_check(bl_ctx *ctx, const void *X, int dtype, int64_t n, in
     Workspace &w = ctx->ws;
     LAUNCH(1, launch_rstats(dtype == BL_F64 ? BL_F64 : BL_F32, r, n, w.sc, ctx->stream));
     if ((st = reset_round(ctx))) return st;
-    ZpassArgs za{X, n, p, ldx, center, scale, xnorm, r, lam, alpha, gamma_for(dtype, n),
+    CK(launch_derive(center, scale, p, w.inv_scale, w.c32, w.is32, ctx->stream));
+    ctx->kernels += 1;
+    ZpassArgs za{X, n, p, ldx, center, w.inv_scale, xnorm, r, lam, alpha, gamma_for(dtype, n),
                  scan, safe ? safe : scan, working, z};
     (void)keep;
     int slot = tbegin(ctx, 7);
@@ -481,6 +486,7 @@ extern "C" int bl_cd_active(bl_ctx *ctx, const void *X, int dtype, int64_t n, in
     LAUNCH(1, launch_derive(center, scale, p, w.inv_scale, w.c32, w.is32, ctx->stream));
     if ((st = reset_counters(ctx))) return st;
     CK(cudaMemsetAsync(&w.sc->status, 0, sizeof(int), ctx->stream));
+    CK(cudaMemsetAsync(&w.sc->cd_updates, 0, sizeof(unsigned long long), ctx->stream));
     const void *cvec = (dtype == BL_F64) ? (const void *)center : (const void *)w.c32;
     const void *isvec = (dtype == BL_F64) ? (const void *)w.inv_scale : (const void *)w.is32;
     int slot = tbegin(ctx, 5);
@@ -490,6 +496,7 @@ extern "C" int bl_cd_active(bl_ctx *ctx, const void *X, int dtype, int64_t n, in
     tend(ctx, slot, 0.0);
     if ((st = sync_sc(ctx))) return st;
     if (sweeps) *sweeps = (int64_t)ctx->sc_host->sweeps;
+    ctx->cd_updates += (int64_t)ctx->sc_host->cd_updates;
     if (ctx->sc_host->status & ST_BAD_INDEX) return fail(ctx, BL_ERR_ARG, "work_idx holds an index outside [0, p)");
     if (ctx->sc_host->status & ST_WORKING_TOO_BIG) return fail(ctx, BL_ERR_UNSUPPORTED, "working set too large");
     if (ctx->sc_host->status & ST_TIMEOUT) return fail(ctx, BL_ERR_TIMEOUT, "CD reached its wall-clock limit");
@@ -665,7 +672,7 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
                                       w.partial, w.r, w.sc, s));
             tend(ctx, slot, 0.0);
             if ((st = reset_round(ctx))) return st;
-            ZpassArgs za{X, n, p, ldx, w.center, w.scale, w.xnorm, w.r, lam, alpha, gamma,
+            ZpassArgs za{X, n, p, ldx, w.center, w.inv_scale, w.xnorm, w.r, lam, alpha, gamma,
                          w.scan, w.safe, w.working, w.z};
             int zslot = tbegin(ctx, 7);
             LAUNCH(1, launch_zpass(dtype, za, w.sc, zgrid, s));
@@ -697,6 +704,7 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
     CK(cudaMemcpyAsync(cp.data(), out->col_ptr, ((size_t)K + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     if ((st = sync_sc(ctx))) return st;
     out->nnz_needed = cp[K];
+    ctx->cd_updates += (int64_t)ctx->sc_host->cd_updates;
     if (out->n_active)
         for (int k = 0; k < K; ++k) out->n_active[k] = cp[k + 1] - cp[k];
     if (ctx->sc_host->status & ST_CAPACITY || out->nnz_needed > out->nnz_capacity)

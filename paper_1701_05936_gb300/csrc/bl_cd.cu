@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(CD_THREADS, 1)
     const A epsA = (A)eps;
     int parity = 0;
     int64_t sweeps = 0;
+    unsigned long long updates = 0;
     int status = 0;
     int prev_tt = -1;
     A prev_nb = 0;
@@ -160,7 +161,11 @@ __global__ void __launch_bounds__(CD_THREADS, 1)
                     prev_nb = nb;
                     const A tol = fmax(epsA, ULP_FLOOR * fabs(nb));
                     moved |= (fabs(d) >= tol);
-                    newnz |= (old == (A)0 && nb != (A)0);
+                    // a coordinate that leaves zero by less than the tolerance does
+                    // not count as entering (a feature at |zt| = lam alpha within
+                    // rounding would otherwise toggle forever)
+                    newnz |= (old == (A)0 && fabs(nb) >= tol);
+                    ++updates;
                     if (t + D < len) load_col(buf[s], idx_s[full ? (int)(t + D) : (int)act_s[t + D]]);
                 }
             }
@@ -248,6 +253,7 @@ __global__ void __launch_bounds__(CD_THREADS, 1)
     }
     if (tid == 0) {
         sc->sweeps += (unsigned long long)sweeps;
+        sc->cd_updates += updates;
         if (status) atomicOr(&sc->status, status);
     }
 }

@@ -32,6 +32,7 @@ struct DevScalars {
     // per-round counters (reset by the host)
     unsigned long long n_viol, n_cols, n_safe, n_strong, n_scan, w, sweeps;
     unsigned long long nnz_total;
+    unsigned long long cd_updates;  // coordinate updates run by CD (never reset by rounds)
     int status;
     int pad;
 };
@@ -110,7 +111,7 @@ cudaError_t launch_rstats(int dtype, const void *r, int64_t n, DevScalars *sc, c
 struct ZpassArgs {
     const void *X;
     int64_t n, p, ldx;
-    const double *center, *scale, *xnorm;
+    const double *center, *inv_scale, *xnorm;
     const void *r;
     double lam, alpha, gamma;
     const uint8_t *scan, *safe;
@@ -118,7 +119,7 @@ struct ZpassArgs {
     float *z;
 };
 cudaError_t launch_zpass(int dtype, const ZpassArgs &a, DevScalars *sc, int grid, cudaStream_t st);
-int zpass_grid(int dtype, int64_t n, int num_sms);
+int zpass_grid(int dtype, int64_t n, int num_sms);  // resident blocks that fit at once
 size_t zpass_smem(int dtype, int64_t n);
 int zpass_depth(int dtype, int64_t n);  // accumulation depth for the rounding bound
 

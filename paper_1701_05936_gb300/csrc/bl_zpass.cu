@@ -14,7 +14,7 @@ namespace bl {
 template <typename T, int U>
 __global__ void __launch_bounds__(256)
     k_zpass(const T *__restrict__ X, int64_t n, int64_t p, int64_t ldx, const double *__restrict__ center,
-            const double *__restrict__ scale, const double *__restrict__ xnorm,
+            const double *__restrict__ inv_scale, const double *__restrict__ xnorm,
             const typename elem<T>::res *__restrict__ r, const DevScalars *__restrict__ sc_in,
             double lam, double alpha, double gamma, const uint8_t *__restrict__ scan,
             const uint8_t *__restrict__ safe, uint8_t *__restrict__ working, float *__restrict__ z,
@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256)
     unsigned int viol = 0, cols = 0;
     for (int64_t j = gw; j < p; j += nw) {
         if (!scan[j]) continue;
-        ++cols;
+        cols += (lane == 0);
         const T *col = X + j * ldx;
         const V *colv = reinterpret_cast<const V *>(col);
         A acc = 0;
@@ -68,14 +68,14 @@ __global__ void __launch_bounds__(256)
             for (int64_t i = nfull * VEC; i < n; ++i) acc = fma((A)col[i], r_s[i], acc);
         acc = warp_sum(acc);
         if (lane == 0) {
-            const double sj = scale[j];
-            const double zj = ((double)acc - center[j] * sum_r) * inv_n / sj;
+            const double f = inv_n * inv_scale[j];
+            const double zj = ((double)acc - center[j] * sum_r) * f;
             z[j] = (float)zj;
             if (safe[j] && !working[j]) {
                 // |fl(x'r) - x'r| <= gamma_m ||x_j|| ||r|| (Higham, Sec. 3.1, with
                 // Cauchy-Schwarz), m = accumulation depth of this kernel.
-                const double tau = gamma * xnorm[j] * rnorm * inv_n / sj * (1.0 + 1e-6) +
-                                   4e-16 * (fabs(center[j] * sum_r) * inv_n / sj + fabs(zj));
+                const double tau = gamma * xnorm[j] * rnorm * f * (1.0 + 1e-6) +
+                                   4e-16 * (fabs(center[j] * sum_r) * f + fabs(zj));
                 if (fabs(zj) > thr - tau) {
                     working[j] = 1;
                     ++viol;
@@ -104,7 +104,7 @@ static cudaError_t zpass_t(const ZpassArgs &a, DevScalars *sc, int grid, cudaStr
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<grid, 256, smem, st>>>((const T *)a.X, a.n, a.p, a.ldx, a.center, a.scale, a.xnorm, (const R *)a.r, sc,
+    kern<<<grid, 256, smem, st>>>((const T *)a.X, a.n, a.p, a.ldx, a.center, a.inv_scale, a.xnorm, (const R *)a.r, sc,
                                   a.lam, a.alpha, a.gamma, a.scan, a.safe, a.working, a.z, sc);
     return cudaGetLastError();
 }
@@ -125,15 +125,24 @@ int zpass_depth(int dtype, int64_t n)
     return (int)(per_lane * vec + (n - nfull * vec) + 5);
 }
 
+// One wave: as many blocks as are resident at once, so that the grid-stride
+// loop never leaves a partial second wave behind.
 int zpass_grid(int dtype, int64_t n, int num_sms)
 {
     const size_t smem = zpass_smem(dtype, n);
-    int per_sm = 6;
-    if (smem > 0) {
-        const int by_smem = (int)((200 * 1024) / (smem + 1024));
-        if (by_smem < per_sm) per_sm = by_smem;
+    int per_sm = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    auto occ = [&](auto kern) {
+        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    };
+    switch (dtype) {
+    case 0: e = occ(k_zpass<double, zpass_unroll<double>()>); break;
+    case 1: e = occ(k_zpass<float, zpass_unroll<float>()>); break;
+    case 3: e = occ(k_zpass<int8_t, zpass_unroll<int8_t>()>); break;
+    default: break;
     }
-    if (per_sm < 1) per_sm = 1;
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     return num_sms * per_sm;
 }
 
