@@ -65,8 +65,8 @@ typedef struct bl_ctx bl_ctx;
 
 /* Largest working set (features entering coordinate descent at one lambda)
  * and largest n that the coordinate-descent kernel of this build accepts. */
-#define BL_MAX_WORKING 12288
-#define BL_MAX_N 16384
+#define BL_MAX_WORKING 8192     /* FP32 and int8 designs; 4096 for FP64 */
+#define BL_MAX_N 16384          /* FP32 and int8 designs; 4096 for FP64 */
 
 /* Options of bl_fit_path. */
 typedef struct {
@@ -107,8 +107,9 @@ typedef struct {
 
 /* Per-kernel timing collected with CUDA events on the ctx stream while timing
  * is enabled (bl_ctx_set_timing).  Kinds: 0 standardize, 1 lambda_max,
- * 2 bedpp_init, 3 screen, 4 compact, 5 cd, 6 residual, 7 zpass, 8 record. */
-#define BL_NUM_KINDS 9
+ * 2 bedpp_init, 3 screen, 4 compact, 5 cd, 6 residual, 7 zpass, 8 record,
+ * 9 gref (the FP64 reference gradients each CD launch starts from). */
+#define BL_NUM_KINDS 10
 typedef struct {
     int64_t launches[BL_NUM_KINDS];
     double ms[BL_NUM_KINDS];         /* summed device time */

@@ -26,7 +26,8 @@ BL_OK, BL_ERR_ARG, BL_ERR_CUDA, BL_ERR_OOM = 0, -1, -2, -3
 BL_ERR_NOT_CONVERGED, BL_ERR_TIMEOUT, BL_ERR_UNSUPPORTED, BL_ERR_CAPACITY = -4, -5, -6, -7
 BL_F64, BL_F32, BL_BF16, BL_I8 = 0, 1, 2, 3
 BL_SCREEN_NONE, BL_SCREEN_SSR, BL_SCREEN_SSR_BEDPP = 0, 1, 2
-KINDS = ["standardize", "lambda_max", "bedpp_init", "screen", "compact", "cd", "residual", "zpass", "record"]
+KINDS = ["standardize", "lambda_max", "bedpp_init", "screen", "compact", "cd", "residual", "zpass", "record",
+         "gref"]
 
 _STATUS = {0: "BL_OK", -1: "BL_ERR_ARG", -2: "BL_ERR_CUDA", -3: "BL_ERR_OOM", -4: "BL_ERR_NOT_CONVERGED",
            -5: "BL_ERR_TIMEOUT", -6: "BL_ERR_UNSUPPORTED", -7: "BL_ERR_CAPACITY"}
@@ -54,7 +55,7 @@ class bl_path(C.Structure):
 
 
 class bl_timing(C.Structure):
-    _fields_ = [("launches", C.c_int64 * 9), ("ms", C.c_double * 9), ("bytes", C.c_double * 9),
+    _fields_ = [("launches", C.c_int64 * 10), ("ms", C.c_double * 10), ("bytes", C.c_double * 10),
                 ("kernel_launches", C.c_int64), ("cd_updates", C.c_int64)]
 
 

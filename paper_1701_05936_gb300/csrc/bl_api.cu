@@ -33,9 +33,9 @@ struct Workspace {
     void *beta;
     uint8_t *keep, *safe, *working, *scan;
     int32_t *idx;
-    double *yc, *xcs, *partial, *part_val;
+    double *yc, *xcs, *partial, *part_val, *r64;
     long long *part_idx;
-    void *r;
+    void *r, *gref;
     DevScalars *sc;
 };
 
@@ -94,7 +94,8 @@ int ensure_ws(bl_ctx *ctx, int64_t n, int64_t p)
     const size_t p8 = align256((size_t)P * 8), p4 = align256((size_t)P * 4), p1 = align256((size_t)P + 16);
     const size_t n8 = align256((size_t)N * 8);
     const size_t idxb = align256((size_t)MAX_WORKING * 4);
-    const size_t total = 6 * p8 + 3 * p4 + p8 + 4 * p1 + idxb + 3 * n8 + (size_t)RESID_GROUPS * n8 +
+    const size_t grefb = align256((size_t)MAX_WORKING * 8);
+    const size_t total = 6 * p8 + 3 * p4 + p8 + 4 * p1 + idxb + grefb + 4 * n8 + (size_t)RESID_GROUPS * n8 +
                          2 * align256(1024 * 8) + align256(sizeof(DevScalars));
     if (w.base) {
         cudaStreamSynchronize(ctx->stream);
@@ -129,8 +130,10 @@ int ensure_ws(bl_ctx *ctx, int64_t n, int64_t p)
     w.working = (uint8_t *)take(p1);
     w.scan = (uint8_t *)take(p1);
     w.idx = (int32_t *)take(idxb);
+    w.gref = take(grefb);
     w.yc = (double *)take(n8);
     w.r = take(n8);
+    w.r64 = (double *)take(n8);
     w.xcs = (double *)take(n8);
     w.partial = (double *)take((size_t)RESID_GROUPS * n8);
     w.part_val = (double *)take(align256(1024 * 8));
@@ -489,9 +492,15 @@ extern "C" int bl_cd_active(bl_ctx *ctx, const void *X, int dtype, int64_t n, in
     CK(cudaMemsetAsync(&w.sc->cd_updates, 0, sizeof(unsigned long long), ctx->stream));
     const void *cvec = (dtype == BL_F64) ? (const void *)center : (const void *)w.c32;
     const void *isvec = (dtype == BL_F64) ? (const void *)w.inv_scale : (const void *)w.is32;
+    if (n_work > 0) {
+        int gslot = tbegin(ctx, 9);
+        LAUNCH(1, launch_gref(dtype, X, n, ldx, p, center, work_idx, n_work, w.sc, r, dtype == BL_F64, w.gref,
+                              ctx->num_sms, ctx->stream));
+        tend(ctx, gslot, (double)n * n_work * elem_size(dtype));
+    }
     int slot = tbegin(ctx, 5);
     if (n_work > 0)
-        LAUNCH(1, launch_cd(dtype, X, n, p, ldx, cvec, isvec, work_idx, n_work, lam, alpha, beta, r, eps,
+        LAUNCH(1, launch_cd(dtype, X, n, p, ldx, cvec, isvec, work_idx, n_work, w.gref, lam, alpha, beta, r, eps,
                             max_sweeps, CD_TIME_LIMIT_NS, w.sc, ctx->stream));
     tend(ctx, slot, 0.0);
     if ((st = sync_sc(ctx))) return st;
@@ -589,7 +598,7 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
     LAUNCH(1, launch_init_z(w.xty, w.keep, p, n, w.z, s));
     slot = tbegin(ctx, 6);
     LAUNCH(1, launch_residual(dtype, X, n, ldx, w.center, w.inv_scale, w.idx, 0, w.sc, w.beta, w.yc, w.partial,
-                              w.r, w.sc, s));
+                              w.r, w.r64, w.sc, s));
     tend(ctx, slot, (double)n * 16);
 
     const void *cvec = beta_f64 ? (const void *)w.center : (const void *)w.c32;
@@ -663,13 +672,16 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
             slot = tbegin(ctx, 4);
             LAUNCH(1, launch_compact(w.working, p, w.idx, wcap, w.sc, s));
             tend(ctx, slot, (double)p);
+            slot = tbegin(ctx, 9);
+            LAUNCH(1, launch_gref(dtype, X, n, ldx, p, w.center, w.idx, -1, w.sc, w.r64, 1, w.gref, ctx->num_sms, s));
+            tend(ctx, slot, 0.0);
             slot = tbegin(ctx, 5);
-            LAUNCH(1, launch_cd(dtype, X, n, p, ldx, cvec, isvec, w.idx, -1, lam, alpha, w.beta, w.r, eps,
+            LAUNCH(1, launch_cd(dtype, X, n, p, ldx, cvec, isvec, w.idx, -1, w.gref, lam, alpha, w.beta, nullptr, eps,
                                 opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc, s));
             tend(ctx, slot, 0.0);
             slot = tbegin(ctx, 6);
             LAUNCH(2, launch_residual(dtype, X, n, ldx, w.center, w.inv_scale, w.idx, -1, w.sc, w.beta, w.yc,
-                                      w.partial, w.r, w.sc, s));
+                                      w.partial, w.r, w.r64, w.sc, s));
             tend(ctx, slot, 0.0);
             if ((st = reset_round(ctx))) return st;
             ZpassArgs za{X, n, p, ldx, w.center, w.inv_scale, w.xnorm, w.r, lam, alpha, gamma,

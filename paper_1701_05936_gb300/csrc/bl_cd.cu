@@ -1,39 +1,121 @@
-// bl_cd.cu -- coordinate descent over the working set, the FP64 residual
-// recomputation (and the objective's RSS), and the per-lambda record step.
+// bl_cd.cu -- cyclic coordinate descent over the working set (one CTA), and
+// the FP64 reference gradients it starts from.
+//
+// Pathwise CD with residual updates and active-set cycling (Sec. 1 and
+// Sec. 3.1.1): for lambda_k, starting from b(lambda_{k-1}),
+//   repeat { one sweep over the working set W in ascending feature order;
+//            sweeps over the nonzero coordinates until no change >= tol }
+//   until a full sweep changes nothing by tol and adds no nonzero;
+// coordinate j:  zt = xt_j'r/n + b_j,  b_j' = S(zt, lam alpha)/(1 + lam(1-alpha)),
+//                r <- r - (b_j' - b_j) xt_j,  xt_ij = (x_ij - c_j)/s_j.
+//
+// Precision.  The residual is split as r = r_ref - dr, where r_ref is the
+// residual at the start of the launch and dr the change made by this launch.
+// g_ref[t] = sum_i (x_ij - c_j) r_ref_i is computed beforehand in FP64
+// (k_gref), and the kernel accumulates only dr and sum_i (x_ij - c_j) dr_i in
+// FP32, so the rounding noise of the dot product scales with |dr| rather than
+// with |r| (near lambda_max, |sum_i (x_ij - c_j) r_i| ~ n lam s_j, whose FP32
+// rounding alone is of the order of the tolerance).  A change below
+// max(eps, 8u(|zt| + |b_j'|)), u the unit roundoff, counts as no change.
 #include "bl_device.cuh"
 #include "bl_internal.h"
 
 namespace bl {
 
+// ------------------------------------------------ reference gradients (FP64)
+template <typename T, typename RT>
+__global__ void __launch_bounds__(256)
+    k_gref(const T *__restrict__ X, int64_t n, int64_t ldx, int64_t p, const double *__restrict__ center,
+           const int32_t *__restrict__ idx, int64_t w_host, int64_t cap, const DevScalars *__restrict__ scw,
+           const RT *__restrict__ r, typename elem<T>::acc *__restrict__ gref)
+{
+    using E = elem<T>;
+    using A = typename E::acc;
+    using V = typename E::vec;
+    constexpr int VEC = E::VEC;
+    int64_t w = (w_host >= 0) ? w_host : (int64_t)scw->w;
+    if (w > cap) w = cap;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nfull = n / VEC;
+    for (int64_t t = gw; t < w; t += nw) {
+        const int32_t j = idx[t];
+        if (j < 0 || (int64_t)j >= p) continue;  // the CD kernel reports bad indices
+        const T *col = X + (int64_t)j * ldx;
+        const V *colv = reinterpret_cast<const V *>(col);
+        const double cj = center[j];
+        double acc = 0.0;
+        for (int64_t q = lane; q < nfull; q += 32) {
+            A e[VEC];
+            unpack(ldg16(colv + q), e);
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) acc = fma((double)e[k] - cj, (double)r[q * VEC + k], acc);
+        }
+        for (int64_t i = nfull * VEC + lane; i < n; i += 32) acc = fma(to_f64(col[i]) - cj, (double)r[i], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) gref[t] = (A)acc;
+    }
+}
+
+template <typename T, typename RT>
+static cudaError_t gref_t(const T *X, int64_t n, int64_t ldx, int64_t p, const double *center, const int32_t *idx,
+                          int64_t w_host, int64_t cap, const DevScalars *scw, const RT *r, void *gref, int num_sms,
+                          cudaStream_t st)
+{
+    using A = typename elem<T>::acc;
+    int64_t blocks = (w_host >= 0) ? (w_host + 7) / 8 : (cap + 7) / 8;
+    if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
+    if (blocks < 1) blocks = 1;
+    k_gref<T, RT><<<(int)blocks, 256, 0, st>>>(X, n, ldx, p, center, idx, w_host, cap, scw, r, (A *)gref);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gref(int dtype, const void *X, int64_t n, int64_t ldx, int64_t p, const double *center,
+                        const int32_t *idx, int64_t w_host, const DevScalars *scw, const void *r, int r_f64,
+                        void *gref, int num_sms, cudaStream_t st)
+{
+    const int64_t cap = (dtype == 0) ? MAX_WORKING_F64 : MAX_WORKING;
+    switch (dtype) {
+    case 0:
+        return r_f64 ? gref_t((const double *)X, n, ldx, p, center, idx, w_host, cap, scw, (const double *)r, gref, num_sms, st)
+                     : gref_t((const double *)X, n, ldx, p, center, idx, w_host, cap, scw, (const float *)r, gref, num_sms, st);
+    case 1:
+        return r_f64 ? gref_t((const float *)X, n, ldx, p, center, idx, w_host, cap, scw, (const double *)r, gref, num_sms, st)
+                     : gref_t((const float *)X, n, ldx, p, center, idx, w_host, cap, scw, (const float *)r, gref, num_sms, st);
+    case 3:
+        return r_f64 ? gref_t((const int8_t *)X, n, ldx, p, center, idx, w_host, cap, scw, (const double *)r, gref, num_sms, st)
+                     : gref_t((const int8_t *)X, n, ldx, p, center, idx, w_host, cap, scw, (const float *)r, gref, num_sms, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 // ------------------------------------------------------ coordinate descent
-// One CTA of CD_THREADS threads runs the whole cyclic CD of one lambda
-// (Sec. 1 / Sec. 3.1.1: pathwise CD with residual updates and active-set
-// cycling, same sweep structure as the oracle).  The residual lives in
-// registers: thread t owns the 16-byte row chunks t, t+256, ... (RPT of them).
-// Coordinate j:  dot = sum_i (x_ij - c_j) r_i  (cell-wise standardization in
-// registers) reduced across the block; every thread then evaluates the same
-// scalar update
-//     zt = dot / (n s_j) + b_j,  b_j' = S(zt, lam alpha) / (1 + lam (1 - alpha)),
-//     r_i -= (b_j' - b_j) (x_ij - c_j) / s_j.
-// Column chunks for the next D coordinates are prefetched into registers.
-// Working-set metadata (index, c_j, 1/s_j, b_j) sits in shared memory.
-template <typename T, int RPT, int D>
-__global__ void __launch_bounds__(CD_THREADS, 1)
-    k_cd(const T *__restrict__ X, int64_t n, int64_t ldx,
-         const typename elem<T>::acc *__restrict__ cvec,
-         const typename elem<T>::acc *__restrict__ isvec, const int32_t *__restrict__ idx,
-         int64_t w_host, int64_t cap, int64_t p, double lam, double alpha, typename elem<T>::res *beta,
-         typename elem<T>::res *r_io, double eps, int64_t max_sweeps, uint64_t time_limit_ns,
-         DevScalars *sc)
+// One CTA of NW warps.  Thread t owns the 16-byte row chunks t, t + 32 NW, ...
+// (RPT of them) of dr in registers.  Column chunks of the next D coordinates
+// are prefetched into registers; all working-set columns are prefetched into
+// L2 by bulk-prefetch instructions when the kernel starts.  Working-set
+// metadata (index, c_j, 1/s_j, g_ref, b_j) sits in shared memory.  Every
+// thread evaluates the same scalar update and writes the same b_j', so no
+// thread ever reads a shared-memory value another thread wrote; the only
+// cross-thread exchange is the reduction of the dot product.
+template <typename T, int NW, int RPT, int D>
+__global__ void __launch_bounds__(32 * NW, 1)
+    k_cd(const T *__restrict__ X, int64_t n, int64_t ldx, const typename elem<T>::acc *__restrict__ cvec,
+         const typename elem<T>::acc *__restrict__ isvec, const int32_t *__restrict__ idx, int64_t w_host,
+         int64_t cap, int64_t p, const typename elem<T>::acc *__restrict__ gref, double lam, double alpha,
+         typename elem<T>::res *beta, typename elem<T>::res *r_io, double eps, int64_t max_sweeps,
+         uint64_t time_limit_ns, DevScalars *sc)
 {
     using E = elem<T>;
     using A = typename E::acc;
     using R = typename E::res;
     using V = typename E::vec;
     constexpr int VEC = E::VEC;
-    constexpr int NT = CD_THREADS;
-    constexpr int NW = NT / 32;
-    constexpr A ULP_FLOOR = sizeof(A) == 4 ? (A)9.5367431640625e-07 : (A)0;  // 2^-20 in FP32
+    constexpr int NT = 32 * NW;
+    static_assert(RPT * VEC <= 64, "row-validity mask holds 64 rows per thread");
+    // 8 units in the last place: 2^-21 in FP32, 2^-50 in FP64
+    constexpr A RES_FLOOR = sizeof(A) == 4 ? (A)4.76837158203125e-07 : (A)8.881784197001252e-16;
 
     const int64_t w = (w_host >= 0) ? w_host : (int64_t)sc->w;
     if (w > cap) {
@@ -43,13 +125,14 @@ __global__ void __launch_bounds__(CD_THREADS, 1)
     extern __shared__ __align__(16) unsigned char smem[];
     A *c_s = reinterpret_cast<A *>(smem);
     A *is_s = c_s + cap;
-    R *beta_s = reinterpret_cast<R *>(is_s + cap);
+    A *g_s = is_s + cap;
+    R *beta_s = reinterpret_cast<R *>(g_s + cap);
     int32_t *idx_s = reinterpret_cast<int32_t *>(beta_s + cap);
     uint16_t *act_s = reinterpret_cast<uint16_t *>(idx_s + cap);
     __shared__ A red[2][NW];
     __shared__ unsigned int scan_s[NW + 1];
-
     __shared__ int flag_s;
+
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) flag_s = 0;
     __syncthreads();
@@ -62,6 +145,7 @@ __global__ void __launch_bounds__(CD_THREADS, 1)
         idx_s[t] = j;
         c_s[t] = cvec[j];
         is_s[t] = isvec[j];
+        g_s[t] = gref[t];
         beta_s[t] = beta[j];
     }
     __syncthreads();
@@ -69,22 +153,26 @@ __global__ void __launch_bounds__(CD_THREADS, 1)
         if (tid == 0) atomicOr(&sc->status, ST_BAD_INDEX);
         return;
     }
+    // pull every working-set column into L2 (the first sweep would otherwise
+    // wait for HBM on each coordinate)
+    const uint32_t col_bytes = (uint32_t)(((uint64_t)n * sizeof(T) + 15) & ~(uint64_t)15);
+    for (int64_t t = tid; t < w; t += NT) {
+        const T *col = X + (int64_t)idx_s[t] * ldx;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(col), "r"(col_bytes) : "memory");
+    }
     const uint64_t t_start = globaltimer_ns();
     const int64_t nch = (n + VEC - 1) / VEC;
-    A r[RPT][VEC];
+    A dr[RPT][VEC];
     uint64_t vmask = 0;  // bit q*VEC+v: row valid
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
         const int64_t ch = (int64_t)q * NT + tid;
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
-            const int64_t row = ch * VEC + v;
-            const bool ok = row < n;
-            r[q][v] = ok ? (A)r_io[row] : (A)0;
-            if (ok) vmask |= (1ull << (q * VEC + v));
+            dr[q][v] = (A)0;
+            if (ch * VEC + v < n) vmask |= (1ull << (q * VEC + v));
         }
     }
-    __syncthreads();
 
     const A thr = (A)(lam * alpha);
     const A inv_den = (A)(1.0 / (1.0 + lam * (1.0 - alpha)));
@@ -102,13 +190,10 @@ __global__ void __launch_bounds__(CD_THREADS, 1)
 #pragma unroll
         for (int q = 0; q < RPT; ++q) {
             const int64_t ch = (int64_t)q * NT + tid;
-            if (ch < nch) buf[q] = ldg16(colv + ch);
-            else buf[q] = V{};
+            buf[q] = (ch < nch) ? ldg16(colv + ch) : V{};
         }
     };
 
-    // One sweep over len coordinates; coordinate t is t itself (full sweep)
-    // or act_s[t] (active sweep).  Returns through moved/newnz.
     auto sweep = [&](bool full, int64_t len, bool &moved, bool &newnz) {
         V buf[D][RPT];
 #pragma unroll
@@ -120,9 +205,9 @@ __global__ void __launch_bounds__(CD_THREADS, 1)
                 const int64_t t = base + s;
                 if (t < len) {
                     const int tt = full ? (int)t : (int)act_s[t];
-                    const A cj = c_s[tt], isj = is_s[tt];
+                    const A cj = c_s[tt], isj = is_s[tt], gj = g_s[tt];
                     const A old = (tt == prev_tt) ? prev_nb : (A)beta_s[tt];
-                    A part = 0;
+                    A acc[4] = {0, 0, 0, 0};
 #pragma unroll
                     for (int q = 0; q < RPT; ++q) {
                         A e[VEC];
@@ -130,17 +215,19 @@ __global__ void __launch_bounds__(CD_THREADS, 1)
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) {
                             const A xd = ((vmask >> (q * VEC + v)) & 1ull) ? e[v] - cj : (A)0;
-                            part = fma(xd, r[q][v], part);
+                            acc[v & 3] = fma(xd, dr[q][v], acc[v & 3]);
                         }
                     }
-                    part = warp_sum(part);
-                    if (lane == 0) red[parity][wid] = part;
-                    __syncthreads();
-                    A dot = 0;
+                    A dot = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
+                    if (NW > 1) {
+                        if (lane == 0) red[parity][wid] = dot;
+                        __syncthreads();
+                        dot = 0;
 #pragma unroll
-                    for (int k = 0; k < NW; ++k) dot += red[parity][k];
-                    parity ^= 1;
-                    const A zt = dot * isj * inv_n + old;
+                        for (int k = 0; k < NW; ++k) dot += red[parity][k];
+                        parity ^= 1;
+                    }
+                    const A zt = fma(gj - dot, isj * inv_n, old);
                     const A nb = soft_threshold(zt, thr) * inv_den;
                     const A d = nb - old;
                     if (d != (A)0) {
@@ -152,18 +239,17 @@ __global__ void __launch_bounds__(CD_THREADS, 1)
 #pragma unroll
                             for (int v = 0; v < VEC; ++v) {
                                 const A xd = ((vmask >> (q * VEC + v)) & 1ull) ? e[v] - cj : (A)0;
-                                r[q][v] = fma(-ds, xd, r[q][v]);
+                                dr[q][v] = fma(ds, xd, dr[q][v]);
                             }
                         }
                     }
-                    if (tid == 0) beta_s[tt] = (R)nb;
+                    beta_s[tt] = (R)nb;
                     prev_tt = tt;
                     prev_nb = nb;
-                    const A tol = fmax(epsA, ULP_FLOOR * fabs(nb));
+                    const A tol = fmax(epsA, RES_FLOOR * (fabs(zt) + fabs(nb)));
                     moved |= (fabs(d) >= tol);
-                    // a coordinate that leaves zero by less than the tolerance does
-                    // not count as entering (a feature at |zt| = lam alpha within
-                    // rounding would otherwise toggle forever)
+                    // leaving zero by less than the tolerance is not entering: a
+                    // feature with |zt| = lam alpha within rounding would toggle
                     newnz |= (old == (A)0 && fabs(nb) >= tol);
                     ++updates;
                     if (t + D < len) load_col(buf[s], idx_s[full ? (int)(t + D) : (int)act_s[t + D]]);
@@ -172,15 +258,14 @@ __global__ void __launch_bounds__(CD_THREADS, 1)
         }
     };
 
-    // Wall-clock guard, checked once per sweep by thread 0 and broadcast, so a
-    // sweep sequence that stops making progress ends with a status instead of
-    // occupying the GPU.
+    // wall-clock guard, checked once per sweep by thread 0 and broadcast
     auto out_of_time = [&]() -> bool {
         __syncthreads();
         if (tid == 0) flag_s = (globaltimer_ns() - t_start) > time_limit_ns;
         __syncthreads();
         return flag_s != 0;
     };
+
     for (;;) {
         bool moved = false, newnz = false;
         sweep(true, w, moved, newnz);
@@ -194,8 +279,8 @@ __global__ void __launch_bounds__(CD_THREADS, 1)
             status = ST_TIMEOUT;
             break;
         }
-        // active list: ordered positions t with beta_s[t] != 0
-        __syncthreads();
+        // active list: ordered positions t with beta_s[t] != 0 (each thread
+        // reads entries it wrote itself)
         const int64_t per = (w + NT - 1) / NT;
         const int64_t b0 = (int64_t)tid * per;
         const int64_t b1 = (b0 + per < w) ? b0 + per : w;
@@ -210,13 +295,13 @@ __global__ void __launch_bounds__(CD_THREADS, 1)
         if (lane == 31) scan_s[wid] = incl;
         __syncthreads();
         if (tid == 0) {
-            unsigned int acc = 0;
+            unsigned int a = 0;
             for (int k = 0; k < NW; ++k) {
                 const unsigned int v = scan_s[k];
-                scan_s[k] = acc;
-                acc += v;
+                scan_s[k] = a;
+                a += v;
             }
-            scan_s[NW] = acc;
+            scan_s[NW] = a;
         }
         __syncthreads();
         unsigned int pos = scan_s[wid] + incl - c;
@@ -240,15 +325,16 @@ __global__ void __launch_bounds__(CD_THREADS, 1)
         }
         if (status) break;
     }
-    __syncthreads();
     for (int64_t t = tid; t < w; t += NT) beta[idx_s[t]] = beta_s[t];
+    if (r_io) {
 #pragma unroll
-    for (int q = 0; q < RPT; ++q) {
-        const int64_t ch = (int64_t)q * NT + tid;
+        for (int q = 0; q < RPT; ++q) {
+            const int64_t ch = (int64_t)q * NT + tid;
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-            const int64_t row = ch * VEC + v;
-            if (row < n) r_io[row] = (R)r[q][v];
+            for (int v = 0; v < VEC; ++v) {
+                const int64_t row = ch * VEC + v;
+                if (row < n) r_io[row] = (R)((A)r_io[row] - dr[q][v]);
+            }
         }
     }
     if (tid == 0) {
@@ -258,276 +344,66 @@ __global__ void __launch_bounds__(CD_THREADS, 1)
     }
 }
 
-template <typename T, int RPT, int D>
+template <typename T, int NW, int RPT, int D>
 static cudaError_t cd_launch(const T *X, int64_t n, int64_t ldx, const void *cvec, const void *isvec,
-                             const int32_t *idx, int64_t w_host, int64_t cap, int64_t p, double lam,
-                             double alpha, void *beta, void *r, double eps, int64_t max_sweeps,
-                             uint64_t tl, DevScalars *sc, cudaStream_t st)
+                             const int32_t *idx, int64_t w_host, int64_t cap, int64_t p, const void *gref, double lam,
+                             double alpha, void *beta, void *r, double eps, int64_t max_sweeps, uint64_t tl,
+                             DevScalars *sc, cudaStream_t st)
 {
     using A = typename elem<T>::acc;
     using R = typename elem<T>::res;
-    const size_t smem = (size_t)cap * (2 * sizeof(A) + sizeof(R) + sizeof(int32_t) + sizeof(uint16_t));
-    auto kern = k_cd<T, RPT, D>;
+    const size_t smem = (size_t)cap * (3 * sizeof(A) + sizeof(R) + sizeof(int32_t) + sizeof(uint16_t));
+    auto kern = k_cd<T, NW, RPT, D>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<1, CD_THREADS, smem, st>>>(X, n, ldx, (const A *)cvec, (const A *)isvec, idx, w_host, cap, p, lam,
-                                      alpha, (R *)beta, (R *)r, eps, max_sweeps, tl, sc);
+    kern<<<1, 32 * NW, smem, st>>>(X, n, ldx, (const A *)cvec, (const A *)isvec, idx, w_host, cap, p, (const A *)gref,
+                                   lam, alpha, (R *)beta, (R *)r, eps, max_sweeps, tl, sc);
     return cudaGetLastError();
 }
 
+// Shape: one warp while the rows fit 8 chunks per lane, else 4 or 8 warps.
 template <typename T>
 static cudaError_t cd_dispatch(const T *X, int64_t n, int64_t ldx, const void *cvec, const void *isvec,
-                               const int32_t *idx, int64_t w_host, int64_t cap, int64_t p, double lam,
-                               double alpha, void *beta, void *r, double eps, int64_t max_sweeps, uint64_t tl,
-                               DevScalars *sc, cudaStream_t st)
+                               const int32_t *idx, int64_t w_host, int64_t cap, int64_t p, const void *gref,
+                               double lam, double alpha, void *beta, void *r, double eps, int64_t max_sweeps,
+                               uint64_t tl, DevScalars *sc, cudaStream_t st)
 {
     constexpr int VEC = elem<T>::VEC;
     const int64_t nch = (n + VEC - 1) / VEC;
-    const int64_t rpt = (nch + CD_THREADS - 1) / CD_THREADS;
-    if (rpt <= 1) return cd_launch<T, 1, 4>(X, n, ldx, cvec, isvec, idx, w_host, cap, p, lam, alpha, beta, r, eps, max_sweeps, tl, sc, st);
-    if (rpt <= 2) return cd_launch<T, 2, 4>(X, n, ldx, cvec, isvec, idx, w_host, cap, p, lam, alpha, beta, r, eps, max_sweeps, tl, sc, st);
-    if (rpt <= 4) return cd_launch<T, 4, 2>(X, n, ldx, cvec, isvec, idx, w_host, cap, p, lam, alpha, beta, r, eps, max_sweeps, tl, sc, st);
-    if (sizeof(T) != 1 && rpt <= 8) return cd_launch<T, 8, 1>(X, n, ldx, cvec, isvec, idx, w_host, cap, p, lam, alpha, beta, r, eps, max_sweeps, tl, sc, st);
-    if (sizeof(T) == 4 && rpt <= 16) return cd_launch<T, 16, 1>(X, n, ldx, cvec, isvec, idx, w_host, cap, p, lam, alpha, beta, r, eps, max_sweeps, tl, sc, st);
+#define BL_CD(NW_, RPT_, D_) \
+    return cd_launch<T, NW_, RPT_, D_>(X, n, ldx, cvec, isvec, idx, w_host, cap, p, gref, lam, alpha, beta, r, eps, max_sweeps, tl, sc, st)
+    if (nch <= 32 * 1) BL_CD(1, 1, 4);
+    if (nch <= 32 * 2) BL_CD(1, 2, 4);
+    if (nch <= 32 * 4) BL_CD(1, 4, 3);
+    if constexpr (VEC == 4) {  // FP32: up to 16384 rows
+        if (nch <= 32 * 8) BL_CD(1, 8, 2);
+        if (nch <= 128 * 4) BL_CD(4, 4, 3);
+        if (nch <= 128 * 8) BL_CD(4, 8, 2);
+        if (nch <= 256 * 8) BL_CD(8, 8, 2);
+        if (nch <= 256 * 16) BL_CD(8, 16, 1);
+    } else if constexpr (VEC == 16) {  // int8: up to 16384 rows, 64 rows per thread
+        if (nch <= 128 * 4) BL_CD(4, 4, 3);
+        if (nch <= 256 * 4) BL_CD(8, 4, 3);
+    } else {  // FP64: up to 4096 rows
+        if (nch <= 32 * 8) BL_CD(1, 8, 1);
+        if (nch <= 128 * 4) BL_CD(4, 4, 3);
+        if (nch <= 128 * 8) BL_CD(4, 8, 1);
+        if (nch <= 256 * 8) BL_CD(8, 8, 1);
+    }
+#undef BL_CD
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_cd(int dtype, const void *X, int64_t n, int64_t p, int64_t ldx, const void *cvec,
-                      const void *isvec, const int32_t *idx, int64_t w_host, double lam, double alpha, void *beta,
-                      void *r, double eps, int64_t max_sweeps, uint64_t time_limit_ns, DevScalars *sc,
-                      cudaStream_t st)
+cudaError_t launch_cd(int dtype, const void *X, int64_t n, int64_t p, int64_t ldx, const void *cvec, const void *isvec,
+                      const int32_t *idx, int64_t w_host, const void *gref, double lam, double alpha, void *beta,
+                      void *r, double eps, int64_t max_sweeps, uint64_t time_limit_ns, DevScalars *sc, cudaStream_t st)
 {
     switch (dtype) {
-    case 0: return cd_dispatch((const double *)X, n, ldx, cvec, isvec, idx, w_host, MAX_WORKING_F64, p, lam, alpha, beta, r, eps, max_sweeps, time_limit_ns, sc, st);
-    case 1: return cd_dispatch((const float *)X, n, ldx, cvec, isvec, idx, w_host, MAX_WORKING, p, lam, alpha, beta, r, eps, max_sweeps, time_limit_ns, sc, st);
-    case 3: return cd_dispatch((const int8_t *)X, n, ldx, cvec, isvec, idx, w_host, MAX_WORKING, p, lam, alpha, beta, r, eps, max_sweeps, time_limit_ns, sc, st);
+    case 0: return cd_dispatch((const double *)X, n, ldx, cvec, isvec, idx, w_host, MAX_WORKING_F64, p, gref, lam, alpha, beta, r, eps, max_sweeps, time_limit_ns, sc, st);
+    case 1: return cd_dispatch((const float *)X, n, ldx, cvec, isvec, idx, w_host, MAX_WORKING, p, gref, lam, alpha, beta, r, eps, max_sweeps, time_limit_ns, sc, st);
+    case 3: return cd_dispatch((const int8_t *)X, n, ldx, cvec, isvec, idx, w_host, MAX_WORKING, p, gref, lam, alpha, beta, r, eps, max_sweeps, time_limit_ns, sc, st);
     default: return cudaErrorInvalidValue;
     }
-}
-
-// ------------------------------------------------------ residual in FP64
-// partial[g][i] = sum over working positions t = g, g+G, ... with b_j != 0 of
-// b_j (x_ij - c_j) / s_j, all in FP64; then r_i = yc_i - sum_g partial[g][i]
-// (fixed order) is rounded to the residual type.
-template <typename T, typename R>
-__global__ void __launch_bounds__(256)
-    k_resid_partial(const T *__restrict__ X, int64_t n, int64_t ldx, const double *__restrict__ center,
-                    const double *__restrict__ inv_scale, const int32_t *__restrict__ idx,
-                    int64_t w_host, const DevScalars *__restrict__ scw, const R *__restrict__ beta,
-                    double *__restrict__ partial)
-{
-    const int64_t w = (w_host >= 0) ? w_host : (int64_t)scw->w;
-    const int G = gridDim.y, g = blockIdx.y;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double acc = 0.0;
-    for (int64_t t = g; t < w; t += G) {
-        const int32_t j = idx[t];
-        const double b = (double)beta[j];
-        if (b != 0.0 && i < n) acc = fma(b * inv_scale[j], to_f64(X[(int64_t)j * ldx + i]) - center[j], acc);
-    }
-    if (i < n) partial[(int64_t)g * n + i] = acc;
-}
-
-template <typename R>
-__global__ void __launch_bounds__(1024)
-    k_resid_final(int64_t n, int G, const double *__restrict__ yc, const double *__restrict__ partial,
-                  R *__restrict__ r_out, DevScalars *sc)
-{
-    __shared__ double buf[33];
-    double s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += 1024) {
-        double v = yc[i];
-        for (int g = 0; g < G; ++g) v -= partial[(int64_t)g * n + i];
-        const R rr = (R)v;
-        r_out[i] = rr;
-        s1 += (double)rr;
-        s2 += (double)rr * (double)rr;
-        s3 += v * v;
-    }
-    // the sums use the same fixed tree as the rest of the library
-    double t1 = warp_sum(s1), t2 = warp_sum(s2), t3 = warp_sum(s3);
-    __shared__ double b1[32], b2[32], b3[32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-        b1[wid] = t1;
-        b2[wid] = t2;
-        b3[wid] = t3;
-    }
-    __syncthreads();
-    if (wid == 0) {
-        t1 = warp_sum(b1[lane]);
-        t2 = warp_sum(b2[lane]);
-        t3 = warp_sum(b3[lane]);
-        if (lane == 0) {
-            sc->sum_r = t1;
-            sc->rnorm = sqrt(t2);
-            sc->rss = t3;
-        }
-    }
-    (void)buf;
-}
-
-template <typename T>
-static cudaError_t resid_t(const T *X, int64_t n, int64_t ldx, const double *center, const double *inv_scale,
-                           const int32_t *idx, int64_t w_host, const DevScalars *scw, const void *beta,
-                           const double *yc, double *partial, void *r_out, DevScalars *sc, cudaStream_t st)
-{
-    using R = typename elem<T>::res;
-    int G = 0;
-    if (w_host != 0) {
-        G = RESID_GROUPS;
-        if (w_host > 0 && w_host < G) G = (int)w_host;
-        dim3 grid((unsigned)((n + 255) / 256), (unsigned)G);
-        k_resid_partial<T, R><<<grid, 256, 0, st>>>(X, n, ldx, center, inv_scale, idx, w_host, scw,
-                                                     (const R *)beta, partial);
-    }
-    k_resid_final<R><<<1, 1024, 0, st>>>(n, G, yc, partial, (R *)r_out, sc);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_residual(int dtype, const void *X, int64_t n, int64_t ldx, const double *center,
-                            const double *inv_scale, const int32_t *idx, int64_t w_host,
-                            const DevScalars *sc_w, const void *beta, const double *yc, double *partial,
-                            void *r_out, DevScalars *sc, cudaStream_t st)
-{
-    switch (dtype) {
-    case 0: return resid_t((const double *)X, n, ldx, center, inv_scale, idx, w_host, sc_w, beta, yc, partial, r_out, sc, st);
-    case 1: return resid_t((const float *)X, n, ldx, center, inv_scale, idx, w_host, sc_w, beta, yc, partial, r_out, sc, st);
-    case 3: return resid_t((const int8_t *)X, n, ldx, center, inv_scale, idx, w_host, sc_w, beta, yc, partial, r_out, sc, st);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
-template <typename R>
-__global__ void __launch_bounds__(1024) k_rstats(const R *__restrict__ r, int64_t n, DevScalars *sc)
-{
-    double s1 = 0.0, s2 = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += 1024) {
-        const double v = (double)r[i];
-        s1 += v;
-        s2 += v * v;
-    }
-    __shared__ double b1[32], b2[32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    s1 = warp_sum(s1);
-    s2 = warp_sum(s2);
-    if (lane == 0) {
-        b1[wid] = s1;
-        b2[wid] = s2;
-    }
-    __syncthreads();
-    if (wid == 0) {
-        s1 = warp_sum(b1[lane]);
-        s2 = warp_sum(b2[lane]);
-        if (lane == 0) {
-            sc->sum_r = s1;
-            sc->rnorm = sqrt(s2);
-            sc->rss = s2;
-        }
-    }
-}
-
-cudaError_t launch_rstats(int dtype, const void *r, int64_t n, DevScalars *sc, cudaStream_t st)
-{
-    if (dtype == 0) k_rstats<double><<<1, 1024, 0, st>>>((const double *)r, n, sc);
-    else k_rstats<float><<<1, 1024, 0, st>>>((const float *)r, n, sc);
-    return cudaGetLastError();
-}
-
-// ----------------------------------------------------------------- record
-// Append the nonzero coefficients of lambda_k (ascending feature index, taken
-// from the ordered working list) to the CSC path; objective and intercept in
-// FP64: Q = rss/(2n) + lam alpha |b|_1 + lam (1-alpha)/2 |b|^2,
-// intercept = ybar - sum_j c_j b_j / s_j.
-__global__ void __launch_bounds__(1024) k_record(RecordArgs a, DevScalars *sc)
-{
-    __shared__ unsigned int wsum[33];
-    __shared__ double b1[32], b2[32], b3[32];
-    const int64_t w = (a.w_host >= 0) ? a.w_host : (int64_t)sc->w;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int64_t per = (w + 1023) / 1024;
-    const int64_t t0 = (int64_t)tid * per;
-    const int64_t t1 = (t0 + per < w) ? t0 + per : w;
-    auto bval = [&](int32_t j) -> double {
-        return a.beta_f64 ? ((const double *)a.beta)[j] : (double)((const float *)a.beta)[j];
-    };
-    unsigned int c = 0;
-    double l1 = 0.0, l2 = 0.0, cb = 0.0;
-    for (int64_t t = t0; t < t1; ++t) {
-        const int32_t j = a.idx[t];
-        const double b = bval(j);
-        if (b != 0.0) {
-            ++c;
-            l1 += fabs(b);
-            l2 += b * b;
-            cb += a.center[j] * (b / a.scale[j]);
-        }
-    }
-    unsigned int incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane == 31) wsum[wid] = incl;
-    l1 = warp_sum(l1);
-    l2 = warp_sum(l2);
-    cb = warp_sum(cb);
-    if (lane == 0) {
-        b1[wid] = l1;
-        b2[wid] = l2;
-        b3[wid] = cb;
-    }
-    __syncthreads();
-    if (wid == 0) {
-        const unsigned int v = wsum[lane];
-        unsigned int inc2 = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned int u = __shfl_up_sync(0xffffffffu, inc2, o);
-            if (lane >= o) inc2 += u;
-        }
-        wsum[lane] = inc2 - v;
-        if (lane == 31) wsum[32] = inc2;
-        l1 = warp_sum(b1[lane]);
-        l2 = warp_sum(b2[lane]);
-        cb = warp_sum(b3[lane]);
-        if (lane == 0) {
-            b1[0] = l1;
-            b2[0] = l2;
-            b3[0] = cb;
-        }
-    }
-    __syncthreads();
-    const int64_t base = a.col_ptr[a.k];
-    int64_t pos = base + wsum[wid] + incl - c;
-    for (int64_t t = t0; t < t1; ++t) {
-        const int32_t j = a.idx[t];
-        const double b = bval(j);
-        if (b != 0.0) {
-            if (pos < a.cap) {
-                a.row_idx[pos] = j;
-                a.val[pos] = b;
-                if (a.val_orig) a.val_orig[pos] = b / a.scale[j];
-            }
-            ++pos;
-        }
-    }
-    if (tid == 0) {
-        const int64_t nnz = wsum[32];
-        a.col_ptr[a.k + 1] = base + nnz;
-        if (base + nnz > a.cap) atomicOr(&sc->status, ST_CAPACITY);
-        a.loss[a.k] = sc->rss / (2.0 * (double)a.n) + a.lam * a.alpha * b1[0] +
-                      0.5 * a.lam * (1.0 - a.alpha) * b2[0];
-        a.intercept[a.k] = sc->ybar - b3[0];
-        sc->nnz_total = nnz;
-    }
-}
-
-cudaError_t launch_record(const RecordArgs &a, DevScalars *sc, cudaStream_t st)
-{
-    k_record<<<1, 1024, 0, st>>>(a, sc);
-    return cudaGetLastError();
 }
 
 }  // namespace bl

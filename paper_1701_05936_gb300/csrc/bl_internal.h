@@ -39,9 +39,9 @@ struct DevScalars {
 
 constexpr int CD_THREADS = 256;
 constexpr int MAX_WORKING = 8192;   // float/int8 designs
-constexpr int MAX_WORKING_F64 = 6144;
+constexpr int MAX_WORKING_F64 = 4096;
 constexpr int64_t MAX_N_F32 = 16384;
-constexpr int64_t MAX_N_F64 = 8192;
+constexpr int64_t MAX_N_F64 = 4096;
 constexpr int RESID_GROUPS = 64;
 constexpr uint64_t CD_TIME_LIMIT_NS = 20ull * 1000ull * 1000ull * 1000ull;  // 20 s per CD launch
 
@@ -92,9 +92,16 @@ cudaError_t launch_compact(const uint8_t *mask, int64_t p, int32_t *idx, int64_t
 cudaError_t launch_init_z(const double *xty, const uint8_t *keep, int64_t p, int64_t n, float *z,
                           cudaStream_t st);
 
-// Coordinate descent over idx[0..w), w = w_host if >= 0 else sc->w.
+// g_ref[t] = sum_i (x_ij - c_j) r_i for j = idx[t] in FP64 (r FP64 if r_f64,
+// else FP32), stored in the arithmetic type of the design.
+cudaError_t launch_gref(int dtype, const void *X, int64_t n, int64_t ldx, int64_t p, const double *center,
+                        const int32_t *idx, int64_t w_host, const DevScalars *scw, const void *r, int r_f64,
+                        void *gref, int num_sms, cudaStream_t st);
+
+// Coordinate descent over idx[0..w), w = w_host if >= 0 else sc->w, from the
+// reference gradients gref.  r (nullable) is decreased by the residual change.
 cudaError_t launch_cd(int dtype, const void *X, int64_t n, int64_t p, int64_t ldx, const void *cvec,
-                      const void *isvec, const int32_t *idx, int64_t w_host, double lam,
+                      const void *isvec, const int32_t *idx, int64_t w_host, const void *gref, double lam,
                       double alpha, void *beta, void *r, double eps, int64_t max_sweeps,
                       uint64_t time_limit_ns, DevScalars *sc, cudaStream_t st);
 
@@ -103,7 +110,7 @@ cudaError_t launch_cd(int dtype, const void *X, int64_t n, int64_t p, int64_t ld
 cudaError_t launch_residual(int dtype, const void *X, int64_t n, int64_t ldx, const double *center,
                             const double *inv_scale, const int32_t *idx, int64_t w_host,
                             const DevScalars *sc_w, const void *beta, const double *yc,
-                            double *partial, void *r_out, DevScalars *sc, cudaStream_t st);
+                            double *partial, void *r_out, double *r64, DevScalars *sc, cudaStream_t st);
 
 // Statistics (sum, norm) of a caller-provided residual.
 cudaError_t launch_rstats(int dtype, const void *r, int64_t n, DevScalars *sc, cudaStream_t st);
