@@ -36,6 +36,7 @@
 #ifndef BIGLASSO_GPU_H
 #define BIGLASSO_GPU_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -251,6 +252,39 @@ int bl_cd_active(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, in
 int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx,
                 const double *y, const bl_options *opt, const double *lambdas_in, int nlambda,
                 bl_path *out);
+
+/* ------------------------------------------------ allocation-free variant -- */
+
+/* Largest working set that bl_cd_active_noalloc accepts. */
+#define BL_NOALLOC_MAX_WORK 4096
+
+/* bl_cd_active for callers that cannot allocate device memory: a host
+ * application whose own allocator already owns all of the GPU's memory (for
+ * instance a serving process that reserves a fixed arena at start-up), or a
+ * latency-critical loop that cannot afford the device-wide synchronization a
+ * cudaMalloc or cudaFree implies.  The paper has no counterpart; this is an
+ * interface of the library only.
+ * Same computation, arguments and results as bl_cd_active, but without a
+ * bl_ctx (creating one allocates): work is enqueued on `stream`, a
+ * cudaStream_t of CUDA device `device` (NULL = legacy default stream), and
+ * the call synchronizes that stream before returning.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.  Its scratch is one
+ * file-scope device array of 3*8*BL_NOALLOC_MAX_WORK + 256 bytes (about 97 KB)
+ * that every GPU which loads the library holds until the process exits;
+ * n_work above BL_NOALLOC_MAX_WORK is rejected with BL_ERR_UNSUPPORTED and a
+ * message.  All calls share that one array, which keeps the last call's
+ * contents (the counters in it are cleared at the start of every call), so
+ * calls that overlap on the GPU -- on different streams or from different
+ * host threads -- race and must be serialized by the caller.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress with
+ * that device current); make that first call before any stream capture.
+ * err (nullable) receives a NUL-terminated message of at most err_len bytes
+ * when the call fails.  Errors: as bl_cd_active, plus BL_ERR_UNSUPPORTED for
+ * n_work > BL_NOALLOC_MAX_WORK. */
+int bl_cd_active_noalloc(int device, void *stream, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx,
+                         const double *center, const double *scale, const int32_t *work_idx, int64_t n_work,
+                         double lam, double alpha, void *beta, void *r, double eps, int64_t max_sweeps,
+                         int64_t *sweeps, char *err, size_t err_len);
 
 #ifdef __cplusplus
 }

@@ -93,6 +93,8 @@ def lib():
                                  C.POINTER(_i64)],
                 "bl_fit_path": [_vp, *X, _vp, C.POINTER(bl_options), C.POINTER(_dbl), _int,
                                 C.POINTER(bl_path)],
+                "bl_cd_active_noalloc": [_int, _vp, *X[:1], _int, _i64, _i64, _i64, _vp, _vp, _vp, _i64, _dbl,
+                                         _dbl, _vp, _vp, _dbl, _i64, C.POINTER(_i64), C.c_char_p, C.c_size_t],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -211,6 +213,21 @@ def bl_cd_active(ctx, X, n, center, scale, work_idx, lam, alpha, beta, r, eps, m
                             int(work_idx.numel()), float(lam), float(alpha), _ptr(beta), _ptr(r), float(eps),
                             int(max_sweeps), C.byref(sw))
     ctx.check(st, allow=(BL_ERR_NOT_CONVERGED,))
+    return sw.value, st
+
+
+def bl_cd_active_noalloc(device, stream, X, n, center, scale, work_idx, lam, alpha, beta, r, eps,
+                         max_sweeps=100_000, allow=(BL_ERR_NOT_CONVERGED,)):
+    """bl_cd_active without a context or any device allocation (see the header)."""
+    sw = C.c_int64()
+    err = C.create_string_buffer(512)
+    Xp, dt, n_, p_, ldx = design_args(X, n)
+    st = lib().bl_cd_active_noalloc(int(device), C.c_void_p(stream.cuda_stream if stream is not None else 0), Xp, dt,
+                                    n_, p_, ldx, _ptr(center), _ptr(scale), _ptr(work_idx), int(work_idx.numel()),
+                                    float(lam), float(alpha), _ptr(beta), _ptr(r), float(eps), int(max_sweeps),
+                                    C.byref(sw), err, 512)
+    if st != BL_OK and st not in allow:
+        raise BLError(st, err.value.decode())
     return sw.value, st
 
 

@@ -99,7 +99,8 @@ cudaError_t launch_gref(int dtype, const void *X, int64_t n, int64_t ldx, int64_
 // thread evaluates the same scalar update and writes the same b_j', so no
 // thread ever reads a shared-memory value another thread wrote; the only
 // cross-thread exchange is the reduction of the dot product.
-template <typename T, int NW, int RPT, int D>
+// WIDX: cvec/isvec are indexed by working-set position t instead of feature j.
+template <typename T, int NW, int RPT, int D, bool WIDX = false>
 __global__ void __launch_bounds__(32 * NW, 1)
     k_cd(const T *__restrict__ X, int64_t n, int64_t ldx, const typename elem<T>::acc *__restrict__ cvec,
          const typename elem<T>::acc *__restrict__ isvec, const int32_t *__restrict__ idx, int64_t w_host,
@@ -143,8 +144,8 @@ __global__ void __launch_bounds__(32 * NW, 1)
             continue;
         }
         idx_s[t] = j;
-        c_s[t] = cvec[j];
-        is_s[t] = isvec[j];
+        c_s[t] = cvec[WIDX ? (int64_t)t : (int64_t)j];
+        is_s[t] = isvec[WIDX ? (int64_t)t : (int64_t)j];
         g_s[t] = gref[t];
         beta_s[t] = beta[j];
     }
@@ -344,7 +345,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
     }
 }
 
-template <typename T, int NW, int RPT, int D>
+template <typename T, int NW, int RPT, int D, bool WIDX>
 static cudaError_t cd_launch(const T *X, int64_t n, int64_t ldx, const void *cvec, const void *isvec,
                              const int32_t *idx, int64_t w_host, int64_t cap, int64_t p, const void *gref, double lam,
                              double alpha, void *beta, void *r, double eps, int64_t max_sweeps, uint64_t tl,
@@ -353,7 +354,7 @@ static cudaError_t cd_launch(const T *X, int64_t n, int64_t ldx, const void *cve
     using A = typename elem<T>::acc;
     using R = typename elem<T>::res;
     const size_t smem = (size_t)cap * (3 * sizeof(A) + sizeof(R) + sizeof(int32_t) + sizeof(uint16_t));
-    auto kern = k_cd<T, NW, RPT, D>;
+    auto kern = k_cd<T, NW, RPT, D, WIDX>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<1, 32 * NW, smem, st>>>(X, n, ldx, (const A *)cvec, (const A *)isvec, idx, w_host, cap, p, (const A *)gref,
@@ -362,7 +363,7 @@ static cudaError_t cd_launch(const T *X, int64_t n, int64_t ldx, const void *cve
 }
 
 // Shape: one warp while the rows fit 8 chunks per lane, else 4 or 8 warps.
-template <typename T>
+template <typename T, bool WIDX = false>
 static cudaError_t cd_dispatch(const T *X, int64_t n, int64_t ldx, const void *cvec, const void *isvec,
                                const int32_t *idx, int64_t w_host, int64_t cap, int64_t p, const void *gref,
                                double lam, double alpha, void *beta, void *r, double eps, int64_t max_sweeps,
@@ -371,7 +372,7 @@ static cudaError_t cd_dispatch(const T *X, int64_t n, int64_t ldx, const void *c
     constexpr int VEC = elem<T>::VEC;
     const int64_t nch = (n + VEC - 1) / VEC;
 #define BL_CD(NW_, RPT_, D_) \
-    return cd_launch<T, NW_, RPT_, D_>(X, n, ldx, cvec, isvec, idx, w_host, cap, p, gref, lam, alpha, beta, r, eps, max_sweeps, tl, sc, st)
+    return cd_launch<T, NW_, RPT_, D_, WIDX>(X, n, ldx, cvec, isvec, idx, w_host, cap, p, gref, lam, alpha, beta, r, eps, max_sweeps, tl, sc, st)
     if (nch <= 32 * 1) BL_CD(1, 1, 4);
     if (nch <= 32 * 2) BL_CD(1, 2, 4);
     if (nch <= 32 * 4) BL_CD(1, 4, 3);
@@ -402,6 +403,21 @@ cudaError_t launch_cd(int dtype, const void *X, int64_t n, int64_t p, int64_t ld
     case 0: return cd_dispatch((const double *)X, n, ldx, cvec, isvec, idx, w_host, MAX_WORKING_F64, p, gref, lam, alpha, beta, r, eps, max_sweeps, time_limit_ns, sc, st);
     case 1: return cd_dispatch((const float *)X, n, ldx, cvec, isvec, idx, w_host, MAX_WORKING, p, gref, lam, alpha, beta, r, eps, max_sweeps, time_limit_ns, sc, st);
     case 3: return cd_dispatch((const int8_t *)X, n, ldx, cvec, isvec, idx, w_host, MAX_WORKING, p, gref, lam, alpha, beta, r, eps, max_sweeps, time_limit_ns, sc, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// The same kernel with c_j and 1/s_j supplied per working-set position and a
+// caller-chosen shared-memory capacity (used by the allocation-free entry).
+cudaError_t launch_cd_widx(int dtype, const void *X, int64_t n, int64_t p, int64_t ldx, const void *c_w,
+                           const void *is_w, const int32_t *idx, int64_t w, int64_t cap, const void *gref, double lam,
+                           double alpha, void *beta, void *r, double eps, int64_t max_sweeps, uint64_t time_limit_ns,
+                           DevScalars *sc, cudaStream_t st)
+{
+    switch (dtype) {
+    case 0: return cd_dispatch<double, true>((const double *)X, n, ldx, c_w, is_w, idx, w, cap, p, gref, lam, alpha, beta, r, eps, max_sweeps, time_limit_ns, sc, st);
+    case 1: return cd_dispatch<float, true>((const float *)X, n, ldx, c_w, is_w, idx, w, cap, p, gref, lam, alpha, beta, r, eps, max_sweeps, time_limit_ns, sc, st);
+    case 3: return cd_dispatch<int8_t, true>((const int8_t *)X, n, ldx, c_w, is_w, idx, w, cap, p, gref, lam, alpha, beta, r, eps, max_sweeps, time_limit_ns, sc, st);
     default: return cudaErrorInvalidValue;
     }
 }

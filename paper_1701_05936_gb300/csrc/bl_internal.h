@@ -105,6 +105,13 @@ cudaError_t launch_cd(int dtype, const void *X, int64_t n, int64_t p, int64_t ld
                       double alpha, void *beta, void *r, double eps, int64_t max_sweeps,
                       uint64_t time_limit_ns, DevScalars *sc, cudaStream_t st);
 
+// As launch_cd with c_w/is_w indexed by working-set position, w given by the
+// host and shared-memory capacity cap (cap >= w).
+cudaError_t launch_cd_widx(int dtype, const void *X, int64_t n, int64_t p, int64_t ldx, const void *c_w,
+                           const void *is_w, const int32_t *idx, int64_t w, int64_t cap, const void *gref,
+                           double lam, double alpha, void *beta, void *r, double eps, int64_t max_sweeps,
+                           uint64_t time_limit_ns, DevScalars *sc, cudaStream_t st);
+
 // r = yc - Xt b over the working set, in FP64, rounded into r_out; also the
 // residual statistics in sc.  partial: RESID_GROUPS * n doubles of scratch.
 cudaError_t launch_residual(int dtype, const void *X, int64_t n, int64_t ldx, const double *center,
