@@ -29,7 +29,7 @@ struct Workspace {
     size_t size = 0;
     int64_t n = 0, p = 0;
     double *center, *scale, *inv_scale, *xnorm, *xty, *xtxstar;
-    float *c32, *is32, *z;
+    float *c32, *is32, *xn32, *z;
     void *beta;
     uint8_t *keep, *safe, *working, *scan;
     int32_t *idx;
@@ -95,7 +95,7 @@ int ensure_ws(bl_ctx *ctx, int64_t n, int64_t p)
     const size_t n8 = align256((size_t)N * 8);
     const size_t idxb = align256((size_t)MAX_WORKING * 4);
     const size_t grefb = align256((size_t)MAX_WORKING * 8);
-    const size_t total = 6 * p8 + 3 * p4 + p8 + 4 * p1 + idxb + grefb + 4 * n8 + (size_t)RESID_GROUPS * n8 +
+    const size_t total = 6 * p8 + 4 * p4 + p8 + 4 * p1 + idxb + grefb + 4 * n8 + (size_t)RESID_GROUPS * n8 +
                          2 * align256(1024 * 8) + align256(sizeof(DevScalars));
     if (w.base) {
         cudaStreamSynchronize(ctx->stream);
@@ -123,6 +123,7 @@ int ensure_ws(bl_ctx *ctx, int64_t n, int64_t p)
     w.xtxstar = (double *)take(p8);
     w.c32 = (float *)take(p4);
     w.is32 = (float *)take(p4);
+    w.xn32 = (float *)take(p4);
     w.z = (float *)take(p4);
     w.beta = take(p8);
     w.keep = (uint8_t *)take(p1);
@@ -453,10 +454,10 @@ extern "C" int bl_kkt_check(bl_ctx *ctx, const void *X, int dtype, int64_t n, in
     Workspace &w = ctx->ws;
     LAUNCH(1, launch_rstats(dtype == BL_F64 ? BL_F64 : BL_F32, r, n, w.sc, ctx->stream));
     if ((st = reset_round(ctx))) return st;
-    CK(launch_derive(center, scale, p, w.inv_scale, w.c32, w.is32, ctx->stream));
+    CK(launch_derive(center, scale, p, w.inv_scale, w.c32, w.is32, ctx->stream, xnorm, w.xn32));
     ctx->kernels += 1;
-    ZpassArgs za{X, n, p, ldx, center, w.inv_scale, xnorm, r, lam, alpha, gamma_for(dtype, n),
-                 scan, safe ? safe : scan, working, z};
+    ZpassArgs za{X, n, p, ldx, center, w.inv_scale, xnorm, w.c32, w.is32, w.xn32, r, lam, alpha, gamma_for(dtype, n),
+                 zpass_reg_gamma(dtype, n), scan, safe ? safe : scan, working, z};
     (void)keep;
     int slot = tbegin(ctx, 7);
     LAUNCH(1, launch_zpass(dtype, za, w.sc, zpass_grid(dtype, n, ctx->num_sms), ctx->stream));
@@ -554,8 +555,8 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
     // one-time passes: y centring, standardization fused with x~'y, lambda_max
     int slot = tbegin(ctx, 0);
     LAUNCH(1, launch_center_y(y, n, w.yc, w.sc, s));
-    LAUNCH(1, launch_standardize(dtype, X, n, p, ldx, true, true, w.yc, w.sc, w.center, w.scale, w.inv_scale, w.c32,
-                          w.is32, w.xnorm, w.keep, w.xty, ctx->num_sms, s));
+    LAUNCH(1, launch_standardize(dtype, X, n, p, ldx, true, true, w.yc, w.sc, w.center, w.scale, w.inv_scale,
+                                 w.c32, w.is32, w.xnorm, w.keep, w.xty, ctx->num_sms, s, w.xn32));
     tend(ctx, slot, (double)n * p * es);
     slot = tbegin(ctx, 1);
     LAUNCH(2, launch_absmax(w.xty, w.keep, p, w.part_val, w.part_idx, w.sc, s));
@@ -604,6 +605,7 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
     const void *cvec = beta_f64 ? (const void *)w.center : (const void *)w.c32;
     const void *isvec = beta_f64 ? (const void *)w.inv_scale : (const void *)w.is32;
     const double gamma = gamma_for(dtype, n);
+    const double gamma_reg = zpass_reg_gamma(dtype, n);
     const int zgrid = zpass_grid(dtype, n, ctx->num_sms);
     const int64_t wcap = max_w_for(dtype);
     bool not_converged = false;
@@ -684,8 +686,8 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
                                       w.partial, w.r, w.r64, w.sc, s));
             tend(ctx, slot, 0.0);
             if ((st = reset_round(ctx))) return st;
-            ZpassArgs za{X, n, p, ldx, w.center, w.inv_scale, w.xnorm, w.r, lam, alpha, gamma,
-                         w.scan, w.safe, w.working, w.z};
+            ZpassArgs za{X, n, p, ldx, w.center, w.inv_scale, w.xnorm, w.c32, w.is32, w.xn32, w.r, lam, alpha,
+                         gamma, gamma_reg, w.scan, w.safe, w.working, w.z};
             int zslot = tbegin(ctx, 7);
             LAUNCH(1, launch_zpass(dtype, za, w.sc, zgrid, s));
             tend(ctx, zslot, 0.0);

@@ -163,17 +163,13 @@ __global__ void __launch_bounds__(32 * NW, 1)
     }
     const uint64_t t_start = globaltimer_ns();
     const int64_t nch = (n + VEC - 1) / VEC;
+    const int64_t nfull = n / VEC;             // chunks with all VEC rows valid
+    const int tail = (int)(n - nfull * VEC);   // valid rows in chunk nfull (0: none)
     A dr[RPT][VEC];
-    uint64_t vmask = 0;  // bit q*VEC+v: row valid
 #pragma unroll
-    for (int q = 0; q < RPT; ++q) {
-        const int64_t ch = (int64_t)q * NT + tid;
+    for (int q = 0; q < RPT; ++q)
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-            dr[q][v] = (A)0;
-            if (ch * VEC + v < n) vmask |= (1ull << (q * VEC + v));
-        }
-    }
+        for (int v = 0; v < VEC; ++v) dr[q][v] = (A)0;
 
     const A thr = (A)(lam * alpha);
     const A inv_den = (A)(1.0 / (1.0 + lam * (1.0 - alpha)));
@@ -208,16 +204,25 @@ __global__ void __launch_bounds__(32 * NW, 1)
                     const int tt = full ? (int)t : (int)act_s[t];
                     const A cj = c_s[tt], isj = is_s[tt], gj = g_s[tt];
                     const A old = (tt == prev_tt) ? prev_nb : (A)beta_s[tt];
+                    // x - c_j once per coordinate; rows of the one partial chunk
+                    // past n, and chunks past it, contribute 0
+                    A xd[RPT][VEC];
                     A acc[4] = {0, 0, 0, 0};
 #pragma unroll
                     for (int q = 0; q < RPT; ++q) {
+                        const int64_t ch = (int64_t)q * NT + tid;
                         A e[VEC];
                         unpack(buf[s][q], e);
+                        if (ch < nfull) {
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) {
-                            const A xd = ((vmask >> (q * VEC + v)) & 1ull) ? e[v] - cj : (A)0;
-                            acc[v & 3] = fma(xd, dr[q][v], acc[v & 3]);
+                            for (int v = 0; v < VEC; ++v) xd[q][v] = e[v] - cj;
+                        } else {
+                            const int nv = (ch == nfull) ? tail : 0;
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) xd[q][v] = (v < nv) ? e[v] - cj : (A)0;
                         }
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) acc[v & 3] = fma(xd[q][v], dr[q][v], acc[v & 3]);
                     }
                     A dot = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
                     if (NW > 1) {
@@ -231,19 +236,11 @@ __global__ void __launch_bounds__(32 * NW, 1)
                     const A zt = fma(gj - dot, isj * inv_n, old);
                     const A nb = soft_threshold(zt, thr) * inv_den;
                     const A d = nb - old;
-                    if (d != (A)0) {
-                        const A ds = d * isj;
+                    const A ds = d * isj;
 #pragma unroll
-                        for (int q = 0; q < RPT; ++q) {
-                            A e[VEC];
-                            unpack(buf[s][q], e);
+                    for (int q = 0; q < RPT; ++q)
 #pragma unroll
-                            for (int v = 0; v < VEC; ++v) {
-                                const A xd = ((vmask >> (q * VEC + v)) & 1ull) ? e[v] - cj : (A)0;
-                                dr[q][v] = fma(ds, xd, dr[q][v]);
-                            }
-                        }
-                    }
+                        for (int v = 0; v < VEC; ++v) dr[q][v] = fma(ds, xd[q][v], dr[q][v]);
                     beta_s[tt] = (R)nb;
                     prev_tt = tt;
                     prev_nb = nb;
@@ -375,7 +372,10 @@ static cudaError_t cd_dispatch(const T *X, int64_t n, int64_t ldx, const void *c
     return cd_launch<T, NW_, RPT_, D_, WIDX>(X, n, ldx, cvec, isvec, idx, w_host, cap, p, gref, lam, alpha, beta, r, eps, max_sweeps, tl, sc, st)
     if (nch <= 32 * 1) BL_CD(1, 1, 4);
     if (nch <= 32 * 2) BL_CD(1, 2, 4);
-    if (nch <= 32 * 4) BL_CD(1, 4, 3);
+    if (nch <= 32 * 4) {
+        if constexpr (VEC == 16) BL_CD(1, 4, 2);
+        else BL_CD(1, 4, 3);
+    }
     if constexpr (VEC == 4) {  // FP32: up to 16384 rows
         if (nch <= 32 * 8) BL_CD(1, 8, 2);
         if (nch <= 128 * 4) BL_CD(4, 4, 3);
@@ -383,8 +383,8 @@ static cudaError_t cd_dispatch(const T *X, int64_t n, int64_t ldx, const void *c
         if (nch <= 256 * 8) BL_CD(8, 8, 2);
         if (nch <= 256 * 16) BL_CD(8, 16, 1);
     } else if constexpr (VEC == 16) {  // int8: up to 16384 rows, 64 rows per thread
-        if (nch <= 128 * 4) BL_CD(4, 4, 3);
-        if (nch <= 256 * 4) BL_CD(8, 4, 3);
+        if (nch <= 128 * 4) BL_CD(4, 4, 2);
+        if (nch <= 256 * 4) BL_CD(8, 4, 2);
     } else {  // FP64: up to 4096 rows
         if (nch <= 32 * 8) BL_CD(1, 8, 1);
         if (nch <= 128 * 4) BL_CD(4, 4, 3);

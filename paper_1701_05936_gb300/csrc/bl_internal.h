@@ -56,11 +56,13 @@ cudaError_t launch_standardize(int dtype, const void *X, int64_t n, int64_t p, i
                                bool stats, bool xty_mode, const double *yc, const DevScalars *sc,
                                double *center, double *scale, double *inv_scale, float *c32,
                                float *is32, double *xnorm, uint8_t *keep, double *xty,
-                               int num_sms, cudaStream_t st);
+                               int num_sms, cudaStream_t st, float *xn32 = nullptr);
 
-// Derived per-feature vectors (1/s, FP32 copies) from given center/scale.
+// Derived per-feature vectors (1/s, FP32 copies) from given center/scale
+// (and the FP32 copy of xnorm when both xnorm and xn32 are given).
 cudaError_t launch_derive(const double *center, const double *scale, int64_t p, double *inv_scale,
-                          float *c32, float *is32, cudaStream_t st);
+                          float *c32, float *is32, cudaStream_t st, const double *xnorm = nullptr,
+                          float *xn32 = nullptr);
 
 cudaError_t launch_absmax(const double *xty, const uint8_t *keep, int64_t p, double *part_val,
                           long long *part_idx, DevScalars *sc, cudaStream_t st);
@@ -126,12 +128,15 @@ struct ZpassArgs {
     const void *X;
     int64_t n, p, ldx;
     const double *center, *inv_scale, *xnorm;
+    const float *c32, *is32, *xn32;  // FP32 copies (register-resident variant)
     const void *r;
-    double lam, alpha, gamma;
+    double lam, alpha, gamma, gamma_reg;
     const uint8_t *scan, *safe;
     uint8_t *working;
     float *z;
 };
+// Rounding-bound factor of the register-resident z pass (gamma_m + 8u).
+double zpass_reg_gamma(int dtype, int64_t n);
 cudaError_t launch_zpass(int dtype, const ZpassArgs &a, DevScalars *sc, int grid, cudaStream_t st);
 int zpass_grid(int dtype, int64_t n, int num_sms);  // resident blocks that fit at once
 size_t zpass_smem(int dtype, int64_t n);

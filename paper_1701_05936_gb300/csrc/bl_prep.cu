@@ -81,7 +81,8 @@ __global__ void __launch_bounds__(256)
                   const double *__restrict__ yc, const DevScalars *__restrict__ sc,
                   double *__restrict__ center, double *__restrict__ scale,
                   double *__restrict__ inv_scale, float *__restrict__ c32, float *__restrict__ is32,
-                  double *__restrict__ xnorm, uint8_t *__restrict__ keep, double *__restrict__ xty)
+                  double *__restrict__ xnorm, uint8_t *__restrict__ keep, double *__restrict__ xty,
+                  float *__restrict__ xn32)
 {
     using E = elem<T>;
     using A = typename E::acc;
@@ -144,7 +145,9 @@ __global__ void __launch_bounds__(256)
                 inv_scale[j] = isj;
                 c32[j] = (float)cj;
                 is32[j] = (float)isj;
-                if (xnorm) xnorm[j] = sqrt((double)n * (var + cj * cj));
+                const double xn = sqrt((double)n * (var + cj * cj));
+                if (xnorm) xnorm[j] = xn;
+                if (xn32) xn32[j] = (float)xn;
             } else {
                 cj = center[j];
                 sj = scale[j];
@@ -160,7 +163,7 @@ static cudaError_t standardize_t(const T *X, int64_t n, int64_t p, int64_t ldx, 
                                  bool xty_mode, const double *yc, const DevScalars *sc,
                                  double *center, double *scale, double *inv_scale, float *c32,
                                  float *is32, double *xnorm, uint8_t *keep, double *xty, int num_sms,
-                                 cudaStream_t st)
+                                 cudaStream_t st, float *xn32)
 {
     const int64_t warps_needed = p;
     int64_t blocks = (warps_needed + 7) / 8;
@@ -169,37 +172,39 @@ static cudaError_t standardize_t(const T *X, int64_t n, int64_t p, int64_t ldx, 
     if (blocks < 1) blocks = 1;
     if (stats && xty_mode)
         k_standardize<T, true, true><<<(int)blocks, 256, 0, st>>>(X, n, p, ldx, yc, sc, center, scale,
-                                                                 inv_scale, c32, is32, xnorm, keep, xty);
+                                                                 inv_scale, c32, is32, xnorm, keep, xty, xn32);
     else if (stats)
         k_standardize<T, true, false><<<(int)blocks, 256, 0, st>>>(X, n, p, ldx, yc, sc, center, scale,
-                                                                  inv_scale, c32, is32, xnorm, keep, xty);
+                                                                  inv_scale, c32, is32, xnorm, keep, xty, xn32);
     else
         k_standardize<T, false, true><<<(int)blocks, 256, 0, st>>>(X, n, p, ldx, yc, sc, center, scale,
-                                                                  inv_scale, c32, is32, xnorm, keep, xty);
+                                                                  inv_scale, c32, is32, xnorm, keep, xty, xn32);
     return cudaGetLastError();
 }
 
 cudaError_t launch_standardize(int dtype, const void *X, int64_t n, int64_t p, int64_t ldx, bool stats,
                                bool xty_mode, const double *yc, const DevScalars *sc, double *center,
                                double *scale, double *inv_scale, float *c32, float *is32,
-                               double *xnorm, uint8_t *keep, double *xty, int num_sms, cudaStream_t st)
+                               double *xnorm, uint8_t *keep, double *xty, int num_sms, cudaStream_t st,
+                               float *xn32)
 {
     switch (dtype) {
     case 0:
         return standardize_t((const double *)X, n, p, ldx, stats, xty_mode, yc, sc, center, scale,
-                             inv_scale, c32, is32, xnorm, keep, xty, num_sms, st);
+                             inv_scale, c32, is32, xnorm, keep, xty, num_sms, st, xn32);
     case 1:
         return standardize_t((const float *)X, n, p, ldx, stats, xty_mode, yc, sc, center, scale,
-                             inv_scale, c32, is32, xnorm, keep, xty, num_sms, st);
+                             inv_scale, c32, is32, xnorm, keep, xty, num_sms, st, xn32);
     case 3:
         return standardize_t((const int8_t *)X, n, p, ldx, stats, xty_mode, yc, sc, center, scale,
-                             inv_scale, c32, is32, xnorm, keep, xty, num_sms, st);
+                             inv_scale, c32, is32, xnorm, keep, xty, num_sms, st, xn32);
     default: return cudaErrorInvalidValue;
     }
 }
 
 __global__ void k_derive(const double *__restrict__ center, const double *__restrict__ scale,
-                         int64_t p, double *inv_scale, float *c32, float *is32)
+                         int64_t p, double *inv_scale, float *c32, float *is32,
+                         const double *__restrict__ xnorm, float *xn32)
 {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p;
          j += (int64_t)gridDim.x * blockDim.x) {
@@ -208,15 +213,17 @@ __global__ void k_derive(const double *__restrict__ center, const double *__rest
         inv_scale[j] = is;
         c32[j] = (float)center[j];
         is32[j] = (float)is;
+        if (xn32) xn32[j] = (float)xnorm[j];
     }
 }
 
 cudaError_t launch_derive(const double *center, const double *scale, int64_t p, double *inv_scale,
-                          float *c32, float *is32, cudaStream_t st)
+                          float *c32, float *is32, cudaStream_t st, const double *xnorm, float *xn32)
 {
     int64_t blocks = (p + 255) / 256;
     if (blocks > 4096) blocks = 4096;
-    k_derive<<<(int)blocks, 256, 0, st>>>(center, scale, p, inv_scale, c32, is32);
+    k_derive<<<(int)blocks, 256, 0, st>>>(center, scale, p, inv_scale, c32, is32, xnorm,
+                                          xnorm ? xn32 : nullptr);
     return cudaGetLastError();
 }
 

@@ -9,6 +9,8 @@
 #include "bl_device.cuh"
 #include "bl_internal.h"
 
+#include <cmath>
+
 namespace bl {
 
 template <typename T, int U>
@@ -91,7 +93,175 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// ------------------------------------------------ register-resident variant
+// For n <= 32 RPL VEC: lane l keeps the residual chunks l, l+32, ... in
+// registers for the whole launch (no shared-memory traffic), each warp owns a
+// contiguous range of columns, the scan flags of 32 columns are read with one
+// coalesced load and a ballot, the loads of the next scanned column are issued
+// before the current one is reduced, and the epilogue (z_j, KKT test) runs in
+// parallel: lane k finishes column jb + k of its 32-column group.  The
+// epilogue is in the design's arithmetic type; its rounding is covered by the
+// bound passed in `gam` (gamma_m plus 8 unit roundoffs) and the 8u terms below.
+template <typename T, int RPL>
+__global__ void __launch_bounds__(256, 2)
+    k_zpass_reg(const T *__restrict__ X, int64_t n, int64_t p, int64_t ldx,
+                const typename elem<T>::acc *__restrict__ cvec, const typename elem<T>::acc *__restrict__ isvec,
+                const typename elem<T>::acc *__restrict__ xnvec, const typename elem<T>::res *__restrict__ r,
+                const DevScalars *__restrict__ sc_in, double lam, double alpha, double gam,
+                const uint8_t *__restrict__ scan, const uint8_t *__restrict__ safe, uint8_t *__restrict__ working,
+                float *__restrict__ z, DevScalars *sc)
+{
+    using E = elem<T>;
+    using A = typename E::acc;
+    using V = typename E::vec;
+    constexpr int VEC = E::VEC;
+    constexpr A U = sizeof(A) == 4 ? (A)5.9604644775390625e-08 : (A)1.1102230246251565e-16;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nch = (n + VEC - 1) / VEC;
+    const int64_t nfull = n / VEC;
+    const int tail = (int)(n - nfull * VEC);
+    A rr[RPL][VEC];
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+        const int64_t ch = (int64_t)lane + 32 * q;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            const int64_t row = ch * VEC + v;
+            rr[q][v] = (row < n) ? (A)r[row] : (A)0;
+        }
+    }
+    const A sum_r = (A)sc_in->sum_r, rnorm = (A)sc_in->rnorm;
+    const A thr = (A)(lam * alpha), inv_n = (A)(1.0 / (double)n), g = (A)gam;
+
+    auto load = [&](V (&b)[RPL], int64_t j) {
+        const V *colv = reinterpret_cast<const V *>(X + j * ldx);
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            const int64_t ch = (int64_t)lane + 32 * q;
+            b[q] = (ch < nch) ? ld_stream(colv + ch) : V{};
+        }
+    };
+    auto dot = [&](const V (&b)[RPL]) -> A {
+        A a0 = 0, a1 = 0;
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            const int64_t ch = (int64_t)lane + 32 * q;
+            A e[VEC];
+            unpack(b[q], e);
+            if (ch >= nfull) {  // the partial chunk: rows past n may hold anything
+                const int nv = (ch == nfull) ? tail : 0;
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) e[v] = (v < nv) ? e[v] : (A)0;
+            }
+#pragma unroll
+            for (int v = 0; v < VEC; v += 2) {
+                a0 = fma(e[v], rr[q][v], a0);
+                if (v + 1 < VEC) a1 = fma(e[v + 1], rr[q][v + 1], a1);
+            }
+        }
+        return warp_sum(a0 + a1);
+    };
+
+    const int64_t per = (p + nw - 1) / nw;
+    const int64_t j0 = gw * per;
+    const int64_t j1 = (j0 + per < p) ? j0 + per : p;
+    unsigned int viol = 0, cols = 0;
+    for (int64_t jb = j0; jb < j1; jb += 32) {
+        const int64_t jl = jb + lane;
+        const bool in = jl < j1 && scan[jl] != 0;
+        unsigned int bal = __ballot_sync(0xffffffffu, in);
+        A mine = 0;
+        if (bal) {
+            V b0[RPL], b1[RPL];
+            int k = __ffs(bal) - 1;
+            bal &= bal - 1;
+            load(b0, jb + k);
+            for (;;) {
+                int k1 = -1;
+                if (bal) {
+                    k1 = __ffs(bal) - 1;
+                    bal &= bal - 1;
+                    load(b1, jb + k1);
+                }
+                const A d0 = dot(b0);
+                if (lane == k) mine = d0;
+                if (k1 < 0) break;
+                int k2 = -1;
+                if (bal) {
+                    k2 = __ffs(bal) - 1;
+                    bal &= bal - 1;
+                    load(b0, jb + k2);
+                }
+                const A d1 = dot(b1);
+                if (lane == k1) mine = d1;
+                if (k2 < 0) break;
+                k = k2;
+            }
+        }
+        if (in) {
+            const A c = cvec[jl], is = isvec[jl];
+            const A f = inv_n * is;
+            const A zj = (mine - c * sum_r) * f;
+            z[jl] = (float)zj;
+            ++cols;
+            if (safe[jl] && !working[jl]) {
+                const A tau = g * xnvec[jl] * rnorm * f * (A)1.01 + (A)8 * U * (fabs(c * sum_r) * f + fabs(zj) + thr);
+                if (fabs(zj) > thr - tau) {
+                    working[jl] = 1;
+                    ++viol;
+                }
+            }
+        }
+    }
+    viol = warp_sum(viol);
+    cols = warp_sum(cols);
+    if (lane == 0) {
+        if (viol) atomicAdd(&sc->n_viol, (unsigned long long)viol);
+        if (cols) atomicAdd(&sc->n_cols, (unsigned long long)cols);
+    }
+}
+
 template <typename T> constexpr int zpass_unroll() { return sizeof(T) == 1 ? 4 : 8; }
+
+template <typename T, int RPL>
+static cudaError_t zpass_reg_t(const ZpassArgs &a, DevScalars *sc, int num_sms, cudaStream_t st)
+{
+    using A = typename elem<T>::acc;
+    using R = typename elem<T>::res;
+    auto kern = k_zpass_reg<T, RPL>;
+    static int per_sm = 0;  // resident blocks per SM, looked up once per instantiation
+    if (per_sm == 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, 256, 0) != cudaSuccess || v < 1) v = 1;
+        per_sm = v;
+    }
+    const A *cv = sizeof(A) == 8 ? (const A *)a.center : (const A *)a.c32;
+    const A *iv = sizeof(A) == 8 ? (const A *)a.inv_scale : (const A *)a.is32;
+    const A *xv = sizeof(A) == 8 ? (const A *)a.xnorm : (const A *)a.xn32;
+    kern<<<num_sms * per_sm, 256, 0, st>>>((const T *)a.X, a.n, a.p, a.ldx, cv, iv, xv, (const R *)a.r, sc, a.lam,
+                                           a.alpha, a.gamma_reg, a.scan, a.safe, a.working, a.z, sc);
+    return cudaGetLastError();
+}
+
+// Register-resident pass when the residual fits 8 chunks per lane.
+static bool zpass_reg_ok(int dtype, int64_t n)
+{
+    if (dtype == 3) return false;
+    const int vec = (int)(16 / elem_size(dtype));
+    return (n + vec - 1) / vec <= 32 * 8;
+}
+
+double zpass_reg_gamma(int dtype, int64_t n)
+{
+    const int vec = (int)(16 / elem_size(dtype));
+    const int64_t nch = (n + vec - 1) / vec;
+    const int64_t rpl = (nch + 31) / 32;
+    const double u = (dtype == 0) ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
+    const double m = (double)(rpl * vec / 2 + 1 + 5);  // two chains of rpl*vec/2, one add, 5 shuffle levels
+    return m * u / (1.0 - m * u) + 8.0 * u;
+}
 
 template <typename T>
 static cudaError_t zpass_t(const ZpassArgs &a, DevScalars *sc, int grid, cudaStream_t st)
@@ -148,6 +318,26 @@ int zpass_grid(int dtype, int64_t n, int num_sms)
 
 cudaError_t launch_zpass(int dtype, const ZpassArgs &a, DevScalars *sc, int grid, cudaStream_t st)
 {
+    if (zpass_reg_ok(dtype, a.n) && a.c32 && a.is32 && a.xn32) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int vec = (int)(16 / elem_size(dtype));
+        const int64_t rpl = ((a.n + vec - 1) / vec + 31) / 32;
+#define BL_ZR(T_, R_) return zpass_reg_t<T_, R_>(a, sc, sms, st)
+        if (dtype == 1) {
+            if (rpl <= 1) BL_ZR(float, 1);
+            if (rpl <= 2) BL_ZR(float, 2);
+            if (rpl <= 4) BL_ZR(float, 4);
+            BL_ZR(float, 8);
+        } else {
+            if (rpl <= 1) BL_ZR(double, 1);
+            if (rpl <= 2) BL_ZR(double, 2);
+            if (rpl <= 4) BL_ZR(double, 4);
+            BL_ZR(double, 8);
+        }
+#undef BL_ZR
+    }
     switch (dtype) {
     case 0: return zpass_t<double>(a, sc, grid, st);
     case 1: return zpass_t<float>(a, sc, grid, st);

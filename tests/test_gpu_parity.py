@@ -179,12 +179,15 @@ def test_kkt_check_matches_oracle_within_rounding_bound(ctx, which):
     sc = scan.cpu().numpy().astype(bool)
     zg = z.cpu().numpy()
     assert np.all(zg[~sc] == 7.0)                                       # untouched outside scan
+    # the kernels' documented bound: gamma_m ||x_j|| ||r|| / (n s_j) for the FP32
+    # (or FP64) accumulation, plus 8u (|z_j| + lam alpha) for the epilogue
     u = 2.0 ** -24 if prob.dtype != "f64" else 2.0 ** -53
     m = (n // (16 // prob.X.itemsize) + 31) // 32 * (16 // prob.X.itemsize) + 16 + 5
-    gam = m * u / (1 - m * u)
+    gam = m * u / (1 - m * u) + 8 * u
     xnorm = np.sqrt((o["Xd"] ** 2).sum(axis=1))
     with np.errstate(divide="ignore", invalid="ignore"):
-        tau = gam * xnorm * np.linalg.norm(r_stored) / (n * o["s"]) * 1.01 + 1e-7 * np.abs(oz) + 1e-12
+        tau = gam * xnorm * np.linalg.norm(r_stored) / (n * o["s"]) * 1.01 + 8 * u * (np.abs(oz) + lam) \
+            + 1e-7 * np.abs(oz) + 1e-12
     assert np.all(np.abs(zg[sc] - oz[sc]) <= tau[sc] + 1e-7 * np.abs(oz[sc]))
     wk = working.cpu().numpy().astype(bool)
     cand = sc & (work_np == 0)
