@@ -342,6 +342,281 @@ __global__ void __launch_bounds__(32 * NW, 1)
     }
 }
 
+// Ring-staged variant: the columns of the next S coordinates stream into a
+// ring of S shared-memory stages by 1-D TMA bulk copies (one elected thread
+// issues them, completion on one mbarrier per stage), so the loads of a
+// coordinate are issued S coordinates ahead with no register cost.  Each
+// wait is bounded by the GPU wall clock; on expiry the kernel raises
+// ST_TIMEOUT, waits (bounded) for the copies it has in flight and returns.
+// Arithmetic and sweep structure are those of k_cd.
+constexpr uint64_t RING_WAIT_NS = 1000ull * 1000ull * 1000ull;  // 1 s per stage wait
+
+template <typename T, int NW, int RPT, bool WIDX = false>
+__global__ void __launch_bounds__(32 * NW, 1)
+    k_cd_ring(const T *__restrict__ X, int64_t n, int64_t ldx, const typename elem<T>::acc *__restrict__ cvec,
+              const typename elem<T>::acc *__restrict__ isvec, const int32_t *__restrict__ idx, int64_t w_host,
+              int64_t cap, int64_t p, const typename elem<T>::acc *__restrict__ gref, double lam, double alpha,
+              typename elem<T>::res *beta, typename elem<T>::res *r_io, double eps, int64_t max_sweeps,
+              uint64_t time_limit_ns, DevScalars *sc, int S, uint32_t stage_bytes, uint32_t copy_bytes,
+              uint32_t ring_off)
+{
+    using E = elem<T>;
+    using A = typename E::acc;
+    using R = typename E::res;
+    using V = typename E::vec;
+    constexpr int VEC = E::VEC;
+    constexpr int NT = 32 * NW;
+    static_assert(RPT * VEC <= 64, "at most 64 rows per thread");
+    constexpr A RES_FLOOR = sizeof(A) == 4 ? (A)4.76837158203125e-07 : (A)8.881784197001252e-16;
+
+    const int64_t w = (w_host >= 0) ? w_host : (int64_t)sc->w;
+    if (w > cap) {
+        if (threadIdx.x == 0) atomicOr(&sc->status, ST_WORKING_TOO_BIG);
+        return;
+    }
+    extern __shared__ __align__(128) unsigned char smem[];
+    A *c_s = reinterpret_cast<A *>(smem);
+    A *is_s = c_s + cap;
+    A *g_s = is_s + cap;
+    R *beta_s = reinterpret_cast<R *>(g_s + cap);
+    int32_t *idx_s = reinterpret_cast<int32_t *>(beta_s + cap);
+    uint16_t *act_s = reinterpret_cast<uint16_t *>(idx_s + cap);
+    unsigned char *ring = smem + ring_off;                                        // S stages
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(ring + (size_t)S * stage_bytes);  // S barriers
+    __shared__ A red[2][NW];
+    __shared__ unsigned int scan_s[NW + 1];
+    __shared__ int flag_s;
+
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) {
+        flag_s = 0;
+        for (int k = 0; k < S; ++k) mbar_init(smem_u32(&mbar[k]), 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    for (int64_t t = tid; t < w; t += NT) {
+        const int32_t j = idx[t];
+        if (j < 0 || (int64_t)j >= p) {
+            flag_s = 1;
+            continue;
+        }
+        idx_s[t] = j;
+        c_s[t] = cvec[WIDX ? (int64_t)t : (int64_t)j];
+        is_s[t] = isvec[WIDX ? (int64_t)t : (int64_t)j];
+        g_s[t] = gref[t];
+        beta_s[t] = beta[j];
+    }
+    __syncthreads();
+    if (flag_s) {
+        if (tid == 0) atomicOr(&sc->status, ST_BAD_INDEX);
+        return;
+    }
+    {
+        const uint32_t col_bytes = (uint32_t)(((uint64_t)n * sizeof(T) + 15) & ~(uint64_t)15);
+        for (int64_t t = tid; t < w; t += NT) {
+            const T *col = X + (int64_t)idx_s[t] * ldx;
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(col), "r"(col_bytes) : "memory");
+        }
+    }
+    const uint64_t t_start = globaltimer_ns();
+    const int64_t nch = (n + VEC - 1) / VEC;
+    const int64_t nfull = n / VEC;
+    const int tail = (int)(n - nfull * VEC);
+    A dr[RPT][VEC];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) dr[q][v] = (A)0;
+
+    const A thr = (A)(lam * alpha);
+    const A inv_den = (A)(1.0 / (1.0 + lam * (1.0 - alpha)));
+    const A inv_n = (A)(1.0 / (double)n);
+    const A epsA = (A)eps;
+    int parity = 0;
+    int64_t sweeps = 0;
+    unsigned long long updates = 0;
+    int status = 0;
+    int prev_tt = -1;
+    A prev_nb = 0;
+    uint32_t seq = 0;  // coordinates consumed so far (the same in every thread)
+
+    auto issue = [&](uint32_t gs, int32_t j) {  // thread 0 only
+        const int st = (int)(gs % (uint32_t)S);
+        const uint32_t bar = smem_u32(&mbar[st]);
+        fence_proxy_async_smem();
+        mbar_expect_tx(bar, copy_bytes);
+        bulk_g2s(smem_u32(ring + (size_t)st * stage_bytes), X + (int64_t)j * ldx, copy_bytes, bar);
+    };
+
+    // returns false when a stage wait timed out (uniform across the block)
+    auto sweep = [&](bool full, int64_t len, bool &moved, bool &newnz) -> bool {
+        if (tid == 0)
+            for (int64_t k = 0; k < len && k < S; ++k) issue(seq + (uint32_t)k, idx_s[full ? (int)k : (int)act_s[k]]);
+        for (int64_t t = 0; t < len; ++t) {
+            const uint32_t gs = seq + (uint32_t)t;
+            const int st = (int)(gs % (uint32_t)S);
+            const bool ok = mbar_wait_bounded(smem_u32(&mbar[st]), (gs / (uint32_t)S) & 1u, RING_WAIT_NS);
+            bool all_ok;
+            if (NW == 1) {
+                all_ok = __all_sync(0xffffffffu, ok);
+            } else {
+                all_ok = __syncthreads_and(ok);
+            }
+            if (!all_ok) {
+                // drain: copies for gs .. min(len, t + S) - 1 may be in flight
+                if (tid == 0) {
+                    const int64_t last = (t + S < len) ? t + S : len;
+                    for (int64_t u = t; u < last; ++u) {
+                        const uint32_t g2 = seq + (uint32_t)u;
+                        mbar_wait_bounded(smem_u32(&mbar[g2 % (uint32_t)S]), (g2 / (uint32_t)S) & 1u, RING_WAIT_NS);
+                    }
+                }
+                __syncthreads();
+                return false;
+            }
+            const int tt = full ? (int)t : (int)act_s[t];
+            const A cj = c_s[tt], isj = is_s[tt], gj = g_s[tt];
+            const A old = (tt == prev_tt) ? prev_nb : (A)beta_s[tt];
+            const V *stage = reinterpret_cast<const V *>(ring + (size_t)st * stage_bytes);
+            A xd[RPT][VEC];
+            A acc[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) {
+                const int64_t ch = (int64_t)q * NT + tid;
+                A e[VEC];
+                if (ch < nch) unpack(stage[ch], e);
+                if (ch < nfull) {
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) xd[q][v] = e[v] - cj;
+                } else {
+                    const int nv = (ch == nfull) ? tail : 0;
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) xd[q][v] = (v < nv) ? e[v] - cj : (A)0;
+                }
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) acc[v & 3] = fma(xd[q][v], dr[q][v], acc[v & 3]);
+            }
+            A dot = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
+            if (NW > 1) {
+                if (lane == 0) red[parity][wid] = dot;
+                __syncthreads();  // also: every thread has read this stage
+                dot = 0;
+#pragma unroll
+                for (int k = 0; k < NW; ++k) dot += red[parity][k];
+                parity ^= 1;
+            } else {
+                __syncwarp();     // every lane has read this stage
+            }
+            if (tid == 0 && t + S < len) issue(gs + (uint32_t)S, idx_s[full ? (int)(t + S) : (int)act_s[t + S]]);
+            const A zt = fma(gj - dot, isj * inv_n, old);
+            const A nb = soft_threshold(zt, thr) * inv_den;
+            const A d = nb - old;
+            const A ds = d * isj;
+#pragma unroll
+            for (int q = 0; q < RPT; ++q)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) dr[q][v] = fma(ds, xd[q][v], dr[q][v]);
+            beta_s[tt] = (R)nb;
+            prev_tt = tt;
+            prev_nb = nb;
+            const A tol = fmax(epsA, RES_FLOOR * (fabs(zt) + fabs(nb)));
+            moved |= (fabs(d) >= tol);
+            newnz |= (old == (A)0 && fabs(nb) >= tol);
+            ++updates;
+        }
+        seq += (uint32_t)len;
+        return true;
+    };
+
+    auto out_of_time = [&]() -> bool {
+        __syncthreads();
+        if (tid == 0) flag_s = (globaltimer_ns() - t_start) > time_limit_ns;
+        __syncthreads();
+        return flag_s != 0;
+    };
+
+    for (;;) {
+        bool moved = false, newnz = false;
+        if (!sweep(true, w, moved, newnz)) {
+            status = ST_TIMEOUT;
+            break;
+        }
+        ++sweeps;
+        if (!moved && !newnz) break;
+        if (sweeps >= max_sweeps) {
+            status = ST_NOT_CONVERGED;
+            break;
+        }
+        if (out_of_time()) {
+            status = ST_TIMEOUT;
+            break;
+        }
+        const int64_t per = (w + NT - 1) / NT;
+        const int64_t b0 = (int64_t)tid * per;
+        const int64_t b1 = (b0 + per < w) ? b0 + per : w;
+        unsigned int c = 0;
+        for (int64_t t = b0; t < b1; ++t) c += (beta_s[t] != (R)0);
+        unsigned int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) scan_s[wid] = incl;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned int a = 0;
+            for (int k = 0; k < NW; ++k) {
+                const unsigned int v = scan_s[k];
+                scan_s[k] = a;
+                a += v;
+            }
+            scan_s[NW] = a;
+        }
+        __syncthreads();
+        unsigned int pos = scan_s[wid] + incl - c;
+        for (int64_t t = b0; t < b1; ++t)
+            if (beta_s[t] != (R)0) act_s[pos++] = (uint16_t)t;
+        const int64_t na = scan_s[NW];
+        __syncthreads();
+        for (;;) {
+            bool mv = false, nz = false;
+            if (!sweep(false, na, mv, nz)) {
+                status = ST_TIMEOUT;
+                break;
+            }
+            ++sweeps;
+            if (!mv) break;
+            if (sweeps >= max_sweeps) {
+                status = ST_NOT_CONVERGED;
+                break;
+            }
+            if (out_of_time()) {
+                status = ST_TIMEOUT;
+                break;
+            }
+        }
+        if (status) break;
+    }
+    for (int64_t t = tid; t < w; t += NT) beta[idx_s[t]] = beta_s[t];
+    if (r_io) {
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int64_t ch = (int64_t)q * NT + tid;
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                const int64_t row = ch * VEC + v;
+                if (row < n) r_io[row] = (R)((A)r_io[row] - dr[q][v]);
+            }
+        }
+    }
+    if (tid == 0) {
+        sc->sweeps += (unsigned long long)sweeps;
+        sc->cd_updates += updates;
+        if (status) atomicOr(&sc->status, status);
+    }
+}
+
 template <typename T, int NW, int RPT, int D, bool WIDX>
 static cudaError_t cd_launch(const T *X, int64_t n, int64_t ldx, const void *cvec, const void *isvec,
                              const int32_t *idx, int64_t w_host, int64_t cap, int64_t p, const void *gref, double lam,
@@ -350,7 +625,30 @@ static cudaError_t cd_launch(const T *X, int64_t n, int64_t ldx, const void *cve
 {
     using A = typename elem<T>::acc;
     using R = typename elem<T>::res;
-    const size_t smem = (size_t)cap * (3 * sizeof(A) + sizeof(R) + sizeof(int32_t) + sizeof(uint16_t));
+    const size_t meta = (size_t)cap * (3 * sizeof(A) + sizeof(R) + sizeof(int32_t) + sizeof(uint16_t));
+    {
+        // ring-staged kernel when at least 4 column stages fit beside the metadata
+        const size_t ring_off = (meta + 127) & ~(size_t)127;
+        // copy n*sizeof(T) rounded up to 16 bytes (never past the column's ldx
+        // extent); stages are spaced 128 bytes apart
+        const uint32_t copy_bytes = (uint32_t)(((uint64_t)n * sizeof(T) + 15) & ~(uint64_t)15);
+        const uint32_t stage_bytes = (copy_bytes + 127u) & ~127u;
+        const size_t budget = 227 * 1024 - 1024;  // keep room for static shared memory
+        int S = 0;
+        if (budget > ring_off) S = (int)((budget - ring_off) / (stage_bytes + 8));
+        if (S > 16) S = 16;
+        if (S >= 4) {
+            const size_t smem_r = ring_off + (size_t)S * stage_bytes + (size_t)S * 8;
+            auto kr = k_cd_ring<T, NW, RPT, WIDX>;
+            cudaError_t e = cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
+            if (e != cudaSuccess) return e;
+            kr<<<1, 32 * NW, smem_r, st>>>(X, n, ldx, (const A *)cvec, (const A *)isvec, idx, w_host, cap, p,
+                                          (const A *)gref, lam, alpha, (R *)beta, (R *)r, eps, max_sweeps, tl, sc, S,
+                                          stage_bytes, copy_bytes, (uint32_t)ring_off);
+            return cudaGetLastError();
+        }
+    }
+    const size_t smem = meta;
     auto kern = k_cd<T, NW, RPT, D, WIDX>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
