@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="a small workload for profiling runs")
+    ap.add_argument("--cd-mode", default="covariance", choices=["covariance", "residual"],
+                    help="coordinate-descent form of the timed (chosen) path")
+    ap.add_argument("--plain-steps", type=int, default=2,
+                    help="steps of the plain form (residual-update CD) timed for comparison; 0 = skip")
     return ap.parse_args()
 
 
@@ -212,7 +216,8 @@ def run_ours(args):
     X = torch.from_numpy(prob.X).to(dev)
     y = torch.from_numpy(prob.y).to(dev)
     ctx = bl.Context(local)
-    kw = dict(alpha=prob.alpha, ratio=prob.ratio, nlambda=prob.nlambda, eps=prob.eps)
+    mode = bl.BL_CD_COVARIANCE if args.cd_mode == "covariance" else bl.BL_CD_RESIDUAL
+    kw = dict(alpha=prob.alpha, ratio=prob.ratio, nlambda=prob.nlambda, eps=prob.eps, cd_mode=mode)
 
     def barrier():
         if world > 1:
@@ -270,6 +275,27 @@ def run_ours(args):
         e2e_ms = float(t.item())
     e2e_value = world * e2e_steps / (e2e_ms / 1e3)
 
+    # the plain form: the same path with residual-update CD, for comparison
+    plain = None
+    if args.plain_steps > 0 and mode != bl.BL_CD_RESIDUAL:
+        kw_p = dict(kw, cd_mode=bl.BL_CD_RESIDUAL)
+        bl.bl_fit_path(ctx, X, prob.n, y, **kw_p)
+        barrier()
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(args.plain_steps):
+            resp = bl.bl_fit_path(ctx, X, prob.n, y, **kw_p)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        pms = p0.elapsed_time(p1) / args.plain_steps
+        Bc = bl.path_dense(res, prob.p)
+        Bp = bl.path_dense(resp, prob.p)
+        plain = {"form": "residual-update CD (plain)", "value": world / (pms / 1e3), "unit": "paths/s",
+                 "ms_per_step": pms, "steps": args.plain_steps,
+                 "chosen_over_plain": (pms / (ms_all / args.steps)),
+                 "max_abs_coef_diff_chosen_vs_plain": float((Bc - Bp).abs().max())}
+
     z = tim["zpass"]
     peaks, which = measured_peaks()
     achieved = (z["bytes"] / 1e9) / (z["ms"] / 1e3) if z["ms"] > 0 else 0.0
@@ -302,6 +328,8 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": "paths/s", "h2d_bytes_per_step": int(prob.X.nbytes + prob.y.nbytes),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(tim["kernel_launches"]), "clocks": clk, "cd": cd_info,
+        "chosen_form": "covariance-form CD" if mode == bl.BL_CD_COVARIANCE else "residual-update CD",
+        "plain_form": plain,
         "kernel_ms_per_step": breakdown, "status": res["status"],
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -57,6 +57,12 @@ typedef enum {
 typedef enum { BL_F64 = 0, BL_F32 = 1, BL_BF16 = 2, BL_I8 = 3 } bl_dtype;
 
 typedef enum {
+    BL_CD_RESIDUAL = 0,   /* CD with residual updates (Sec. 3.1.1): r -= delta xt_j */
+    BL_CD_COVARIANCE = 1  /* the same cyclic CD with the gradient updated through the
+                             working set's correlation matrix xt_W'xt_W/n */
+} bl_cd_mode;
+
+typedef enum {
     BL_SCREEN_NONE = 0,      /* every kept feature is scanned and enters CD */
     BL_SCREEN_SSR = 1,       /* strong rule + KKT check over all features */
     BL_SCREEN_SSR_BEDPP = 2  /* hybrid rule of Sec. 2.2 (default) */
@@ -76,7 +82,7 @@ typedef struct {
     double lambda_min_ratio; /* grid end lambda_min/lambda_max, 0 < ratio < 1 */
     int64_t max_sweeps;      /* cap on CD sweeps per lambda (e.g. 100000) */
     int32_t screen;          /* bl_screen_rule */
-    int32_t reserved;
+    int32_t cd_mode;         /* bl_cd_mode (0 = residual updates) */
 } bl_options;
 
 /* Outputs of bl_fit_path.  Pointers marked device are caller-allocated device

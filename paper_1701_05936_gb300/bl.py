@@ -26,6 +26,7 @@ BL_OK, BL_ERR_ARG, BL_ERR_CUDA, BL_ERR_OOM = 0, -1, -2, -3
 BL_ERR_NOT_CONVERGED, BL_ERR_TIMEOUT, BL_ERR_UNSUPPORTED, BL_ERR_CAPACITY = -4, -5, -6, -7
 BL_F64, BL_F32, BL_BF16, BL_I8 = 0, 1, 2, 3
 BL_SCREEN_NONE, BL_SCREEN_SSR, BL_SCREEN_SSR_BEDPP = 0, 1, 2
+BL_CD_RESIDUAL, BL_CD_COVARIANCE = 0, 1
 KINDS = ["standardize", "lambda_max", "bedpp_init", "screen", "compact", "cd", "residual", "zpass", "record",
          "gref"]
 
@@ -42,7 +43,7 @@ class BLError(RuntimeError):
 
 class bl_options(C.Structure):
     _fields_ = [("alpha", C.c_double), ("eps", C.c_double), ("lambda_min_ratio", C.c_double),
-                ("max_sweeps", C.c_int64), ("screen", C.c_int32), ("reserved", C.c_int32)]
+                ("max_sweeps", C.c_int64), ("screen", C.c_int32), ("cd_mode", C.c_int32)]
 
 
 class bl_path(C.Structure):
@@ -232,7 +233,7 @@ def bl_cd_active_noalloc(device, stream, X, n, center, scale, work_idx, lam, alp
 
 
 def bl_fit_path(ctx, X, n, y, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, lambdas=None,
-                screen=BL_SCREEN_SSR_BEDPP, max_sweeps=100_000, nnz_capacity=None):
+                screen=BL_SCREEN_SSR_BEDPP, max_sweeps=100_000, nnz_capacity=None, cd_mode=BL_CD_RESIDUAL):
     """The whole path on the GPU.  X (p, ldx) and y (n, float64) on the ctx's
     device.  Returns a dict of device tensors (lambdas, col_ptr, row_idx, val,
     val_orig, intercept, loss) and host tensors (per-lambda counters)."""
@@ -259,7 +260,7 @@ def bl_fit_path(ctx, X, n, y, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, lambd
     for k, t in host.items():
         setattr(path, k, t.data_ptr())
     path.nnz_capacity = nnz_capacity
-    opt = bl_options(float(alpha), float(eps), float(ratio), int(max_sweeps), int(screen), 0)
+    opt = bl_options(float(alpha), float(eps), float(ratio), int(max_sweeps), int(screen), int(cd_mode))
     lam_arr = None
     if lambdas is not None:
         lam_arr = (C.c_double * K)(*[float(v) for v in lambdas])

@@ -52,6 +52,8 @@ struct bl_ctx {
     std::vector<TimedLaunch> launches;
     std::vector<cudaEvent_t> pool;
     bl_timing totals{};
+    void *gram = nullptr;      // correlation matrix of the working set (covariance-form CD)
+    size_t gram_bytes = 0;
     int64_t kernels = 0;
     int64_t cd_updates = 0;
 };
@@ -272,6 +274,7 @@ extern "C" int bl_ctx_destroy(bl_ctx *ctx)
     }
     for (auto e : ctx->pool) cudaEventDestroy(e);
     if (ctx->ws.base) cudaFree(ctx->ws.base);
+    if (ctx->gram) cudaFree(ctx->gram);
     if (ctx->sc_host) cudaFreeHost(ctx->sc_host);
     delete ctx;
     return BL_OK;
@@ -527,6 +530,7 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
     if (!(eps > 0.0)) return fail(ctx, BL_ERR_ARG, "eps must be > 0");
     if (opt->max_sweeps < 1) return fail(ctx, BL_ERR_ARG, "max_sweeps must be >= 1");
     if (opt->screen < 0 || opt->screen > 2) return fail(ctx, BL_ERR_ARG, "unknown screening rule");
+    if (opt->cd_mode < 0 || opt->cd_mode > 1) return fail(ctx, BL_ERR_ARG, "unknown cd_mode");
     if (!lambdas_in && K > 1 && !(opt->lambda_min_ratio > 0.0 && opt->lambda_min_ratio < 1.0))
         return fail(ctx, BL_ERR_ARG, "lambda_min_ratio must be in (0, 1)");
     if (lambdas_in) {
@@ -602,6 +606,19 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
                               w.r, w.r64, w.sc, s));
     tend(ctx, slot, (double)n * 16);
 
+    const bool gram_mode = opt->cd_mode == BL_CD_COVARIANCE;
+    if (gram_mode) {
+        const int64_t cap = max_w_for(dtype);
+        const size_t need = (size_t)cap * (size_t)cap * (beta_f64 ? 8 : 4);
+        if (ctx->gram_bytes < need) {
+            CK(cudaStreamSynchronize(s));
+            if (ctx->gram) cudaFree(ctx->gram);
+            ctx->gram = nullptr;
+            ctx->gram_bytes = 0;
+            CK(cudaMalloc(&ctx->gram, need));
+            ctx->gram_bytes = need;
+        }
+    }
     const void *cvec = beta_f64 ? (const void *)w.center : (const void *)w.c32;
     const void *isvec = beta_f64 ? (const void *)w.inv_scale : (const void *)w.is32;
     const double gamma = gamma_for(dtype, n);
@@ -678,8 +695,14 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
             LAUNCH(1, launch_gref(dtype, X, n, ldx, p, w.center, w.idx, -1, w.sc, w.r64, 1, w.gref, ctx->num_sms, s));
             tend(ctx, slot, 0.0);
             slot = tbegin(ctx, 5);
-            LAUNCH(1, launch_cd(dtype, X, n, p, ldx, cvec, isvec, w.idx, -1, w.gref, lam, alpha, w.beta, nullptr, eps,
-                                opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc, s));
+            if (gram_mode) {
+                LAUNCH(1, launch_gram(dtype, X, n, ldx, cvec, isvec, w.idx, -1, w.sc, ctx->gram, ctx->num_sms, s));
+                LAUNCH(1, launch_cd_gram(dtype, ctx->gram, n, p, isvec, w.idx, -1, w.gref, lam, alpha, w.beta, eps,
+                                         opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc, s));
+            } else {
+                LAUNCH(1, launch_cd(dtype, X, n, p, ldx, cvec, isvec, w.idx, -1, w.gref, lam, alpha, w.beta, nullptr,
+                                    eps, opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc, s));
+            }
             tend(ctx, slot, 0.0);
             slot = tbegin(ctx, 6);
             LAUNCH(2, launch_residual(dtype, X, n, ldx, w.center, w.inv_scale, w.idx, -1, w.sc, w.beta, w.yc,
