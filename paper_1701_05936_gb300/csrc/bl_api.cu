@@ -696,8 +696,13 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
             tend(ctx, slot, 0.0);
             slot = tbegin(ctx, 5);
             if (gram_mode) {
-                LAUNCH(1, launch_gram(dtype, X, n, ldx, cvec, isvec, w.idx, -1, w.sc, ctx->gram, ctx->num_sms, s));
-                LAUNCH(1, launch_cd_gram(dtype, ctx->gram, n, p, isvec, w.idx, -1, w.gref, lam, alpha, w.beta, eps,
+                // the covariance form sizes its launches from w, read back here
+                int64_t wh = 0;
+                CK(cudaMemcpyAsync(&wh, &w.sc->w, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                if (wh > wcap) return fail(ctx, BL_ERR_UNSUPPORTED, "working set exceeds the CD kernel's limit");
+                LAUNCH(1, launch_gram(dtype, X, n, ldx, cvec, isvec, w.idx, wh, w.sc, ctx->gram, ctx->num_sms, s));
+                LAUNCH(1, launch_cd_gram(dtype, ctx->gram, n, p, isvec, w.idx, wh, w.gref, lam, alpha, w.beta, eps,
                                          opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc, s));
             } else {
                 LAUNCH(1, launch_cd(dtype, X, n, p, ldx, cvec, isvec, w.idx, -1, w.gref, lam, alpha, w.beta, nullptr,

@@ -120,9 +120,10 @@ cudaError_t launch_gram(int dtype, const void *X, int64_t n, int64_t ldx, const 
                         const int32_t *idx, int64_t w_host, const DevScalars *scw, void *Rm, int num_sms,
                         cudaStream_t st);
 
-// Covariance-form CD over the working set from R and the reference gradients.
+// Covariance-form CD over the w (host-known) working-set entries from R and
+// the reference gradients.
 cudaError_t launch_cd_gram(int dtype, const void *Rm, int64_t n, int64_t p, const void *isvec, const int32_t *idx,
-                           int64_t w_host, const void *gref, double lam, double alpha, void *beta, double eps,
+                           int64_t w, const void *gref, double lam, double alpha, void *beta, double eps,
                            int64_t max_sweeps, uint64_t time_limit_ns, DevScalars *sc, cudaStream_t st);
 
 // r = yc - Xt b over the working set, in FP64, rounded into r_out; also the
