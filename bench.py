@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="a small workload for profiling runs")
-    ap.add_argument("--cd-mode", default="covariance", choices=["covariance", "residual"],
+    ap.add_argument("--cd-mode", default="blocked", choices=["blocked", "covariance", "residual"],
                     help="coordinate-descent form of the timed (chosen) path")
     ap.add_argument("--plain-steps", type=int, default=2,
                     help="steps of the plain form (residual-update CD) timed for comparison; 0 = skip")
@@ -216,7 +216,8 @@ def run_ours(args):
     X = torch.from_numpy(prob.X).to(dev)
     y = torch.from_numpy(prob.y).to(dev)
     ctx = bl.Context(local)
-    mode = bl.BL_CD_COVARIANCE if args.cd_mode == "covariance" else bl.BL_CD_RESIDUAL
+    mode = {"blocked": bl.BL_CD_BLOCKED, "covariance": bl.BL_CD_COVARIANCE,
+            "residual": bl.BL_CD_RESIDUAL}[args.cd_mode]
     kw = dict(alpha=prob.alpha, ratio=prob.ratio, nlambda=prob.nlambda, eps=prob.eps, cd_mode=mode)
 
     def barrier():
@@ -328,7 +329,9 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": "paths/s", "h2d_bytes_per_step": int(prob.X.nbytes + prob.y.nbytes),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(tim["kernel_launches"]), "clocks": clk, "cd": cd_info,
-        "chosen_form": "covariance-form CD" if mode == bl.BL_CD_COVARIANCE else "residual-update CD",
+        "chosen_form": {bl.BL_CD_BLOCKED: "residual-update CD in blocks of 16 coordinates",
+                        bl.BL_CD_COVARIANCE: "covariance-form CD",
+                        bl.BL_CD_RESIDUAL: "residual-update CD"}[mode],
         "plain_form": plain,
         "kernel_ms_per_step": breakdown, "status": res["status"],
     }

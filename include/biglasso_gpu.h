@@ -58,8 +58,14 @@ typedef enum { BL_F64 = 0, BL_F32 = 1, BL_BF16 = 2, BL_I8 = 3 } bl_dtype;
 
 typedef enum {
     BL_CD_RESIDUAL = 0,   /* CD with residual updates (Sec. 3.1.1): r -= delta xt_j */
-    BL_CD_COVARIANCE = 1  /* the same cyclic CD with the gradient updated through the
+    BL_CD_COVARIANCE = 1, /* the same cyclic CD with the gradient updated through the
                              working set's correlation matrix xt_W'xt_W/n */
+    BL_CD_BLOCKED = 2     /* residual updates in blocks of consecutive coordinates: the
+                             block's dot products and residual update run in parallel,
+                             the scalar updates in order with the within-block coupling
+                             xt_i'xt_k/n (identical iterates in exact arithmetic); FP32
+                             and FP64 designs with n <= 2048 (FP32) / 1024 (FP64), else
+                             BL_CD_RESIDUAL is used */
 } bl_cd_mode;
 
 typedef enum {

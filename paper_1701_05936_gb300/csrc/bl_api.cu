@@ -530,7 +530,7 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
     if (!(eps > 0.0)) return fail(ctx, BL_ERR_ARG, "eps must be > 0");
     if (opt->max_sweeps < 1) return fail(ctx, BL_ERR_ARG, "max_sweeps must be >= 1");
     if (opt->screen < 0 || opt->screen > 2) return fail(ctx, BL_ERR_ARG, "unknown screening rule");
-    if (opt->cd_mode < 0 || opt->cd_mode > 1) return fail(ctx, BL_ERR_ARG, "unknown cd_mode");
+    if (opt->cd_mode < 0 || opt->cd_mode > 2) return fail(ctx, BL_ERR_ARG, "unknown cd_mode");
     if (!lambdas_in && K > 1 && !(opt->lambda_min_ratio > 0.0 && opt->lambda_min_ratio < 1.0))
         return fail(ctx, BL_ERR_ARG, "lambda_min_ratio must be in (0, 1)");
     if (lambdas_in) {
@@ -607,7 +607,8 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
     tend(ctx, slot, (double)n * 16);
 
     const bool gram_mode = opt->cd_mode == BL_CD_COVARIANCE;
-    if (gram_mode) {
+    const bool blk_mode = opt->cd_mode == BL_CD_BLOCKED && cd_blk_ok(dtype, n);
+    if (gram_mode || blk_mode) {
         const int64_t cap = max_w_for(dtype);
         const size_t need = (size_t)cap * (size_t)cap * (beta_f64 ? 8 : 4);
         if (ctx->gram_bytes < need) {
@@ -695,15 +696,19 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
             LAUNCH(1, launch_gref(dtype, X, n, ldx, p, w.center, w.idx, -1, w.sc, w.r64, 1, w.gref, ctx->num_sms, s));
             tend(ctx, slot, 0.0);
             slot = tbegin(ctx, 5);
-            if (gram_mode) {
-                // the covariance form sizes its launches from w, read back here
+            if (gram_mode || blk_mode) {
+                // these forms size their launches from w, read back here
                 int64_t wh = 0;
                 CK(cudaMemcpyAsync(&wh, &w.sc->w, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
                 CK(cudaStreamSynchronize(s));
                 if (wh > wcap) return fail(ctx, BL_ERR_UNSUPPORTED, "working set exceeds the CD kernel's limit");
                 LAUNCH(1, launch_gram(dtype, X, n, ldx, cvec, isvec, w.idx, wh, w.sc, ctx->gram, ctx->num_sms, s));
-                LAUNCH(1, launch_cd_gram(dtype, ctx->gram, n, p, isvec, w.idx, wh, w.gref, lam, alpha, w.beta, eps,
-                                         opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc, s));
+                if (gram_mode)
+                    LAUNCH(1, launch_cd_gram(dtype, ctx->gram, n, p, isvec, w.idx, wh, w.gref, lam, alpha, w.beta, eps,
+                                             opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc, s));
+                else
+                    LAUNCH(1, launch_cd_blk(dtype, X, n, p, ldx, cvec, isvec, w.idx, wh, w.gref, ctx->gram, lam, alpha,
+                                            w.beta, nullptr, eps, opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc, s));
             } else {
                 LAUNCH(1, launch_cd(dtype, X, n, p, ldx, cvec, isvec, w.idx, -1, w.gref, lam, alpha, w.beta, nullptr,
                                     eps, opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc, s));

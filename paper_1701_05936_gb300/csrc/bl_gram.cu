@@ -359,4 +359,401 @@ cudaError_t launch_cd_gram(int dtype, const void *Rm, int64_t n, int64_t p, cons
     }
 }
 
+// ------------------------------------------- residual-form CD, block look-ahead
+// The same cyclic CD with residual updates, organised in blocks of B
+// consecutive coordinates of the sweep.  For a block (coordinates k = 0..B-1):
+//   all 256 threads form xd_k = x_k - c_k for their rows and the partial dots
+//   xd_k' dr; a butterfly reduce-scatter plus one barrier gives
+//   zt_k = (g_ref_k - xd_k' dr)/(n s_k) + b_k for every k;
+//   warp 0 then runs the scalar chain: for k in order, b_k' = S(zt_k, lam alpha)
+//   /(1 + lam(1-alpha)), d_k = b_k' - b_k, and zt_i -= d_k R_ik for i > k (the
+//   change of xt_i'r/n that coordinate k's residual update causes);
+//   finally every thread applies dr += sum_k d_k xd_k / s_k to its rows.
+// In exact arithmetic this is exactly the coordinate-by-coordinate cyclic CD;
+// the dot products and residual updates of a block run in parallel and only
+// the scalar chain is sequential.  R is the working set's correlation matrix
+// (k_gram).  The columns and R entries of the next block are loaded while the
+// current block runs.
+template <typename T, int RPT, int B>
+__global__ void __launch_bounds__(256, 1)
+    k_cd_blk(const T *__restrict__ X, int64_t n, int64_t ldx, const typename elem<T>::acc *__restrict__ cvec,
+             const typename elem<T>::acc *__restrict__ isvec, const int32_t *__restrict__ idx, int64_t w, int64_t p,
+             const typename elem<T>::acc *__restrict__ gref, const typename elem<T>::acc *__restrict__ Rm, double lam,
+             double alpha, typename elem<T>::res *beta, typename elem<T>::res *r_io, double eps, int64_t max_sweeps,
+             uint64_t time_limit_ns, DevScalars *sc)
+{
+    using E = elem<T>;
+    using A = typename E::acc;
+    using R = typename E::res;
+    using V = typename E::vec;
+    constexpr int VEC = E::VEC;
+    constexpr int NT = 256, NW = 8;
+    constexpr int QPL = (B * B + 31) / 32;  // correlation entries per lane of warp 0
+    static_assert(B == 16 || B == 8, "block of 8 or 16 coordinates");
+    constexpr A RES_FLOOR = sizeof(A) == 4 ? (A)4.76837158203125e-07 : (A)8.881784197001252e-16;
+    const int64_t ld = gram_ld(w);
+    extern __shared__ __align__(16) unsigned char smem[];
+    A *c_s = reinterpret_cast<A *>(smem);
+    A *is_s = c_s + ld;
+    A *g_s = is_s + ld;
+    R *beta_s = reinterpret_cast<R *>(g_s + ld);
+    int32_t *idx_s = reinterpret_cast<int32_t *>(beta_s + ld);
+    uint16_t *act_s = reinterpret_cast<uint16_t *>(idx_s + ld);
+    __shared__ A red[NW][B];
+    __shared__ A dks[B];
+    __shared__ A Qs[B][B + 1];
+    __shared__ A zts[B], bs[B];
+    __shared__ unsigned int scan_s[NW + 1];
+    __shared__ int flag_s, mv_s, nz_s;
+
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) flag_s = 0;
+    __syncthreads();
+    for (int64_t t = tid; t < w; t += NT) {
+        const int32_t j = idx[t];
+        if (j < 0 || (int64_t)j >= p) {
+            flag_s = 1;
+            continue;
+        }
+        idx_s[t] = j;
+        c_s[t] = cvec[j];
+        is_s[t] = isvec[j];
+        g_s[t] = gref[t];
+        beta_s[t] = beta[j];
+    }
+    __syncthreads();
+    if (flag_s) {
+        if (tid == 0) atomicOr(&sc->status, ST_BAD_INDEX);
+        return;
+    }
+    {
+        const uint32_t col_bytes = (uint32_t)(((uint64_t)n * sizeof(T) + 15) & ~(uint64_t)15);
+        for (int64_t t = tid; t < w; t += NT) {
+            const T *col = X + (int64_t)idx_s[t] * ldx;
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(col), "r"(col_bytes) : "memory");
+        }
+    }
+    const uint64_t t_start = globaltimer_ns();
+    const int64_t nch = (n + VEC - 1) / VEC;
+    const int64_t nfull = n / VEC;
+    const int tail = (int)(n - nfull * VEC);
+    A dr[RPT][VEC];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) dr[q][v] = (A)0;
+    const A thr = (A)(lam * alpha);
+    const A inv_den = (A)(1.0 / (1.0 + lam * (1.0 - alpha)));
+    const A inv_n = (A)(1.0 / (double)n);
+    const A epsA = (A)eps;
+    int64_t sweeps = 0;
+    unsigned long long updates = 0;
+    int status = 0;
+
+    // one sweep over len coordinates; returns (moved, newnz) to every thread
+    auto sweep = [&](bool full, int64_t len, bool &moved_out, bool &newnz_out) {
+        bool moved = false, newnz = false;  // meaningful in warp 0
+        const int64_t nblk = (len + B - 1) / B;
+        V xn[B][RPT];
+        A qn[QPL];
+        auto pos_of = [&](int64_t t) -> int { return full ? (int)t : (int)act_s[t]; };
+        auto load_block = [&](int64_t blk) {
+            const int64_t t0 = blk * B;
+            const int cnt = (int)((len - t0 < B) ? len - t0 : B);
+#pragma unroll
+            for (int k = 0; k < B; ++k) {
+                if (k < cnt) {
+                    const V *colv = reinterpret_cast<const V *>(X + (int64_t)idx_s[pos_of(t0 + k)] * ldx);
+#pragma unroll
+                    for (int q = 0; q < RPT; ++q) {
+                        const int64_t ch = (int64_t)q * NT + tid;
+                        xn[k][q] = (ch < nch) ? ldg16(colv + ch) : V{};
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < RPT; ++q) xn[k][q] = V{};
+                }
+            }
+            if (wid == 0) {
+#pragma unroll
+                for (int m = 0; m < QPL; ++m) {
+                    const int e = lane + 32 * m;
+                    const int i = e / B, k = e % B;
+                    A qv = (A)0;
+                    if (e < B * B && i < cnt && k < cnt && i > k)
+                        qv = Rm[(int64_t)pos_of(t0 + i) * ld + pos_of(t0 + k)];
+                    qn[m] = qv;
+                }
+            }
+        };
+        if (nblk > 0) load_block(0);
+        for (int64_t blk = 0; blk < nblk; ++blk) {
+            const int64_t t0 = blk * B;
+            const int cnt = (int)((len - t0 < B) ? len - t0 : B);
+            // xd = x - c (rows past n, and coordinates past cnt, are 0) and the
+            // partial dots with dr, straight from the prefetched registers
+            A xd[B][RPT][VEC];
+            A part[B];
+#pragma unroll
+            for (int k = 0; k < B; ++k) {
+                const A ck = (k < cnt) ? c_s[pos_of(t0 + k)] : (A)0;
+                A acc = 0;
+#pragma unroll
+                for (int q = 0; q < RPT; ++q) {
+                    const int64_t ch = (int64_t)q * NT + tid;
+                    A e[VEC];
+                    unpack(xn[k][q], e);
+                    const int nv = (k >= cnt) ? 0 : (ch < nfull ? VEC : (ch == nfull ? tail : 0));
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        xd[k][q][v] = (v < nv) ? e[v] - ck : (A)0;
+                        acc = fma(xd[k][q][v], dr[q][v], acc);
+                    }
+                }
+                part[k] = acc;
+            }
+            if (wid == 0) {
+#pragma unroll
+                for (int m = 0; m < QPL; ++m) {
+                    const int e = lane + 32 * m;
+                    if (e < B * B) Qs[e / B][e % B] = qn[m];
+                }
+            }
+            if (blk + 1 < nblk) load_block(blk + 1);  // the next block streams in meanwhile
+            // butterfly reduce-scatter: lanes 2k and 2k+1 (B = 16) end with the
+            // warp's sum for column k
+            {
+                A v8[B / 2];
+                const bool hi16 = (lane & 16) != 0;
+#pragma unroll
+                for (int j = 0; j < B / 2; ++j) {
+                    const A send = hi16 ? part[j] : part[B / 2 + j];
+                    const A keep = hi16 ? part[B / 2 + j] : part[j];
+                    v8[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+                }
+                A v4[B / 4];
+                const bool hi8 = (lane & 8) != 0;
+#pragma unroll
+                for (int j = 0; j < B / 4; ++j) {
+                    const A send = hi8 ? v8[j] : v8[B / 4 + j];
+                    const A keep = hi8 ? v8[B / 4 + j] : v8[j];
+                    v4[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                }
+                A v2[B / 8 > 0 ? B / 8 : 1];
+                const bool hi4 = (lane & 4) != 0;
+#pragma unroll
+                for (int j = 0; j < B / 8; ++j) {
+                    const A send = hi4 ? v4[j] : v4[B / 8 + j];
+                    const A keep = hi4 ? v4[B / 8 + j] : v4[j];
+                    v2[j] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+                }
+                A v1;
+                int col;
+                if (B == 16) {
+                    const bool hi2 = (lane & 2) != 0;
+                    const A send = hi2 ? v2[0] : v2[1];
+                    const A keep = hi2 ? v2[1] : v2[0];
+                    v1 = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+                    v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
+                    col = lane >> 1;  // bits 4..1 of the lane
+                } else {  // B == 8: after offset 4 each lane holds one column
+                    v1 = v2[0];
+                    v1 += __shfl_xor_sync(0xffffffffu, v1, 2);
+                    v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
+                    col = lane >> 2;  // bits 4..2 of the lane
+                }
+                if ((lane & (32 / B - 1)) == 0) red[wid][col] = v1;
+            }
+            __syncthreads();
+            if (wid == 0) {
+                int my_pos = 0;
+                A my_is = 0;
+                if (lane < cnt) {
+                    my_pos = pos_of(t0 + lane);
+                    A a = 0;
+#pragma unroll
+                    for (int ww = 0; ww < NW; ++ww) a += red[ww][lane];
+                    const A b = (A)beta_s[my_pos];
+                    my_is = is_s[my_pos];
+                    zts[lane] = fma(g_s[my_pos] - a, my_is * inv_n, b);
+                    bs[lane] = b;
+                }
+                __syncwarp();
+                A zt[B], bb[B];
+#pragma unroll
+                for (int k = 0; k < B; ++k) {
+                    zt[k] = (k < cnt) ? zts[k] : (A)0;
+                    bb[k] = (k < cnt) ? bs[k] : (A)0;
+                }
+#pragma unroll
+                for (int k = 0; k < B; ++k) {
+                    if (k < cnt) {
+                        const A s = zt[k];
+                        const A nb = soft_threshold(s, thr) * inv_den;
+                        const A d = nb - bb[k];
+                        const A tol = fmax(epsA, RES_FLOOR * (fabs(s) + fabs(nb)));
+                        moved |= (fabs(d) >= tol);
+                        newnz |= (bb[k] == (A)0 && fabs(nb) >= tol);
+#pragma unroll
+                        for (int i = k + 1; i < B; ++i) zt[i] = fma(-d, Qs[i][k], zt[i]);
+                        if (lane == k) {
+                            dks[k] = d * my_is;
+                            beta_s[my_pos] = (R)nb;
+                        }
+                    } else if (lane == k) {
+                        dks[k] = (A)0;
+                    }
+                }
+                updates += (unsigned long long)cnt;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < B; ++k) {
+                const A ds = dks[k];
+#pragma unroll
+                for (int q = 0; q < RPT; ++q)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) dr[q][v] = fma(ds, xd[k][q][v], dr[q][v]);
+            }
+        }
+        if (tid == 0) {
+            mv_s = moved;
+            nz_s = newnz;
+        }
+        __syncthreads();
+        moved_out = mv_s != 0;
+        newnz_out = nz_s != 0;
+        __syncthreads();
+    };
+    auto out_of_time = [&]() -> bool {
+        __syncthreads();
+        if (tid == 0) flag_s = (globaltimer_ns() - t_start) > time_limit_ns;
+        __syncthreads();
+        return flag_s != 0;
+    };
+
+    for (;;) {
+        bool moved = false, newnz = false;
+        sweep(true, w, moved, newnz);
+        ++sweeps;
+        if (!moved && !newnz) break;
+        if (sweeps >= max_sweeps) {
+            status = ST_NOT_CONVERGED;
+            break;
+        }
+        if (out_of_time()) {
+            status = ST_TIMEOUT;
+            break;
+        }
+        const int64_t per = (w + NT - 1) / NT;
+        const int64_t b0 = (int64_t)tid * per;
+        const int64_t b1 = (b0 + per < w) ? b0 + per : w;
+        unsigned int c = 0;
+        for (int64_t t = b0; t < b1; ++t) c += (beta_s[t] != (R)0);
+        unsigned int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) scan_s[wid] = incl;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned int a = 0;
+            for (int k = 0; k < NW; ++k) {
+                const unsigned int v = scan_s[k];
+                scan_s[k] = a;
+                a += v;
+            }
+            scan_s[NW] = a;
+        }
+        __syncthreads();
+        unsigned int pos = scan_s[wid] + incl - c;
+        for (int64_t t = b0; t < b1; ++t)
+            if (beta_s[t] != (R)0) act_s[pos++] = (uint16_t)t;
+        const int64_t na = scan_s[NW];
+        __syncthreads();
+        for (;;) {
+            bool mv = false, nz = false;
+            sweep(false, na, mv, nz);
+            ++sweeps;
+            if (!mv) break;
+            if (sweeps >= max_sweeps) {
+                status = ST_NOT_CONVERGED;
+                break;
+            }
+            if (out_of_time()) {
+                status = ST_TIMEOUT;
+                break;
+            }
+        }
+        if (status) break;
+    }
+    __syncthreads();
+    for (int64_t t = tid; t < w; t += NT) beta[idx_s[t]] = beta_s[t];
+    if (r_io) {
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int64_t ch = (int64_t)q * NT + tid;
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                const int64_t row = ch * VEC + v;
+                if (row < n) r_io[row] = (R)((A)r_io[row] - dr[q][v]);
+            }
+        }
+    }
+    if (tid == 0) {
+        sc->sweeps += (unsigned long long)sweeps;
+        sc->cd_updates += updates;
+        if (status) atomicOr(&sc->status, status);
+    }
+}
+
+template <typename T, int RPT, int B>
+static cudaError_t cd_blk_t(const T *X, int64_t n, int64_t ldx, const void *cvec, const void *isvec,
+                            const int32_t *idx, int64_t w, int64_t p, const void *gref, const void *Rm, double lam,
+                            double alpha, void *beta, void *r, double eps, int64_t max_sweeps, uint64_t tl,
+                            DevScalars *sc, cudaStream_t st)
+{
+    using A = typename elem<T>::acc;
+    using R = typename elem<T>::res;
+    const size_t smem = (size_t)gram_ld(w) * (3 * sizeof(A) + sizeof(R) + sizeof(int32_t) + sizeof(uint16_t));
+    auto kern = k_cd_blk<T, RPT, B>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<1, 256, smem, st>>>(X, n, ldx, (const A *)cvec, (const A *)isvec, idx, w, p, (const A *)gref,
+                               (const A *)Rm, lam, alpha, (R *)beta, (R *)r, eps, max_sweeps, tl, sc);
+    return cudaGetLastError();
+}
+
+// Whether the block kernel covers this shape (else the caller uses another form).
+bool cd_blk_ok(int dtype, int64_t n)
+{
+    if (dtype == 3) return false;
+    const int vec = (int)(16 / elem_size(dtype));
+    return (n + vec - 1) / vec <= 512;
+}
+
+cudaError_t launch_cd_blk(int dtype, const void *X, int64_t n, int64_t p, int64_t ldx, const void *cvec,
+                          const void *isvec, const int32_t *idx, int64_t w, const void *gref, const void *Rm,
+                          double lam, double alpha, void *beta, void *r, double eps, int64_t max_sweeps,
+                          uint64_t time_limit_ns, DevScalars *sc, cudaStream_t st)
+{
+    if (w <= 0) return cudaSuccess;
+    const int vec = (int)(16 / elem_size(dtype));
+    const int64_t nch = (n + vec - 1) / vec;
+#define BL_BLK(T_, RPT_, B_)                                                                                       \
+    return cd_blk_t<T_, RPT_, B_>((const T_ *)X, n, ldx, cvec, isvec, idx, w, p, gref, Rm, lam, alpha, beta, r, eps, \
+                                  max_sweeps, time_limit_ns, sc, st)
+    if (dtype == 1) {
+        if (nch <= 256) BL_BLK(float, 1, 16);
+        if (nch <= 512) BL_BLK(float, 2, 8);
+    } else if (dtype == 0) {
+        if (nch <= 256) BL_BLK(double, 1, 8);
+        if (nch <= 512) BL_BLK(double, 2, 8);
+    }
+#undef BL_BLK
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace bl

@@ -126,6 +126,14 @@ cudaError_t launch_cd_gram(int dtype, const void *Rm, int64_t n, int64_t p, cons
                            int64_t w, const void *gref, double lam, double alpha, void *beta, double eps,
                            int64_t max_sweeps, uint64_t time_limit_ns, DevScalars *sc, cudaStream_t st);
 
+// Residual-form CD in blocks of consecutive coordinates (needs R from
+// launch_gram); cd_blk_ok tells whether this build covers the shape.
+bool cd_blk_ok(int dtype, int64_t n);
+cudaError_t launch_cd_blk(int dtype, const void *X, int64_t n, int64_t p, int64_t ldx, const void *cvec,
+                          const void *isvec, const int32_t *idx, int64_t w, const void *gref, const void *Rm,
+                          double lam, double alpha, void *beta, void *r, double eps, int64_t max_sweeps,
+                          uint64_t time_limit_ns, DevScalars *sc, cudaStream_t st);
+
 // r = yc - Xt b over the working set, in FP64, rounded into r_out; also the
 // residual statistics in sc.  partial: RESID_GROUPS * n doubles of scratch.
 cudaError_t launch_residual(int dtype, const void *X, int64_t n, int64_t ldx, const double *center,

@@ -258,7 +258,7 @@ def compare_paths(prob, g, o, tol, obj_rtol=1e-7, allow_exempt=0):
     return diff
 
 
-@pytest.mark.parametrize("cd_mode", [bl.BL_CD_RESIDUAL, bl.BL_CD_COVARIANCE])
+@pytest.mark.parametrize("cd_mode", [bl.BL_CD_RESIDUAL, bl.BL_CD_COVARIANCE, bl.BL_CD_BLOCKED])
 @pytest.mark.parametrize("which", [0, 1, 2])
 def test_fit_path_matches_oracle_small(ctx, which, cd_mode):
     prob = small_problems()[which]
@@ -282,9 +282,9 @@ def test_fit_path_elastic_net_and_screen_rules_agree(ctx):
         g = bl.bl_fit_path(ctx, X, prob.n, y, alpha=0.5, ratio=0.05, nlambda=60, eps=1e-7, screen=rule)
         compare_paths(prob, g, o, 1e-5)
         outs.append(bl.path_dense(g, prob.p).cpu().numpy())
-    gc = bl.bl_fit_path(ctx, X, prob.n, y, alpha=0.5, ratio=0.05, nlambda=60, eps=1e-7,
-                        cd_mode=bl.BL_CD_COVARIANCE)
-    compare_paths(prob, gc, o, 1e-5)
+    for mode in (bl.BL_CD_COVARIANCE, bl.BL_CD_BLOCKED):
+        gc = bl.bl_fit_path(ctx, X, prob.n, y, alpha=0.5, ratio=0.05, nlambda=60, eps=1e-7, cd_mode=mode)
+        compare_paths(prob, gc, o, 1e-5)
     assert np.abs(outs[0] - outs[2]).max() <= 2e-6 and np.abs(outs[1] - outs[2]).max() <= 2e-6
     # lasso: SSR-BEDPP scans no more columns than SSR
     g1 = bl.bl_fit_path(ctx, X, prob.n, y, alpha=1.0, ratio=0.05, nlambda=60, screen=bl.BL_SCREEN_SSR)
@@ -368,11 +368,11 @@ def test_edge_invalid_arguments_and_limits(ctx):
 # ----------------------------------------------- full size, bench launch config
 def test_full_size_ar1_workload_matches_oracle(ctx):
     """The 1000 x 100,000 FP32 AR(1) workload the benchmark times, whole path,
-    in both CD forms (the benchmark's chosen form is the covariance form)."""
+    in every CD form (the benchmark's chosen form is the blocked residual form)."""
     prob = synth.workload(2)
     X, y = to_dev(prob)
     o = oracle.fit_path(prob.dense_f64(), prob.y, alpha=1.0, ratio=prob.ratio, nlambda=100, eps=1e-7)
-    for mode in (bl.BL_CD_COVARIANCE, bl.BL_CD_RESIDUAL):
+    for mode in (bl.BL_CD_BLOCKED, bl.BL_CD_COVARIANCE, bl.BL_CD_RESIDUAL):
         g = bl.bl_fit_path(ctx, X, prob.n, y, alpha=1.0, ratio=prob.ratio, nlambda=100, eps=1e-7, cd_mode=mode)
         assert g["status"] == bl.BL_OK
         d = compare_paths(prob, g, o, 1e-5, allow_exempt=2)
