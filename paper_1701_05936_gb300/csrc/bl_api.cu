@@ -702,13 +702,18 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
                 CK(cudaMemcpyAsync(&wh, &w.sc->w, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
                 CK(cudaStreamSynchronize(s));
                 if (wh > wcap) return fail(ctx, BL_ERR_UNSUPPORTED, "working set exceeds the CD kernel's limit");
-                LAUNCH(1, launch_gram(dtype, X, n, ldx, cvec, isvec, w.idx, wh, w.sc, ctx->gram, ctx->num_sms, s));
-                if (gram_mode)
+                if (gram_mode) {
+                    LAUNCH(1, launch_gram(dtype, X, n, ldx, cvec, isvec, w.idx, wh, w.sc, ctx->gram, ctx->num_sms, s));
                     LAUNCH(1, launch_cd_gram(dtype, ctx->gram, n, p, isvec, w.idx, wh, w.gref, lam, alpha, w.beta, eps,
                                              opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc, s));
-                else
+                } else if (cd_blk_fits(dtype, n, wh)) {
+                    LAUNCH(1, launch_gram(dtype, X, n, ldx, cvec, isvec, w.idx, wh, w.sc, ctx->gram, ctx->num_sms, s));
                     LAUNCH(1, launch_cd_blk(dtype, X, n, p, ldx, cvec, isvec, w.idx, wh, w.gref, ctx->gram, lam, alpha,
                                             w.beta, nullptr, eps, opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc, s));
+                } else {  // working set too large for the block stages: coordinate-at-a-time form
+                    LAUNCH(1, launch_cd(dtype, X, n, p, ldx, cvec, isvec, w.idx, wh, w.gref, lam, alpha, w.beta, nullptr,
+                                        eps, opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc, s));
+                }
             } else {
                 LAUNCH(1, launch_cd(dtype, X, n, p, ldx, cvec, isvec, w.idx, -1, w.gref, lam, alpha, w.beta, nullptr,
                                     eps, opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc, s));

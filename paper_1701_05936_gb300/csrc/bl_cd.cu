@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
         if (threadIdx.x == 0) atomicOr(&sc->status, ST_WORKING_TOO_BIG);
         return;
     }
-    extern __shared__ __align__(128) unsigned char smem[];
+    extern __shared__ __align__(16) unsigned char smem[];
     A *c_s = reinterpret_cast<A *>(smem);
     A *is_s = c_s + cap;
     A *g_s = is_s + cap;

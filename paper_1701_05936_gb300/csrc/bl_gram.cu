@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(32, 1)
     constexpr A RES_FLOOR = sizeof(A) == 4 ? (A)4.76837158203125e-07 : (A)8.881784197001252e-16;
     const int64_t ld = gram_ld(w);
     const uint32_t row_bytes = (uint32_t)(ld * (int64_t)sizeof(A));
-    extern __shared__ __align__(128) unsigned char smem[];
+    extern __shared__ __align__(16) unsigned char smem[];
     A *G_s = reinterpret_cast<A *>(smem);
     A *Dg = G_s + ld;
     R *beta_s = reinterpret_cast<R *>(Dg + ld);
@@ -372,15 +372,19 @@ cudaError_t launch_cd_gram(int dtype, const void *Rm, int64_t n, int64_t p, cons
 // In exact arithmetic this is exactly the coordinate-by-coordinate cyclic CD;
 // the dot products and residual updates of a block run in parallel and only
 // the scalar chain is sequential.  R is the working set's correlation matrix
-// (k_gram).  The columns and R entries of the next block are loaded while the
-// current block runs.
+// (k_gram).  The columns of each block stream into one of two shared-memory
+// block stages by 1-D TMA bulk copies issued two blocks ahead (one mbarrier
+// per stage, waits bounded by the GPU wall clock); the R entries of the next
+// block are loaded by warp 0 during the current chain.
+constexpr uint64_t BLK_WAIT_NS = 1000ull * 1000ull * 1000ull;  // 1 s per stage wait
+
 template <typename T, int RPT, int B>
 __global__ void __launch_bounds__(256, 1)
     k_cd_blk(const T *__restrict__ X, int64_t n, int64_t ldx, const typename elem<T>::acc *__restrict__ cvec,
              const typename elem<T>::acc *__restrict__ isvec, const int32_t *__restrict__ idx, int64_t w, int64_t p,
              const typename elem<T>::acc *__restrict__ gref, const typename elem<T>::acc *__restrict__ Rm, double lam,
              double alpha, typename elem<T>::res *beta, typename elem<T>::res *r_io, double eps, int64_t max_sweeps,
-             uint64_t time_limit_ns, DevScalars *sc)
+             uint64_t time_limit_ns, DevScalars *sc, uint32_t copy_bytes, uint32_t col_stride, uint32_t stage_off)
 {
     using E = elem<T>;
     using A = typename E::acc;
@@ -399,6 +403,8 @@ __global__ void __launch_bounds__(256, 1)
     R *beta_s = reinterpret_cast<R *>(g_s + ld);
     int32_t *idx_s = reinterpret_cast<int32_t *>(beta_s + ld);
     uint16_t *act_s = reinterpret_cast<uint16_t *>(idx_s + ld);
+    unsigned char *stages = smem + stage_off;  // 2 stages of B columns, col_stride bytes apart
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(stages + 2 * (size_t)B * col_stride);
     __shared__ A red[NW][B];
     __shared__ A dks[B];
     __shared__ A Qs[B][B + 1];
@@ -407,7 +413,12 @@ __global__ void __launch_bounds__(256, 1)
     __shared__ int flag_s, mv_s, nz_s;
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid == 0) flag_s = 0;
+    if (tid == 0) {
+        flag_s = 0;
+        mbar_init(smem_u32(&mbar[0]), 1);
+        mbar_init(smem_u32(&mbar[1]), 1);
+        fence_mbar_init();
+    }
     __syncthreads();
     for (int64_t t = tid; t < w; t += NT) {
         const int32_t j = idx[t];
@@ -426,15 +437,11 @@ __global__ void __launch_bounds__(256, 1)
         if (tid == 0) atomicOr(&sc->status, ST_BAD_INDEX);
         return;
     }
-    {
-        const uint32_t col_bytes = (uint32_t)(((uint64_t)n * sizeof(T) + 15) & ~(uint64_t)15);
-        for (int64_t t = tid; t < w; t += NT) {
-            const T *col = X + (int64_t)idx_s[t] * ldx;
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(col), "r"(col_bytes) : "memory");
-        }
+    for (int64_t t = tid; t < w; t += NT) {
+        const T *col = X + (int64_t)idx_s[t] * ldx;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(col), "r"(copy_bytes) : "memory");
     }
     const uint64_t t_start = globaltimer_ns();
-    const int64_t nch = (n + VEC - 1) / VEC;
     const int64_t nfull = n / VEC;
     const int tail = (int)(n - nfull * VEC);
     A dr[RPT][VEC];
@@ -449,61 +456,76 @@ __global__ void __launch_bounds__(256, 1)
     int64_t sweeps = 0;
     unsigned long long updates = 0;
     int status = 0;
+    uint32_t bseq = 0;  // blocks consumed so far in this launch (same in every thread)
 
-    // one sweep over len coordinates; returns (moved, newnz) to every thread
-    auto sweep = [&](bool full, int64_t len, bool &moved_out, bool &newnz_out) {
+    // one sweep over len coordinates; returns false on a stage-wait timeout
+    auto sweep = [&](bool full, int64_t len, bool &moved_out, bool &newnz_out) -> bool {
         bool moved = false, newnz = false;  // meaningful in warp 0
         const int64_t nblk = (len + B - 1) / B;
-        V xn[B][RPT];
-        A qn[QPL];
         auto pos_of = [&](int64_t t) -> int { return full ? (int)t : (int)act_s[t]; };
-        auto load_block = [&](int64_t blk) {
+        // one thread issues the column copies of block blk into stage (bseq+rel)%2
+        auto issue_block = [&](int64_t blk, uint32_t gblk) {
             const int64_t t0 = blk * B;
             const int cnt = (int)((len - t0 < B) ? len - t0 : B);
-#pragma unroll
-            for (int k = 0; k < B; ++k) {
-                if (k < cnt) {
-                    const V *colv = reinterpret_cast<const V *>(X + (int64_t)idx_s[pos_of(t0 + k)] * ldx);
-#pragma unroll
-                    for (int q = 0; q < RPT; ++q) {
-                        const int64_t ch = (int64_t)q * NT + tid;
-                        xn[k][q] = (ch < nch) ? ldg16(colv + ch) : V{};
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < RPT; ++q) xn[k][q] = V{};
-                }
-            }
-            if (wid == 0) {
-#pragma unroll
-                for (int m = 0; m < QPL; ++m) {
-                    const int e = lane + 32 * m;
-                    const int i = e / B, k = e % B;
-                    A qv = (A)0;
-                    if (e < B * B && i < cnt && k < cnt && i > k)
-                        qv = Rm[(int64_t)pos_of(t0 + i) * ld + pos_of(t0 + k)];
-                    qn[m] = qv;
-                }
+            const int st = (int)(gblk & 1u);
+            const uint32_t bar = smem_u32(&mbar[st]);
+            fence_proxy_async_smem();
+            mbar_expect_tx(bar, (uint32_t)cnt * copy_bytes);
+            for (int k = 0; k < cnt; ++k) {
+                const T *col = X + (int64_t)idx_s[pos_of(t0 + k)] * ldx;
+                bulk_g2s(smem_u32(stages + ((size_t)st * B + k) * col_stride), col, copy_bytes, bar);
             }
         };
-        if (nblk > 0) load_block(0);
-        for (int64_t blk = 0; blk < nblk; ++blk) {
+        // R entries of block blk (i > k, both inside the block), clamped loads
+        A qn[QPL];
+        auto load_q = [&](int64_t blk) {
             const int64_t t0 = blk * B;
             const int cnt = (int)((len - t0 < B) ? len - t0 : B);
+#pragma unroll
+            for (int m = 0; m < QPL; ++m) {
+                const int e = lane + 32 * m;
+                int i = e / B, k = e % B;
+                if (i >= cnt) i = cnt - 1;
+                if (k >= cnt) k = cnt - 1;
+                qn[m] = Rm[(int64_t)pos_of(t0 + i) * ld + pos_of(t0 + k)];
+            }
+        };
+        if (tid == 32) {
+            if (nblk > 0) issue_block(0, bseq);
+            if (nblk > 1) issue_block(1, bseq + 1);
+        }
+        if (wid == 0 && nblk > 0) load_q(0);
+        for (int64_t blk = 0; blk < nblk; ++blk) {
+            const uint32_t gblk = bseq + (uint32_t)blk;
+            const int st = (int)(gblk & 1u);
+            const int64_t t0 = blk * B;
+            const int cnt = (int)((len - t0 < B) ? len - t0 : B);
+            const bool ok = mbar_wait_bounded(smem_u32(&mbar[st]), (gblk >> 1) & 1u, BLK_WAIT_NS);
+            if (!__syncthreads_and(ok)) {
+                if (tid == 32) {  // drain: this block's copies and, if issued, the next block's
+                    mbar_wait_bounded(smem_u32(&mbar[st]), (gblk >> 1) & 1u, BLK_WAIT_NS);
+                    if (blk + 1 < nblk)
+                        mbar_wait_bounded(smem_u32(&mbar[(gblk + 1) & 1u]), ((gblk + 1) >> 1) & 1u, BLK_WAIT_NS);
+                }
+                __syncthreads();
+                return false;
+            }
             // xd = x - c (rows past n, and coordinates past cnt, are 0) and the
-            // partial dots with dr, straight from the prefetched registers
+            // partial dots with dr, from the staged columns
             A xd[B][RPT][VEC];
             A part[B];
+            const unsigned char *stg = stages + (size_t)st * B * col_stride;
 #pragma unroll
             for (int k = 0; k < B; ++k) {
                 const A ck = (k < cnt) ? c_s[pos_of(t0 + k)] : (A)0;
+                const V *colv = reinterpret_cast<const V *>(stg + (size_t)k * col_stride);
                 A acc = 0;
 #pragma unroll
                 for (int q = 0; q < RPT; ++q) {
                     const int64_t ch = (int64_t)q * NT + tid;
-                    A e[VEC];
-                    unpack(xn[k][q], e);
                     const int nv = (k >= cnt) ? 0 : (ch < nfull ? VEC : (ch == nfull ? tail : 0));
+                    A e[VEC];
+                    if (nv > 0) unpack(colv[ch], e);
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) {
                         xd[k][q][v] = (v < nv) ? e[v] - ck : (A)0;
@@ -519,9 +541,8 @@ __global__ void __launch_bounds__(256, 1)
                     if (e < B * B) Qs[e / B][e % B] = qn[m];
                 }
             }
-            if (blk + 1 < nblk) load_block(blk + 1);  // the next block streams in meanwhile
-            // butterfly reduce-scatter: lanes 2k and 2k+1 (B = 16) end with the
-            // warp's sum for column k
+            // butterfly reduce-scatter: after it the lanes 32/B apart share one
+            // column's warp sum
             {
                 A v8[B / 2];
                 const bool hi16 = (lane & 16) != 0;
@@ -555,16 +576,17 @@ __global__ void __launch_bounds__(256, 1)
                     const A keep = hi2 ? v2[1] : v2[0];
                     v1 = keep + __shfl_xor_sync(0xffffffffu, send, 2);
                     v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
-                    col = lane >> 1;  // bits 4..1 of the lane
-                } else {  // B == 8: after offset 4 each lane holds one column
+                    col = lane >> 1;
+                } else {
                     v1 = v2[0];
                     v1 += __shfl_xor_sync(0xffffffffu, v1, 2);
                     v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
-                    col = lane >> 2;  // bits 4..2 of the lane
+                    col = lane >> 2;
                 }
                 if ((lane & (32 / B - 1)) == 0) red[wid][col] = v1;
             }
-            __syncthreads();
+            __syncthreads();  // every thread has read stage st; red complete
+            if (tid == 32 && blk + 2 < nblk) issue_block(blk + 2, gblk + 2);
             if (wid == 0) {
                 int my_pos = 0;
                 A my_is = 0;
@@ -578,12 +600,13 @@ __global__ void __launch_bounds__(256, 1)
                     zts[lane] = fma(g_s[my_pos] - a, my_is * inv_n, b);
                     bs[lane] = b;
                 }
+                if (blk + 1 < nblk) load_q(blk + 1);
                 __syncwarp();
                 A zt[B], bb[B];
 #pragma unroll
                 for (int k = 0; k < B; ++k) {
-                    zt[k] = (k < cnt) ? zts[k] : (A)0;
-                    bb[k] = (k < cnt) ? bs[k] : (A)0;
+                    zt[k] = zts[k];
+                    bb[k] = bs[k];
                 }
 #pragma unroll
                 for (int k = 0; k < B; ++k) {
@@ -616,6 +639,7 @@ __global__ void __launch_bounds__(256, 1)
                     for (int v = 0; v < VEC; ++v) dr[q][v] = fma(ds, xd[k][q][v], dr[q][v]);
             }
         }
+        bseq += (uint32_t)nblk;
         if (tid == 0) {
             mv_s = moved;
             nz_s = newnz;
@@ -624,6 +648,7 @@ __global__ void __launch_bounds__(256, 1)
         moved_out = mv_s != 0;
         newnz_out = nz_s != 0;
         __syncthreads();
+        return true;
     };
     auto out_of_time = [&]() -> bool {
         __syncthreads();
@@ -634,7 +659,10 @@ __global__ void __launch_bounds__(256, 1)
 
     for (;;) {
         bool moved = false, newnz = false;
-        sweep(true, w, moved, newnz);
+        if (!sweep(true, w, moved, newnz)) {
+            status = ST_TIMEOUT;
+            break;
+        }
         ++sweeps;
         if (!moved && !newnz) break;
         if (sweeps >= max_sweeps) {
@@ -675,7 +703,10 @@ __global__ void __launch_bounds__(256, 1)
         __syncthreads();
         for (;;) {
             bool mv = false, nz = false;
-            sweep(false, na, mv, nz);
+            if (!sweep(false, na, mv, nz)) {
+                status = ST_TIMEOUT;
+                break;
+            }
             ++sweeps;
             if (!mv) break;
             if (sweeps >= max_sweeps) {
@@ -717,13 +748,37 @@ static cudaError_t cd_blk_t(const T *X, int64_t n, int64_t ldx, const void *cvec
 {
     using A = typename elem<T>::acc;
     using R = typename elem<T>::res;
-    const size_t smem = (size_t)gram_ld(w) * (3 * sizeof(A) + sizeof(R) + sizeof(int32_t) + sizeof(uint16_t));
+    const size_t meta = (size_t)gram_ld(w) * (3 * sizeof(A) + sizeof(R) + sizeof(int32_t) + sizeof(uint16_t));
+    const size_t stage_off = (meta + 127) & ~(size_t)127;
+    // copy n*sizeof(T) rounded up to 16 bytes (never past the column's ldx extent)
+    const uint32_t copy_bytes = (uint32_t)(((uint64_t)n * sizeof(T) + 15) & ~(uint64_t)15);
+    const uint32_t col_stride = (copy_bytes + 127u) & ~127u;
+    const size_t smem = stage_off + 2 * (size_t)B * col_stride + 16;
+    if (smem > 227 * 1024 - 1024) return cudaErrorInvalidValue;  // caller falls back
     auto kern = k_cd_blk<T, RPT, B>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<1, 256, smem, st>>>(X, n, ldx, (const A *)cvec, (const A *)isvec, idx, w, p, (const A *)gref,
-                               (const A *)Rm, lam, alpha, (R *)beta, (R *)r, eps, max_sweeps, tl, sc);
+                               (const A *)Rm, lam, alpha, (R *)beta, (R *)r, eps, max_sweeps, tl, sc, copy_bytes,
+                               col_stride, (uint32_t)stage_off);
     return cudaGetLastError();
+}
+
+// Shared memory the block kernel needs (0 when this build does not cover the shape).
+size_t cd_blk_smem(int dtype, int64_t n, int64_t w)
+{
+    if (dtype == 3) return 0;
+    const size_t es = elem_size(dtype);
+    const int vec = (int)(16 / es);
+    const int64_t nch = (n + vec - 1) / vec;
+    if (nch > 512) return 0;
+    const int B = (nch <= 256 && dtype == 1) ? 16 : 8;
+    const size_t a = (dtype == 0) ? 8 : 4;
+    const size_t meta = (size_t)((w + 3) & ~(int64_t)3) * (3 * a + a + 4 + 2);
+    const size_t stage_off = (meta + 127) & ~(size_t)127;
+    const size_t copy = ((size_t)n * es + 15) & ~(size_t)15;
+    const size_t colst = (copy + 127) & ~(size_t)127;
+    return stage_off + 2 * (size_t)B * colst + 16;
 }
 
 // Whether the block kernel covers this shape (else the caller uses another form).
@@ -732,6 +787,13 @@ bool cd_blk_ok(int dtype, int64_t n)
     if (dtype == 3) return false;
     const int vec = (int)(16 / elem_size(dtype));
     return (n + vec - 1) / vec <= 512;
+}
+
+// Whether the block kernel fits shared memory for this working-set size.
+bool cd_blk_fits(int dtype, int64_t n, int64_t w)
+{
+    const size_t need = cd_blk_smem(dtype, n, w);
+    return need > 0 && need <= 227 * 1024 - 1024;
 }
 
 cudaError_t launch_cd_blk(int dtype, const void *X, int64_t n, int64_t p, int64_t ldx, const void *cvec,

@@ -129,6 +129,7 @@ cudaError_t launch_cd_gram(int dtype, const void *Rm, int64_t n, int64_t p, cons
 // Residual-form CD in blocks of consecutive coordinates (needs R from
 // launch_gram); cd_blk_ok tells whether this build covers the shape.
 bool cd_blk_ok(int dtype, int64_t n);
+bool cd_blk_fits(int dtype, int64_t n, int64_t w);
 cudaError_t launch_cd_blk(int dtype, const void *X, int64_t n, int64_t p, int64_t ldx, const void *cvec,
                           const void *isvec, const int32_t *idx, int64_t w, const void *gref, const void *Rm,
                           double lam, double alpha, void *beta, void *r, double eps, int64_t max_sweeps,
