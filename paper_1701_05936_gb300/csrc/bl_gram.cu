@@ -12,6 +12,7 @@
 #include "bl_device.cuh"
 #include "bl_internal.h"
 
+#include <algorithm>
 #include <type_traits>
 
 namespace bl {
@@ -376,7 +377,42 @@ cudaError_t launch_cd_gram(int dtype, const void *Rm, int64_t n, int64_t p, cons
 // block stages by 1-D TMA bulk copies issued two blocks ahead (one mbarrier
 // per stage, waits bounded by the GPU wall clock); the R entries of the next
 // block are loaded by warp 0 during the current chain.
+//
+// Rows past n: every stage slot is zero-filled once per launch and a copy
+// never writes past the rounded column length, so those rows read as x = 0
+// (the one chunk that holds the column's last rows is cleared past n by the
+// thread that owns it); dr is kept at 0 there, so they add nothing to a dot.
 constexpr uint64_t BLK_WAIT_NS = 1000ull * 1000ull * 1000ull;  // 1 s per stage wait
+
+// a*b rounded on its own (never contracted into a following add), so the
+// chain's step and the stored coefficient agree bit for bit.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+// N values of a 16-byte aligned shared-memory row, in 16-byte loads.
+template <typename A, int N> __device__ __forceinline__ void lds_row(const A *p, A (&out)[N])
+{
+    static_assert((N * sizeof(A)) % 16 == 0, "row of whole 16-byte vectors");
+    if constexpr (sizeof(A) == 4) {
+        const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+        for (int i = 0; i < N / 4; ++i) {
+            const float4 v = q[i];
+            out[4 * i] = v.x;
+            out[4 * i + 1] = v.y;
+            out[4 * i + 2] = v.z;
+            out[4 * i + 3] = v.w;
+        }
+    } else {
+        const double2 *q = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            const double2 v = q[i];
+            out[2 * i] = v.x;
+            out[2 * i + 1] = v.y;
+        }
+    }
+}
 
 template <typename T, int RPT, int B>
 __global__ void __launch_bounds__(256, 1)
@@ -391,9 +427,12 @@ __global__ void __launch_bounds__(256, 1)
     using R = typename E::res;
     using V = typename E::vec;
     constexpr int VEC = E::VEC;
-    constexpr int NT = 256, NW = 8;
+    constexpr int NT = 256, NW = 8;  // every warp owns rows; warp 0 also runs the scalar chain
+    constexpr int NTT = NT;
+    constexpr int CW = 0;
     constexpr int QPL = (B * B + 31) / 32;  // correlation entries per lane of warp 0
     static_assert(B == 16 || B == 8, "block of 8 or 16 coordinates");
+    static_assert(B <= 32 && (B * sizeof(A)) % 16 == 0, "block rows of whole 16-byte vectors");
     constexpr A RES_FLOOR = sizeof(A) == 4 ? (A)4.76837158203125e-07 : (A)8.881784197001252e-16;
     const int64_t ld = gram_ld(w);
     extern __shared__ __align__(16) unsigned char smem[];
@@ -406,21 +445,31 @@ __global__ void __launch_bounds__(256, 1)
     unsigned char *stages = smem + stage_off;  // 2 stages of B columns, col_stride bytes apart
     uint64_t *mbar = reinterpret_cast<uint64_t *>(stages + 2 * (size_t)B * col_stride);
     __shared__ A red[NW][B];
-    __shared__ A dks[B];
-    __shared__ A Qs[B][B + 1];
-    __shared__ A zts[B], bs[B];
+    __shared__ __align__(16) A dks[B];
+    __shared__ __align__(16) A QT[B * B];       // QT[k*B + i] = R(coordinate k, coordinate i) of the block
+    __shared__ __align__(16) A zts[B];
+    __shared__ __align__(16) A bs[B];
+    __shared__ __align__(16) A cblk[2][B];      // c of each stage's coordinates (0 past the block's end)
+    __shared__ int posblk[2][B];                // working-set position of each stage's coordinates
     __shared__ unsigned int scan_s[NW + 1];
-    __shared__ int flag_s, mv_s, nz_s;
+    __shared__ int flag_s, mv_s, nz_s, to_s;
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) {
         flag_s = 0;
+        to_s = 0;
         mbar_init(smem_u32(&mbar[0]), 1);
         mbar_init(smem_u32(&mbar[1]), 1);
         fence_mbar_init();
     }
+    {  // zero-fill both stages (rows past n and unused slots read as 0)
+        float4 *z = reinterpret_cast<float4 *>(stages);
+        const int nz16 = (int)(2 * (size_t)B * col_stride / 16);
+        for (int t = tid; t < nz16; t += NTT) z[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        fence_proxy_async_smem();
+    }
     __syncthreads();
-    for (int64_t t = tid; t < w; t += NT) {
+    for (int64_t t = tid; t < w; t += NTT) {
         const int32_t j = idx[t];
         if (j < 0 || (int64_t)j >= p) {
             flag_s = 1;
@@ -437,7 +486,7 @@ __global__ void __launch_bounds__(256, 1)
         if (tid == 0) atomicOr(&sc->status, ST_BAD_INDEX);
         return;
     }
-    for (int64_t t = tid; t < w; t += NT) {
+    for (int64_t t = tid; t < w; t += NTT) {
         const T *col = X + (int64_t)idx_s[t] * ldx;
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(col), "r"(copy_bytes) : "memory");
     }
@@ -460,90 +509,109 @@ __global__ void __launch_bounds__(256, 1)
 
     // one sweep over len coordinates; returns false on a stage-wait timeout
     auto sweep = [&](bool full, int64_t len, bool &moved_out, bool &newnz_out) -> bool {
-        bool moved = false, newnz = false;  // meaningful in warp 0
+        bool moved = false, newnz = false;  // per lane of the chain warp
         const int64_t nblk = (len + B - 1) / B;
-        auto pos_of = [&](int64_t t) -> int { return full ? (int)t : (int)act_s[t]; };
-        // one thread issues the column copies of block blk into stage (bseq+rel)%2
+        // warp 1 issues the column copies of block blk into stage gblk%2, one
+        // column per lane, and records the block's positions and centres beside it
         auto issue_block = [&](int64_t blk, uint32_t gblk) {
             const int64_t t0 = blk * B;
             const int cnt = (int)((len - t0 < B) ? len - t0 : B);
             const int st = (int)(gblk & 1u);
             const uint32_t bar = smem_u32(&mbar[st]);
-            fence_proxy_async_smem();
-            mbar_expect_tx(bar, (uint32_t)cnt * copy_bytes);
-            for (int k = 0; k < cnt; ++k) {
-                const T *col = X + (int64_t)idx_s[pos_of(t0 + k)] * ldx;
-                bulk_g2s(smem_u32(stages + ((size_t)st * B + k) * col_stride), col, copy_bytes, bar);
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                mbar_expect_tx(bar, (uint32_t)cnt * copy_bytes);
+            }
+            __syncwarp();
+            if (lane < B) {
+                const int kk = (lane < cnt) ? lane : 0;
+                const int pos = full ? (int)(t0 + kk) : (int)act_s[t0 + kk];
+                posblk[st][lane] = pos;
+                cblk[st][lane] = (lane < cnt) ? c_s[pos] : (A)0;
+                if (lane < cnt) {
+                    const T *col = X + (int64_t)idx_s[pos] * ldx;
+                    fence_proxy_async_smem();
+                    bulk_g2s(smem_u32(stages + ((size_t)st * B + lane) * col_stride), col, copy_bytes, bar);
+                }
             }
         };
-        // R entries of block blk (i > k, both inside the block), clamped loads
+        // R entries of the block in stage st: qn[m] = R(k, i), k = e / B, i = e % B
         A qn[QPL];
-        auto load_q = [&](int64_t blk) {
-            const int64_t t0 = blk * B;
-            const int cnt = (int)((len - t0 < B) ? len - t0 : B);
+        auto load_q = [&](int st) {
 #pragma unroll
             for (int m = 0; m < QPL; ++m) {
                 const int e = lane + 32 * m;
-                int i = e / B, k = e % B;
-                if (i >= cnt) i = cnt - 1;
-                if (k >= cnt) k = cnt - 1;
-                qn[m] = Rm[(int64_t)pos_of(t0 + i) * ld + pos_of(t0 + k)];
+                const int k = (e / B) % B, i = e % B;
+                qn[m] = Rm[(int64_t)posblk[st][k] * ld + posblk[st][i]];
             }
         };
-        if (tid == 32) {
+        if (wid == 1) {
             if (nblk > 0) issue_block(0, bseq);
             if (nblk > 1) issue_block(1, bseq + 1);
         }
-        if (wid == 0 && nblk > 0) load_q(0);
+        __syncthreads();
+        if (wid == CW && nblk > 0) load_q((int)(bseq & 1u));
         for (int64_t blk = 0; blk < nblk; ++blk) {
             const uint32_t gblk = bseq + (uint32_t)blk;
             const int st = (int)(gblk & 1u);
             const int64_t t0 = blk * B;
             const int cnt = (int)((len - t0 < B) ? len - t0 : B);
-            const bool ok = mbar_wait_bounded(smem_u32(&mbar[st]), (gblk >> 1) & 1u, BLK_WAIT_NS);
-            if (!__syncthreads_and(ok)) {
-                if (tid == 32) {  // drain: this block's copies and, if issued, the next block's
-                    mbar_wait_bounded(smem_u32(&mbar[st]), (gblk >> 1) & 1u, BLK_WAIT_NS);
-                    if (blk + 1 < nblk)
-                        mbar_wait_bounded(smem_u32(&mbar[(gblk + 1) & 1u]), ((gblk + 1) >> 1) & 1u, BLK_WAIT_NS);
-                }
-                __syncthreads();
-                return false;
-            }
-            // xd = x - c (rows past n, and coordinates past cnt, are 0) and the
-            // partial dots with dr, from the staged columns
+            int my_pos = 0;
+            A my_b = 0, my_is = 0, my_g = 0;
+            A dk[B];
             A xd[B][RPT][VEC];
-            A part[B];
-            const unsigned char *stg = stages + (size_t)st * B * col_stride;
-#pragma unroll
-            for (int k = 0; k < B; ++k) {
-                const A ck = (k < cnt) ? c_s[pos_of(t0 + k)] : (A)0;
-                const V *colv = reinterpret_cast<const V *>(stg + (size_t)k * col_stride);
-                A acc = 0;
-#pragma unroll
-                for (int q = 0; q < RPT; ++q) {
-                    const int64_t ch = (int64_t)q * NT + tid;
-                    const int nv = (k >= cnt) ? 0 : (ch < nfull ? VEC : (ch == nfull ? tail : 0));
-                    A e[VEC];
-                    if (nv > 0) unpack(colv[ch], e);
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) {
-                        xd[k][q][v] = (v < nv) ? e[v] - ck : (A)0;
-                        acc = fma(xd[k][q][v], dr[q][v], acc);
-                    }
+            if (wid == CW) {
+                // chain warp: this lane's coordinate (its b, 1/s and g_ref change
+                // only in its own block) and the block's R entries
+                if (lane < B) {
+                    my_pos = posblk[st][lane];
+                    my_b = (A)beta_s[my_pos];
+                    my_is = is_s[my_pos];
+                    my_g = g_s[my_pos];
                 }
-                part[k] = acc;
-            }
-            if (wid == 0) {
 #pragma unroll
                 for (int m = 0; m < QPL; ++m) {
                     const int e = lane + 32 * m;
-                    if (e < B * B) Qs[e / B][e % B] = qn[m];
+                    if (e < B * B) QT[e] = qn[m];
                 }
             }
-            // butterfly reduce-scatter: after it the lanes 32/B apart share one
-            // column's warp sum
             {
+                if (!mbar_wait_bounded(smem_u32(&mbar[st]), (gblk >> 1) & 1u, BLK_WAIT_NS)) to_s = 1;
+                unsigned char *stg = stages + (size_t)st * B * col_stride;
+                // the one thread that owns the chunk holding row n-1 clears the rows past n
+                if (tail) {
+#pragma unroll
+                    for (int q = 0; q < RPT; ++q) {
+                        if ((int64_t)q * NT + tid == nfull) {
+                            for (int k = 0; k < cnt; ++k) {
+                                T *cp = reinterpret_cast<T *>(stg + (size_t)k * col_stride);
+                                for (int v = tail; v < VEC; ++v) cp[nfull * VEC + v] = (T)0;
+                            }
+                        }
+                    }
+                }
+                // xd = x - c and the partial dots with dr, from the staged columns
+                A cb[B];
+                lds_row<A, B>(cblk[st], cb);
+                A part[B];
+#pragma unroll
+                for (int k = 0; k < B; ++k) {
+                    const V *colv = reinterpret_cast<const V *>(stg + (size_t)k * col_stride);
+                    A acc = 0;
+#pragma unroll
+                    for (int q = 0; q < RPT; ++q) {
+                        A e[VEC];
+                        unpack(colv[q * NT + tid], e);
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            xd[k][q][v] = e[v] - cb[k];
+                            acc = fma(xd[k][q][v], dr[q][v], acc);
+                        }
+                    }
+                    part[k] = acc;
+                }
+                // butterfly reduce-scatter: after it the lanes 32/B apart share one
+                // column's warp sum
                 A v8[B / 2];
                 const bool hi16 = (lane & 16) != 0;
 #pragma unroll
@@ -585,64 +653,85 @@ __global__ void __launch_bounds__(256, 1)
                 }
                 if ((lane & (32 / B - 1)) == 0) red[wid][col] = v1;
             }
-            __syncthreads();  // every thread has read stage st; red complete
-            if (tid == 32 && blk + 2 < nblk) issue_block(blk + 2, gblk + 2);
-            if (wid == 0) {
-                int my_pos = 0;
-                A my_is = 0;
-                if (lane < cnt) {
-                    my_pos = pos_of(t0 + lane);
+            __syncthreads();  // every data warp has read stage st; red complete
+            if (to_s) {       // a stage wait ran out: drain what is in flight and stop
+                if (tid == 32) {
+                    mbar_wait_bounded(smem_u32(&mbar[st]), (gblk >> 1) & 1u, BLK_WAIT_NS);
+                    if (blk + 1 < nblk)
+                        mbar_wait_bounded(smem_u32(&mbar[(gblk + 1) & 1u]), ((gblk + 1) >> 1) & 1u, BLK_WAIT_NS);
+                }
+                __syncthreads();
+                return false;
+            }
+            if (wid == 1 && blk + 2 < nblk) issue_block(blk + 2, gblk + 2);
+            if (wid == CW) {
+                if (lane < B) {
                     A a = 0;
 #pragma unroll
                     for (int ww = 0; ww < NW; ++ww) a += red[ww][lane];
-                    const A b = (A)beta_s[my_pos];
-                    my_is = is_s[my_pos];
-                    zts[lane] = fma(g_s[my_pos] - a, my_is * inv_n, b);
-                    bs[lane] = b;
+                    zts[lane] = (lane < cnt) ? fma(my_g - a, my_is * inv_n, my_b) : (A)0;
+                    bs[lane] = (lane < cnt) ? my_b : (A)0;
                 }
-                if (blk + 1 < nblk) load_q(blk + 1);
                 __syncwarp();
                 A zt[B], bb[B];
+                lds_row<A, B>(zts, zt);
+                lds_row<A, B>(bs, bb);
+                if (blk + 1 < nblk) load_q(st ^ 1);
+                // the sequential chain: only what the next coordinate depends on
+                A my_s = 0;
 #pragma unroll
                 for (int k = 0; k < B; ++k) {
-                    zt[k] = zts[k];
-                    bb[k] = bs[k];
-                }
+                    const A s = zt[k];
+                    if (lane == k) my_s = s;
+                    const A d = mul_rn(soft_threshold(s, thr), inv_den) - bb[k];
+                    if (k + 1 < B) {
+                        A qr[B];
+                        lds_row<A, B>(&QT[k * B], qr);
 #pragma unroll
-                for (int k = 0; k < B; ++k) {
-                    if (k < cnt) {
-                        const A s = zt[k];
-                        const A nb = soft_threshold(s, thr) * inv_den;
-                        const A d = nb - bb[k];
-                        const A tol = fmax(epsA, RES_FLOOR * (fabs(s) + fabs(nb)));
-                        moved |= (fabs(d) >= tol);
-                        newnz |= (bb[k] == (A)0 && fabs(nb) >= tol);
-#pragma unroll
-                        for (int i = k + 1; i < B; ++i) zt[i] = fma(-d, Qs[i][k], zt[i]);
-                        if (lane == k) {
-                            dks[k] = d * my_is;
-                            beta_s[my_pos] = (R)nb;
-                        }
-                    } else if (lane == k) {
-                        dks[k] = (A)0;
+                        for (int i = k + 1; i < B; ++i) zt[i] = fma(-d, qr[i], zt[i]);
                     }
                 }
-                updates += (unsigned long long)cnt;
+                // per coordinate (lane k holds coordinate k): new value, step,
+                // convergence and new-nonzero tests
+                if (lane < B) {
+                    if (lane < cnt) {
+                        const A nb = mul_rn(soft_threshold(my_s, thr), inv_den);
+                        const A d = nb - my_b;
+                        const A tol = fmax(epsA, RES_FLOOR * (fabs(my_s) + fabs(nb)));
+                        moved |= (fabs(d) >= tol);
+                        newnz |= (my_b == (A)0 && fabs(nb) >= tol);
+                        dks[lane] = d * my_is;
+                        beta_s[my_pos] = (R)nb;
+                    } else {
+                        dks[lane] = (A)0;
+                    }
+                }
             }
+            updates += (unsigned long long)cnt;
             __syncthreads();
+            {
+                lds_row<A, B>(dks, dk);
 #pragma unroll
-            for (int k = 0; k < B; ++k) {
-                const A ds = dks[k];
+                for (int k = 0; k < B; ++k) {
+#pragma unroll
+                    for (int q = 0; q < RPT; ++q)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) dr[q][v] = fma(dk[k], xd[k][q][v], dr[q][v]);
+                }
 #pragma unroll
                 for (int q = 0; q < RPT; ++q)
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) dr[q][v] = fma(ds, xd[k][q][v], dr[q][v]);
+                    for (int v = 0; v < VEC; ++v)
+                        if (((int64_t)q * NT + tid) * VEC + v >= n) dr[q][v] = (A)0;
             }
         }
         bseq += (uint32_t)nblk;
-        if (tid == 0) {
-            mv_s = moved;
-            nz_s = newnz;
+        if (wid == CW) {
+            const bool am = __any_sync(0xffffffffu, moved), an = __any_sync(0xffffffffu, newnz);
+            if (lane == 0) {
+                mv_s = am;
+                nz_s = an;
+            }
         }
         __syncthreads();
         moved_out = mv_s != 0;
@@ -673,9 +762,9 @@ __global__ void __launch_bounds__(256, 1)
             status = ST_TIMEOUT;
             break;
         }
-        const int64_t per = (w + NT - 1) / NT;
-        const int64_t b0 = (int64_t)tid * per;
-        const int64_t b1 = (b0 + per < w) ? b0 + per : w;
+        const int64_t per = (w + NT - 1) / NT;  // the 256 data threads share the scan
+        const int64_t b0 = (wid < NW) ? (int64_t)tid * per : w;
+        const int64_t b1 = (wid < NW && b0 + per < w) ? b0 + per : w;
         unsigned int c = 0;
         for (int64_t t = b0; t < b1; ++t) c += (beta_s[t] != (R)0);
         unsigned int incl = c;
@@ -684,7 +773,7 @@ __global__ void __launch_bounds__(256, 1)
             const unsigned int v = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += v;
         }
-        if (lane == 31) scan_s[wid] = incl;
+        if (lane == 31 && wid < NW) scan_s[wid] = incl;
         __syncthreads();
         if (tid == 0) {
             unsigned int a = 0;
@@ -696,7 +785,7 @@ __global__ void __launch_bounds__(256, 1)
             scan_s[NW] = a;
         }
         __syncthreads();
-        unsigned int pos = scan_s[wid] + incl - c;
+        unsigned int pos = (wid < NW) ? scan_s[wid] + incl - c : 0u;
         for (int64_t t = b0; t < b1; ++t)
             if (beta_s[t] != (R)0) act_s[pos++] = (uint16_t)t;
         const int64_t na = scan_s[NW];
@@ -721,8 +810,8 @@ __global__ void __launch_bounds__(256, 1)
         if (status) break;
     }
     __syncthreads();
-    for (int64_t t = tid; t < w; t += NT) beta[idx_s[t]] = beta_s[t];
-    if (r_io) {
+    for (int64_t t = tid; t < w; t += NTT) beta[idx_s[t]] = beta_s[t] + (R)0;
+    if (r_io && wid < NW) {
 #pragma unroll
         for (int q = 0; q < RPT; ++q) {
             const int64_t ch = (int64_t)q * NT + tid;
@@ -752,7 +841,9 @@ static cudaError_t cd_blk_t(const T *X, int64_t n, int64_t ldx, const void *cvec
     const size_t stage_off = (meta + 127) & ~(size_t)127;
     // copy n*sizeof(T) rounded up to 16 bytes (never past the column's ldx extent)
     const uint32_t copy_bytes = (uint32_t)(((uint64_t)n * sizeof(T) + 15) & ~(uint64_t)15);
-    const uint32_t col_stride = (copy_bytes + 127u) & ~127u;
+    // a slot holds every thread's chunks (RPT per thread), so no read leaves it
+    const uint32_t chunk_bytes = (uint32_t)(RPT * 256 * 16);
+    const uint32_t col_stride = std::max((copy_bytes + 127u) & ~127u, chunk_bytes);
     const size_t smem = stage_off + 2 * (size_t)B * col_stride + 16;
     if (smem > 227 * 1024 - 1024) return cudaErrorInvalidValue;  // caller falls back
     auto kern = k_cd_blk<T, RPT, B>;
@@ -777,7 +868,8 @@ size_t cd_blk_smem(int dtype, int64_t n, int64_t w)
     const size_t meta = (size_t)((w + 3) & ~(int64_t)3) * (3 * a + a + 4 + 2);
     const size_t stage_off = (meta + 127) & ~(size_t)127;
     const size_t copy = ((size_t)n * es + 15) & ~(size_t)15;
-    const size_t colst = (copy + 127) & ~(size_t)127;
+    const int rpt = (nch <= 256) ? 1 : 2;
+    const size_t colst = std::max((copy + 127) & ~(size_t)127, (size_t)rpt * 256 * 16);
     return stage_off + 2 * (size_t)B * colst + 16;
 }
 
