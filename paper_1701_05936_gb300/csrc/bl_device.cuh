@@ -148,10 +148,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 }
 
 // Soft-thresholding operator S(z, t) = sign(z) max(|z| - t, 0).
+// S(z, t) = sign(z) max(abs(z) - t, 0), written as z - clamp(z, -t, t): the
+// same roundings (z - t, z + t or an exact +0) without a compare-and-select on
+// the dependent path of coordinate descent.
 template <typename A> __device__ __forceinline__ A soft_threshold(A z, A t)
 {
-    A a = fabs(z) - t;
-    return a > (A)0 ? copysign(a, z) : (A)0;
+    return z - fmin(fmax(z, -t), t);
 }
 
 }  // namespace bl

@@ -429,7 +429,9 @@ __global__ void __launch_bounds__(256, 1)
     constexpr int VEC = E::VEC;
     constexpr int NT = 256, NW = 8;  // every warp owns rows; warp 0 also runs the scalar chain
     constexpr int NTT = NT;
-    constexpr int CW = 0;
+    constexpr int CW = 0;                  // chain warp
+    constexpr int ISSUE0 = 1, NISSUE = 4;  // warps 1..4 issue the column copies
+    static_assert(B % NISSUE == 0, "copies spread evenly over the issuing warps");
     constexpr int QPL = (B * B + 31) / 32;  // correlation entries per lane of warp 0
     static_assert(B == 16 || B == 8, "block of 8 or 16 coordinates");
     static_assert(B <= 32 && (B * sizeof(A)) % 16 == 0, "block rows of whole 16-byte vectors");
@@ -511,27 +513,30 @@ __global__ void __launch_bounds__(256, 1)
     auto sweep = [&](bool full, int64_t len, bool &moved_out, bool &newnz_out) -> bool {
         bool moved = false, newnz = false;  // per lane of the chain warp
         const int64_t nblk = (len + B - 1) / B;
-        // warp 1 issues the column copies of block blk into stage gblk%2, one
-        // column per lane, and records the block's positions and centres beside it
+        // warps 1..4 issue the column copies of block blk into stage gblk%2, one
+        // column per lane (a copy instruction waits for the copy engine, so
+        // spreading them keeps each warp's share short), and record the block's
+        // positions and centres beside the columns.  The stage's previous
+        // contents were consumed into registers before the barrier that
+        // precedes this.
         auto issue_block = [&](int64_t blk, uint32_t gblk) {
             const int64_t t0 = blk * B;
             const int cnt = (int)((len - t0 < B) ? len - t0 : B);
             const int st = (int)(gblk & 1u);
             const uint32_t bar = smem_u32(&mbar[st]);
-            if (lane == 0) {
-                fence_proxy_async_smem();
-                mbar_expect_tx(bar, (uint32_t)cnt * copy_bytes);
-            }
-            __syncwarp();
-            if (lane < B) {
-                const int kk = (lane < cnt) ? lane : 0;
+            // the stage's one arrival carries the expected byte count; copies issued
+            // by the other warps may land before it, but the phase cannot complete
+            // until that arrival has been made
+            if (wid == ISSUE0 && lane == 0) mbar_expect_tx(bar, (uint32_t)cnt * copy_bytes);
+            const int kl = (wid - ISSUE0) * (B / NISSUE) + lane;  // this lane's coordinate of the block
+            if (lane < B / NISSUE) {
+                const int kk = (kl < cnt) ? kl : 0;
                 const int pos = full ? (int)(t0 + kk) : (int)act_s[t0 + kk];
-                posblk[st][lane] = pos;
-                cblk[st][lane] = (lane < cnt) ? c_s[pos] : (A)0;
-                if (lane < cnt) {
+                posblk[st][kl] = pos;
+                cblk[st][kl] = (kl < cnt) ? c_s[pos] : (A)0;
+                if (kl < cnt) {
                     const T *col = X + (int64_t)idx_s[pos] * ldx;
-                    fence_proxy_async_smem();
-                    bulk_g2s(smem_u32(stages + ((size_t)st * B + lane) * col_stride), col, copy_bytes, bar);
+                    bulk_g2s(smem_u32(stages + ((size_t)st * B + kl) * col_stride), col, copy_bytes, bar);
                 }
             }
         };
@@ -545,7 +550,8 @@ __global__ void __launch_bounds__(256, 1)
                 qn[m] = Rm[(int64_t)posblk[st][k] * ld + posblk[st][i]];
             }
         };
-        if (wid == 1) {
+        const bool issuer = wid >= ISSUE0 && wid < ISSUE0 + NISSUE;
+        if (issuer) {
             if (nblk > 0) issue_block(0, bseq);
             if (nblk > 1) issue_block(1, bseq + 1);
         }
@@ -663,7 +669,7 @@ __global__ void __launch_bounds__(256, 1)
                 __syncthreads();
                 return false;
             }
-            if (wid == 1 && blk + 2 < nblk) issue_block(blk + 2, gblk + 2);
+            if (issuer && blk + 2 < nblk) issue_block(blk + 2, gblk + 2);
             if (wid == CW) {
                 if (lane < B) {
                     A a = 0;
