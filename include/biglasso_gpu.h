@@ -121,8 +121,9 @@ typedef struct {
 /* Per-kernel timing collected with CUDA events on the ctx stream while timing
  * is enabled (bl_ctx_set_timing).  Kinds: 0 standardize, 1 lambda_max,
  * 2 bedpp_init, 3 screen, 4 compact, 5 cd, 6 residual, 7 zpass, 8 record,
- * 9 gref (the FP64 reference gradients each CD launch starts from). */
-#define BL_NUM_KINDS 10
+ * 9 gref (the FP64 reference gradients each CD launch starts from),
+ * 10 xtr (the batched z pass of bl_xtr_batched), 11 reserved. */
+#define BL_NUM_KINDS 12
 typedef struct {
     int64_t launches[BL_NUM_KINDS];
     double ms[BL_NUM_KINDS];         /* summed device time */
@@ -266,6 +267,35 @@ int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int
                 bl_path *out);
 
 /* ------------------------------------------------ allocation-free variant -- */
+
+/* Batched z pass (Sec. 3.1.2 with formula (3) of Sec. 3.1.1): one read of X
+ * serves nrhs residual vectors at once, e.g. the folds of a cross-validation
+ * and several responses, each standardized on its own row subset ("fit"):
+ *
+ *   Z[b*ldz + j] = (x_j' r_b - c_fj * sum_i r_bi) / (n_f * s_fj),  f = fit_of[b],
+ *
+ * for j < p and b < nrhs.  x_j' r_b runs on the tensor cores with TF32 inputs
+ * (the upper 19 bits of each FP32 value) and FP32 accumulation, so
+ * abs(Z - exact) is of order 2^-9 * ||x_j|| * ||r_b|| / (n_f s_fj); callers that
+ * take a decision from Z recheck the uncertain entries in FP32 (bl_kkt_check).
+ *   X        device, FP32 (BL_F32 only; others return BL_ERR_UNSUPPORTED),
+ *            column-major n x p, ldx >= n, ldx*4 a multiple of 16, X 16-byte aligned.
+ *   R        device FP32, column-major n x nrhs (ldr >= n, ldr*4 a multiple of 16,
+ *            16-byte aligned); r_b must be 0 on the rows outside fit f.
+ *   nrhs     1 .. 256.
+ *   center, scale  device FP64, nfit x p, row f at offset f*ldc (ldc >= p): c_f, s_f
+ *            of fit f (as bl_standardize computes them on the fit's rows); a column
+ *            with s_fj = 0 gives Z = 0.
+ *   n_fit    host FP64 [nfit]: the row count n_f of each fit.
+ *   fit_of   device int32 [nrhs]: the fit of each right-hand side, in [0, nfit).
+ *   Z        device FP32, nrhs x ldz (ldz >= p), written for j < p.
+ * Enqueued on the ctx stream and synchronized at the end.  BL_ERR_ARG on NULL
+ * pointers, bad sizes, strides or alignment (before any launch);
+ * BL_ERR_UNSUPPORTED for a non-FP32 design; BL_ERR_TIMEOUT if a pipeline wait
+ * of the kernel ran out (its outputs are then not valid). */
+int bl_xtr_batched(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx, const float *R,
+                   int64_t ldr, int64_t nrhs, const double *center, const double *scale, int64_t ldc,
+                   const double *n_fit, int64_t nfit, const int32_t *fit_of, float *Z, int64_t ldz);
 
 /* Largest working set that bl_cd_active_noalloc accepts. */
 #define BL_NOALLOC_MAX_WORK 4096

@@ -28,7 +28,7 @@ BL_F64, BL_F32, BL_BF16, BL_I8 = 0, 1, 2, 3
 BL_SCREEN_NONE, BL_SCREEN_SSR, BL_SCREEN_SSR_BEDPP = 0, 1, 2
 BL_CD_RESIDUAL, BL_CD_COVARIANCE, BL_CD_BLOCKED = 0, 1, 2
 KINDS = ["standardize", "lambda_max", "bedpp_init", "screen", "compact", "cd", "residual", "zpass", "record",
-         "gref"]
+         "gref", "xtr", "reserved"]
 
 _STATUS = {0: "BL_OK", -1: "BL_ERR_ARG", -2: "BL_ERR_CUDA", -3: "BL_ERR_OOM", -4: "BL_ERR_NOT_CONVERGED",
            -5: "BL_ERR_TIMEOUT", -6: "BL_ERR_UNSUPPORTED", -7: "BL_ERR_CAPACITY"}
@@ -56,7 +56,8 @@ class bl_path(C.Structure):
 
 
 class bl_timing(C.Structure):
-    _fields_ = [("launches", C.c_int64 * 10), ("ms", C.c_double * 10), ("bytes", C.c_double * 10),
+    _fields_ = [("launches", C.c_int64 * len(KINDS)), ("ms", C.c_double * len(KINDS)),
+                ("bytes", C.c_double * len(KINDS)),
                 ("kernel_launches", C.c_int64), ("cd_updates", C.c_int64)]
 
 
@@ -96,6 +97,8 @@ def lib():
                                 C.POINTER(bl_path)],
                 "bl_cd_active_noalloc": [_int, _vp, *X[:1], _int, _i64, _i64, _i64, _vp, _vp, _vp, _i64, _dbl,
                                          _dbl, _vp, _vp, _dbl, _i64, C.POINTER(_i64), C.c_char_p, C.c_size_t],
+                "bl_xtr_batched": [_vp, *X, _vp, _i64, _i64, _vp, _vp, _i64, C.POINTER(_dbl), _i64, _vp, _vp,
+                                   _i64],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -215,6 +218,20 @@ def bl_cd_active(ctx, X, n, center, scale, work_idx, lam, alpha, beta, r, eps, m
                             int(max_sweeps), C.byref(sw))
     ctx.check(st, allow=(BL_ERR_NOT_CONVERGED,))
     return sw.value, st
+
+
+def bl_xtr_batched(ctx, X, n, R, center, scale, n_fit, fit_of, Z):
+    """Batched z pass: Z[b, j] = (x_j' r_b - c_fj sum r_b)/(n_f s_fj), f = fit_of[b].
+
+    R is a (nrhs, ldr) FP32 tensor (row b = r_b, zero outside fit f's rows),
+    center/scale are (nfit, p) FP64, n_fit a sequence of nfit row counts,
+    fit_of an int32 tensor of nrhs fits and Z an (nrhs, ldz) FP32 output.
+    """
+    nrhs, ldr = R.shape
+    nfit, ldc = center.shape
+    nf = (C.c_double * nfit)(*[float(v) for v in n_fit])
+    ctx.check(lib().bl_xtr_batched(ctx.h, *design_args(X, n), _ptr(R), int(ldr), int(nrhs), _ptr(center),
+                                   _ptr(scale), int(ldc), nf, int(nfit), _ptr(fit_of), _ptr(Z), int(Z.shape[1])))
 
 
 def bl_cd_active_noalloc(device, stream, X, n, center, scale, work_idx, lam, alpha, beta, r, eps,

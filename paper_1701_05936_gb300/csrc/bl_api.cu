@@ -54,6 +54,8 @@ struct bl_ctx {
     bl_timing totals{};
     void *gram = nullptr;      // correlation matrix of the working set (covariance-form CD)
     size_t gram_bytes = 0;
+    void *xtr = nullptr;       // batched z pass: per-fit epilogue vectors, sum r, row counts
+    size_t xtr_bytes = 0;
     int64_t kernels = 0;
     int64_t cd_updates = 0;
 };
@@ -275,6 +277,7 @@ extern "C" int bl_ctx_destroy(bl_ctx *ctx)
     for (auto e : ctx->pool) cudaEventDestroy(e);
     if (ctx->ws.base) cudaFree(ctx->ws.base);
     if (ctx->gram) cudaFree(ctx->gram);
+    if (ctx->xtr) cudaFree(ctx->xtr);
     if (ctx->sc_host) cudaFreeHost(ctx->sc_host);
     delete ctx;
     return BL_OK;
@@ -517,6 +520,50 @@ extern "C" int bl_cd_active(bl_ctx *ctx, const void *X, int dtype, int64_t n, in
     return BL_OK;
 }
 
+// ======================================================= batched z pass
+extern "C" int bl_xtr_batched(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx, const float *R,
+                              int64_t ldr, int64_t nrhs, const double *center, const double *scale, int64_t ldc,
+                              const double *n_fit, int64_t nfit, const int32_t *fit_of, float *Z, int64_t ldz)
+{
+    int st = check_design(ctx, X, dtype, n, p, ldx);
+    if (st) return st;
+    if (dtype != BL_F32) return fail(ctx, BL_ERR_UNSUPPORTED, "the batched z pass takes FP32 designs");
+    if (!R || !center || !scale || !n_fit || !fit_of || !Z) return fail(ctx, BL_ERR_ARG, "NULL argument");
+    if (nrhs < 1 || nrhs > 256) return fail(ctx, BL_ERR_ARG, "nrhs must be in 1..256");
+    if (nfit < 1 || nfit > 256) return fail(ctx, BL_ERR_ARG, "nfit must be in 1..256");
+    if (ldr < n || (ldr * 4) % 16 != 0 || ((uintptr_t)R) % 16 != 0)
+        return fail(ctx, BL_ERR_ARG, "R needs ldr >= n, ldr*4 a multiple of 16 and 16-byte alignment");
+    if (ldc < p || ldz < p) return fail(ctx, BL_ERR_ARG, "ldc and ldz must be >= p");
+    for (int64_t f = 0; f < nfit; ++f)
+        if (!(n_fit[f] >= 1.0)) return fail(ctx, BL_ERR_ARG, "every fit needs at least one row");
+    if (xtr_stages((int)nrhs, nullptr) == 0) return fail(ctx, BL_ERR_UNSUPPORTED, "nrhs too large for shared memory");
+    ctx->err.clear();
+    CK(cudaSetDevice(ctx->device));
+    if ((st = ensure_ws(ctx, n, p))) return st;
+    // per-fit FP32 c and 1/(n s), sum r per right-hand side, row counts
+    const size_t fitb = (size_t)nfit * (size_t)p * 4, need = 2 * fitb + 256 * 4 + 256 * 8 + 256;
+    if (ctx->xtr_bytes < need) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (ctx->xtr) cudaFree(ctx->xtr);
+        ctx->xtr = nullptr;
+        ctx->xtr_bytes = 0;
+        CK(cudaMalloc(&ctx->xtr, need));
+        ctx->xtr_bytes = need;
+    }
+    char *b = (char *)ctx->xtr;
+    float *cfit = (float *)b, *insfit = (float *)(b + fitb), *sumr = (float *)(b + 2 * fitb);
+    double *nfd = (double *)(b + 2 * fitb + 256 * 4);
+    CK(cudaMemcpyAsync(nfd, n_fit, (size_t)nfit * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(&ctx->ws.sc->status, 0, sizeof(int), ctx->stream));
+    int slot = tbegin(ctx, 10);
+    LAUNCH(3, launch_xtr((const float *)X, n, p, ldx, R, ldr, (int)nrhs, center, scale, ldc, nfd, (int)nfit, fit_of,
+                         cfit, insfit, sumr, Z, ldz, ctx->ws.sc, ctx->num_sms, ctx->stream));
+    tend(ctx, slot, (double)n * (double)p * 4.0);
+    if ((st = sync_sc(ctx))) return st;
+    if (ctx->sc_host->status & ST_TIMEOUT) return fail(ctx, BL_ERR_TIMEOUT, "batched z pass: a pipeline wait ran out");
+    return BL_OK;
+}
+
 // ================================================================= the path
 extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx,
                            const double *y, const bl_options *opt, const double *lambdas_in, int K,
@@ -614,6 +661,7 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
         if (ctx->gram_bytes < need) {
             CK(cudaStreamSynchronize(s));
             if (ctx->gram) cudaFree(ctx->gram);
+    if (ctx->xtr) cudaFree(ctx->xtr);
             ctx->gram = nullptr;
             ctx->gram_bytes = 0;
             CK(cudaMalloc(&ctx->gram, need));

@@ -147,7 +147,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
     return true;
 }
 
-// Soft-thresholding operator S(z, t) = sign(z) max(|z| - t, 0).
 // S(z, t) = sign(z) max(abs(z) - t, 0), written as z - clamp(z, -t, t): the
 // same roundings (z - t, z + t or an exact +0) without a compare-and-select on
 // the dependent path of coordinate descent.

@@ -128,6 +128,11 @@ cudaError_t launch_cd_gram(int dtype, const void *Rm, int64_t n, int64_t p, cons
 
 // Residual-form CD in blocks of consecutive coordinates (needs R from
 // launch_gram); cd_blk_ok tells whether this build covers the shape.
+int xtr_stages(int nrhs, size_t *smem);
+cudaError_t launch_xtr(const float *X, int64_t n, int64_t p, int64_t ldx, const float *R, int64_t ldr, int nrhs,
+                       const double *center, const double *scale, int64_t ldc, const double *n_fit_dev, int nfit,
+                       const int32_t *fit_of, float *cfit, float *insfit, float *sumr, float *Z, int64_t ldz,
+                       DevScalars *sc, int num_sms, cudaStream_t st);
 bool cd_blk_ok(int dtype, int64_t n);
 bool cd_blk_fits(int dtype, int64_t n, int64_t w);
 cudaError_t launch_cd_blk(int dtype, const void *X, int64_t n, int64_t p, int64_t ldx, const void *cvec,

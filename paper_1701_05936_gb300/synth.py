@@ -23,6 +23,9 @@ Sec. 4.2 simulated data and Table 2's real-data shapes):
   variance of X beta over sigma^2 equals the SNR.    (1000 x 100,000, FP32)
 * ``genotype``      -- x_ij ~ Binomial(2, MAF_j), MAF_j ~ U[0.05, 0.5], int8;
   k causal effects N(0, 0.3^2); sigma^2 = Var(g)(1-h2)/h2.  (5000 x 500,000)
+* ``batched_ar1``   -- AR(1) rho=0.3 columns shared by m responses (k nonzero
+  N(0,1) effects each, SNR 2) and balanced cross-validation folds: the
+  batched z pass of Sec. 3.1.2.         (2000 x 200,000, 16 responses, 10 folds)
 """
 from __future__ import annotations
 
@@ -145,6 +148,88 @@ def genotype(n=5000, p=500_000, k=50, effect_sd=0.3, h2=0.3, workload=3,
     y = gvals + sigma * g.standard_normal(n)
     return Problem(name or f"geno_{n}x{p}", X, y, n, p, ldx, "i8", beta, alpha,
                    ratio, nlambda, eps, {"k": k, "h2": h2, "sigma": sigma})
+
+
+@dataclass
+class BatchedProblem:
+    """Several responses sharing one raw design, with cross-validation folds
+    (Sec. 3.1.2): the fits are all rows (fit 0) and, for each fold f, the rows
+    whose fold_id differs from f (fit f + 1)."""
+    name: str
+    X: np.ndarray            # shape (p, ldx), storage dtype; column j = X[j, :n]
+    Y: np.ndarray            # float64[m, n]: response r = Y[r]
+    fold_id: np.ndarray      # int8[n] in [0, nfolds)
+    n: int
+    p: int
+    ldx: int
+    m: int
+    nfolds: int
+    dtype: str
+    betas: np.ndarray        # float64[m, p], raw scale
+    alpha: float = 0.5
+    ratio: float = 0.05
+    nlambda: int = 100
+    eps: float = 1e-7
+    meta: dict = field(default_factory=dict)
+
+    def fit_rows(self, f: int) -> np.ndarray:
+        """Row indices of fit f (0: all rows; f >= 1: fold f-1 held out)."""
+        if f == 0:
+            return np.arange(self.n)
+        return np.nonzero(self.fold_id != f - 1)[0]
+
+
+def batched_ar1(n=2000, p=200_000, m=16, nfolds=10, rho=0.3, k=30, snr=2.0,
+                dtype="f32", workload=4, replicate=0, alpha=0.5, ratio=0.05,
+                nlambda=100, eps=1e-7, pad_value=0.0, name=None) -> BatchedProblem:
+    """AR(1) columns (x_j = rho x_{j-1} + sqrt(1-rho^2) e_j, drawn in chunks of
+    columns), m responses with k nonzero N(0,1) effects each at SNR snr (sample
+    Var(X beta)/sigma^2), balanced folds fold_id[perm[i]] = i mod nfolds."""
+    g = rng_for(workload, replicate)
+    X, ldx = _alloc_x(n, p, dtype, pad_value)
+    a = np.sqrt(1.0 - rho * rho)
+    chunk = max(1, (1 << 23) // max(n, 1))
+    prev = None
+    for j0 in range(0, p, chunk):
+        j1 = min(p, j0 + chunk)
+        E = g.standard_normal((j1 - j0, n))
+        for t in range(j1 - j0):
+            prev = E[t] if prev is None else rho * prev + a * E[t]
+            X[j0 + t, :n] = prev
+    betas = np.zeros((m, p))
+    Y = np.empty((m, n))
+    k = min(k, p)
+    for r in range(m):
+        idx = g.choice(p, size=k, replace=False)
+        betas[r, idx] = g.standard_normal(k)
+        signal = X[idx, :n].astype(np.float64).T @ betas[r, idx]
+        var_sig = float(np.var(signal))
+        sigma = np.sqrt(var_sig / snr) if var_sig > 0 else 1.0
+        Y[r] = signal + sigma * g.standard_normal(n)
+    perm = g.permutation(n)
+    fold_id = np.empty(n, dtype=np.int8)
+    fold_id[perm] = (np.arange(n) % nfolds).astype(np.int8)
+    return BatchedProblem(name or f"batched_ar1_{n}x{p}_{m}resp_{nfolds}fold", X, Y, fold_id, n, p, ldx, m,
+                          nfolds, dtype, betas, alpha, ratio, nlambda, eps,
+                          {"rho": rho, "k": k, "snr": snr})
+
+
+def batched_residuals(bp: BatchedProblem, replicate: int = 0):
+    """Residual-shaped test vectors for the batched z pass: right-hand side
+    b = r * (nfolds + 1) + f is N(0,1) on fit f's rows and 0 elsewhere.
+    Returns (R float32[nrhs, ldr], fit_of int32[nrhs])."""
+    g = rng_for(40 + bp.nfolds, replicate)
+    F = bp.nfolds + 1
+    ldr = padded_ld(bp.n, "f32")
+    R = np.zeros((bp.m * F, ldr), np.float32)
+    fit_of = np.empty(bp.m * F, np.int32)
+    for r in range(bp.m):
+        for f in range(F):
+            b = r * F + f
+            rows = bp.fit_rows(f)
+            R[b, rows] = g.standard_normal(len(rows))
+            fit_of[b] = f
+    return R, fit_of
 
 
 def workload(index: int, replicate: int = 0, scale: Optional[float] = None,

@@ -45,4 +45,4 @@ def test_struct_layouts_match_the_header():
     assert C.sizeof(bl.bl_options) == 40
     # bl_path: 15 pointer/int64 fields + lambda_max, jstar, ybar
     assert C.sizeof(bl.bl_path) == 18 * 8
-    assert C.sizeof(bl.bl_timing) == 10 * 8 * 3 + 16
+    assert C.sizeof(bl.bl_timing) == 12 * 8 * 3 + 16
