@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--small", action="store_true", help="a small workload for profiling runs")
     ap.add_argument("--cd-mode", default="blocked", choices=["blocked", "covariance", "residual"],
                     help="coordinate-descent form of the timed (chosen) path")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched z pass (cross-validation workload) object")
     ap.add_argument("--plain-steps", type=int, default=2,
                     help="steps of the plain form (residual-update CD) timed for comparison; 0 = skip")
     return ap.parse_args()
@@ -194,6 +196,82 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def batched_zpass(local: int, reps: int = 20, plain_rhs: int = 8):
+    """The batched z pass (Sec. 3.1.2, formula (3)) on the cross-validation
+    workload: 2000 x 200,000 FP32 AR(1), 16 responses x (10 folds + all rows) =
+    176 residuals, timed with CUDA events on the ctx stream (1.6 GB of X per
+    pass, larger than L2), beside the plain FP32 single-residual z pass."""
+    import torch
+    from paper_1701_05936_gb300 import bl, synth
+    dev = torch.device("cuda", local)
+    bp = synth.batched_ar1(replicate=0)
+    F = bp.nfolds + 1
+    R, fit_of = synth.batched_residuals(bp, 0)
+    ctx = bl.Context(local)
+    X = torch.from_numpy(bp.X).to(dev)
+    cen = torch.zeros((F, bp.p), dtype=torch.float64, device=dev)
+    sca = torch.zeros((F, bp.p), dtype=torch.float64, device=dev)
+    nfit = []
+    for f in range(F):   # each fit's c and s from bl_standardize on its rows (setup, untimed)
+        rows = torch.from_numpy(bp.fit_rows(f)).to(dev)
+        nf = int(rows.numel())
+        ldf = synth.padded_ld(nf, "f32")
+        Xf = torch.zeros((bp.p, ldf), dtype=torch.float32, device=dev)
+        Xf[:, :nf] = X.index_select(1, rows)
+        xn = torch.zeros(bp.p, dtype=torch.float64, device=dev)
+        keep = torch.zeros(bp.p, dtype=torch.uint8, device=dev)
+        bl.bl_standardize(ctx, Xf, nf, cen[f], sca[f], xn, keep)
+        del Xf
+        nfit.append(nf)
+    Rd = torch.from_numpy(R).to(dev)
+    fo = torch.from_numpy(fit_of).to(dev)
+    nrhs = R.shape[0]
+    Z = torch.empty((nrhs, bp.p), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        bl.bl_xtr_batched(ctx, X, bp.n, Rd, cen, sca, nfit, fo, Z)
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    for _ in range(reps):
+        bl.bl_xtr_batched(ctx, X, bp.n, Rd, cen, sca, nfit, fo, Z)
+    torch.cuda.synchronize()
+    t = ctx.timing()["xtr"]
+    ms = t["ms"] / max(1, t["launches"])
+    # the plain form: the FP32 z pass of a single residual (k_zpass), on the
+    # fits' own statistics, for a few residuals
+    xn = torch.zeros(bp.p, dtype=torch.float64, device=dev)
+    keep = torch.ones(bp.p, dtype=torch.uint8, device=dev)
+    scan = torch.ones(bp.p, dtype=torch.uint8, device=dev)
+    working = torch.zeros(bp.p, dtype=torch.uint8, device=dev)
+    zp = torch.empty(bp.p, dtype=torch.float32, device=dev)
+    xnorm = torch.sqrt((X[:, :bp.n].double() ** 2).sum(dim=1))
+    ctx.set_timing(True)
+    for b in range(plain_rhs):
+        f = int(fit_of[b])
+        bl.bl_kkt_check(ctx, X, bp.n, cen[f], sca[f], xnorm, keep, Rd[b], 1.0, 1.0, scan, scan, working, zp)
+    torch.cuda.synchronize()
+    tp = ctx.timing()["zpass"]
+    plain_ms = tp["ms"] / max(1, tp["launches"])
+    ctx.close()
+    peaks, which = measured_peaks()
+    tf32_peak = peaks["bf16_tflops"] * (1.1 / 2.25)
+    bytes_alg = 4.0 * (bp.n * bp.p + bp.n * nrhs + nrhs * bp.p + 2 * F * bp.p)
+    flops = 2.0 * bp.n * bp.p * nrhs
+    gbs = bytes_alg / 1e9 / (ms / 1e3)
+    tfs = flops / 1e12 / (ms / 1e3)
+    return {
+        "workload": f"ar1_{bp.n}x{bp.p}_f32_rho0.3, {bp.m} responses x ({bp.nfolds} folds + all rows) = {nrhs} residuals",
+        "kernel": "k_xtr_tf32 (tcgen05 TF32, TMEM accumulators, TMA tiles, formula-(3) epilogue)",
+        "ms_per_pass": ms, "passes": reps,
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": gbs / peaks["hbm_gbs"], "peak_source": f"{which} hbm_gbs",
+                     "algorithmic_bytes_per_pass": bytes_alg, "traffic": None},
+        "tensor": {"achieved": tfs, "peak": tf32_peak, "unit": "TFLOP/s", "frac": tfs / tf32_peak,
+                   "peak_source": f"{which} bf16_tflops x 1.1/2.25 (nominal TF32/BF16)"},
+        "plain_form": {"form": "FP32 single-residual z pass (k_zpass) per residual", "ms_per_residual": plain_ms,
+                       "ms_for_all": plain_ms * nrhs, "chosen_over_plain": plain_ms * nrhs / ms},
+    }
 
 
 def config(prob):
@@ -345,6 +423,8 @@ def run_ours(args):
         "plain_form": plain,
         "kernel_ms_per_step": breakdown, "status": res["status"],
     }
+    if rank == 0 and not args.no_batched:
+        line["batched_zpass"] = batched_zpass(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob)
     ctx.close()

@@ -8,18 +8,19 @@
 // rows) with its own centre c_f, scale s_f and row count n_f, and r_b is zero on
 // the rows outside fit f.  One read of X serves every right-hand side.
 //
-// Kernel structure (one CTA per SM, persistent over 256-feature tiles):
-//   warp 0, one lane : TMA producer.  Per stage: two 128 x 32 tiles of X
+// Kernel structure (one CTA per SM, persistent over 128-feature tiles):
+//   warp 0, one lane : TMA producer.  Per stage: the 128 x 32 tile of X
 //                      (features x observations, 128-byte rows, 128-byte
 //                      swizzle) and the np x 32 tile of R' (np = nrhs rounded
 //                      up to 16; rows past nrhs and observations past n are
 //                      zero-filled by the copy engine).
-//   warp 1           : owns the TMEM accumulators (2 x np FP32 columns); one
-//                      lane issues tcgen05.mma kind::tf32 (M=128, N=np, K=8,
-//                      four per stage and sub-tile) and commits each stage
-//                      back to the producer.
+//   warp 1           : owns two TMEM accumulators of np FP32 columns; one lane
+//                      issues tcgen05.mma kind::tf32 (M=128, N=np, K=8, four
+//                      per stage) into the accumulator of the tile's parity and
+//                      commits each stage back to the producer.
 //   warps 2..5       : epilogue.  Warp w reads TMEM lanes 32*(w%4).. (one
-//                      feature per thread), applies the formula above and
+//                      feature per thread) of the other accumulator while the
+//                      next tile accumulates, applies the formula above and
 //                      writes Z problem-major (coalesced across features).
 // TF32 takes the upper 19 bits of each FP32 operand; accumulation is FP32.
 // Every wait is bounded by the GPU wall clock; on expiry the kernel raises
@@ -39,7 +40,7 @@ namespace bl {
 namespace {
 
 constexpr int XT_BM = 128;                 // features per MMA (TMEM lanes)
-constexpr int XT_SUB = 2;                  // MMAs per tile: 256 features
+constexpr int XT_ACC = 2;                  // TMEM accumulators (tiles in flight)
 constexpr int XT_BK = 32;                  // observations per stage (128 bytes of FP32)
 constexpr int XT_MAXS = 6;                 // pipeline stages at most
 constexpr int XT_THREADS = 192;
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
     k_xtr_tf32(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapR, XtrArgs a)
 {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t full[XT_MAXS], empty[XT_MAXS], tfull, tempty, drain;
+    __shared__ __align__(8) uint64_t full[XT_MAXS], empty[XT_MAXS], tfull[XT_ACC], tempty[XT_ACC], drain;
     __shared__ uint32_t tmem_slot;
     __shared__ int fit_s[256];
     __shared__ float sumr_s[256];
@@ -113,8 +114,10 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
             mbar_init(smem_u32(&full[s]), 1);
             mbar_init(smem_u32(&empty[s]), 1);
         }
-        mbar_init(smem_u32(&tfull), 1);
-        mbar_init(smem_u32(&tempty), 4);  // one arrival per epilogue warp
+        for (int t = 0; t < XT_ACC; ++t) {
+            mbar_init(smem_u32(&tfull[t]), 1);
+            mbar_init(smem_u32(&tempty[t]), 4);  // one arrival per epilogue warp
+        }
         mbar_init(smem_u32(&drain), 1);
         err_s = 0;
         fence_mbar_init();
@@ -133,7 +136,7 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    const uint32_t b_off = XT_SUB * XT_A_BYTES;  // R' tile after the two X tiles of a stage
+    const uint32_t b_off = XT_A_BYTES;  // R' tile after the X tile of a stage
     const uint32_t tx_bytes = a.stage_bytes;
 
     if (warp == 0) {
@@ -151,8 +154,7 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
                     }
                     const uint32_t st = base + (uint32_t)s * a.stage_bytes;
                     mbar_expect_tx(smem_u32(&full[s]), tx_bytes);
-                    tma_load_2d(st, &mapX, kc * XT_BK, tile * XT_BM * XT_SUB, smem_u32(&full[s]));
-                    tma_load_2d(st + XT_A_BYTES, &mapX, kc * XT_BK, tile * XT_BM * XT_SUB + XT_BM, smem_u32(&full[s]));
+                    tma_load_2d(st, &mapX, kc * XT_BK, tile * XT_BM, smem_u32(&full[s]));
                     tma_load_2d(st + b_off, &mapR, kc * XT_BK, 0, smem_u32(&full[s]));
                     last_round[s] = r;
                 }
@@ -167,8 +169,9 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
             int it = 0, tl = 0;
             bool ok = true;
             for (int tile = blockIdx.x; ok && tile < a.ntiles; tile += gridDim.x, ++tl) {
-                // the epilogue has drained the accumulators of the previous tile
-                if (tl > 0 && !mbar_wait_bounded(smem_u32(&tempty), (tl - 1) & 1, XT_WAIT_NS)) {
+                // the epilogue has drained this accumulator (used two tiles ago)
+                const int acc = tl % XT_ACC, use = tl / XT_ACC;
+                if (use > 0 && !mbar_wait_bounded(smem_u32(&tempty[acc]), (use - 1) & 1, XT_WAIT_NS)) {
                     ok = false;
                     break;
                 }
@@ -181,18 +184,14 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
                     }
                     tc_fence_after();
                     const uint32_t st = base + (uint32_t)s * a.stage_bytes;
-                    const uint64_t bd = desc_k128(st + b_off);
+                    const uint64_t bd = desc_k128(st + b_off), ad = desc_k128(st);
 #pragma unroll
-                    for (int sub = 0; sub < XT_SUB; ++sub) {
-                        const uint64_t ad = desc_k128(st + (uint32_t)sub * XT_A_BYTES);
-#pragma unroll
-                        for (int kk = 0; kk < XT_BK / 8; ++kk)  // K = 8 TF32 = 32 bytes per MMA
-                            mma_tf32(tmem + (uint32_t)(sub * a.np), ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2),
-                                     a.idesc, (kc | kk) != 0);
-                    }
+                    for (int kk = 0; kk < XT_BK / 8; ++kk)  // K = 8 TF32 = 32 bytes per MMA
+                        mma_tf32(tmem + (uint32_t)(acc * a.np), ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2),
+                                 a.idesc, (kc | kk) != 0);
                     mma_commit(smem_u32(&empty[s]));
                 }
-                if (ok) mma_commit(smem_u32(&tfull));
+                if (ok) mma_commit(smem_u32(&tfull[acc]));
             }
             if (!ok) atomicOr(&err_s, 2);
             // all MMAs this thread issued are complete before TMEM is freed
@@ -203,19 +202,19 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
         const int q = warp & 3;
         int tl = 0;
         for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++tl) {
-            if (!mbar_wait_bounded(smem_u32(&tfull), tl & 1, XT_WAIT_NS)) {
+            const int acc = tl % XT_ACC, use = tl / XT_ACC;
+            if (!mbar_wait_bounded(smem_u32(&tfull[acc]), use & 1, XT_WAIT_NS)) {
                 if (lane == 0) atomicOr(&err_s, 4);
                 break;
             }
             tc_fence_after();
-#pragma unroll 1
-            for (int sub = 0; sub < XT_SUB; ++sub) {
-                const int64_t j = (int64_t)tile * (XT_BM * XT_SUB) + sub * XT_BM + 32 * q + lane;
+            {
+                const int64_t j = (int64_t)tile * XT_BM + 32 * q + lane;
                 const bool live = j < a.p;
 #pragma unroll 1
                 for (int c0 = 0; c0 < a.np; c0 += 16) {
                     uint32_t v[16];
-                    const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(sub * a.np + c0);
+                    const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * a.np + c0);
                     asm volatile(
                         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
                         "[%16];"
@@ -240,7 +239,7 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&tempty));
+            if (lane == 0) mbar_arrive(smem_u32(&tempty[acc]));
         }
     }
     tc_fence_before();
@@ -317,7 +316,7 @@ bool tensor_map_f32(CUtensorMap *m, const void *ptr, uint64_t inner, uint64_t ou
 int xtr_stages(int nrhs, size_t *smem)
 {
     const int np = (nrhs + 15) / 16 * 16;
-    const size_t stage = (size_t)XT_SUB * XT_A_BYTES + (size_t)np * XT_BK * 4;
+    const size_t stage = (size_t)XT_A_BYTES + (size_t)np * XT_BK * 4;
     int s = (int)((227 * 1024 - 2048) / stage);
     if (s > XT_MAXS) s = XT_MAXS;
     if (smem) *smem = 1024 + (size_t)s * stage;
@@ -347,14 +346,14 @@ cudaError_t launch_xtr(const float *X, int64_t n, int64_t p, int64_t ldx, const 
     a.nrhs = nrhs;
     a.np = np;
     a.stages = S;
-    a.ntiles = (int)((p + XT_BM * XT_SUB - 1) / (XT_BM * XT_SUB));
+    a.ntiles = (int)((p + XT_BM - 1) / XT_BM);
     a.kchunks = (int)((n + XT_BK - 1) / XT_BK);
     // instruction descriptor: FP32 accumulate, TF32 A and B, both K-major, N = np, M = 128
     a.idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(np >> 3) << 17) | ((uint32_t)(XT_BM >> 4) << 24);
     uint32_t cols = 32;
-    while (cols < (uint32_t)(XT_SUB * np)) cols <<= 1;
+    while (cols < (uint32_t)(XT_ACC * np)) cols <<= 1;
     a.tmem_cols = cols;
-    a.stage_bytes = (uint32_t)(XT_SUB * XT_A_BYTES + (uint32_t)np * XT_BK * 4);
+    a.stage_bytes = (uint32_t)(XT_A_BYTES + (uint32_t)np * XT_BK * 4);
     a.fit_of = fit_of;
     a.cfit = cfit;
     a.insfit = insfit;
