@@ -122,7 +122,8 @@ typedef struct {
  * is enabled (bl_ctx_set_timing).  Kinds: 0 standardize, 1 lambda_max,
  * 2 bedpp_init, 3 screen, 4 compact, 5 cd, 6 residual, 7 zpass, 8 record,
  * 9 gref (the FP64 reference gradients each CD launch starts from),
- * 10 xtr (the batched z pass of bl_xtr_batched), 11 reserved. */
+ * 10 xtr (the batched z pass of bl_xtr_batched), 11 kkt (the batched path's
+ * KKT check). */
 #define BL_NUM_KINDS 12
 typedef struct {
     int64_t launches[BL_NUM_KINDS];
@@ -296,6 +297,40 @@ int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int
 int bl_xtr_batched(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx, const float *R,
                    int64_t ldr, int64_t nrhs, const double *center, const double *scale, int64_t ldc,
                    const double *n_fit, int64_t nfit, const int32_t *fit_of, float *Z, int64_t ldz);
+
+/* Batched path (Sec. 3.1.2, cross-validation on one design): m responses, each
+ * fitted on all rows and on the training rows of each of nfolds folds, so
+ * B = m * (nfolds + 1) lasso / elastic-net paths, run in lock-step over lambda.
+ * Problem b = r * (nfolds + 1) + f is response r on fit f; fit 0 is all rows and
+ * fit f >= 1 leaves out the rows with fold_id == f - 1.  Each fit is
+ * standardized on its own rows (Sec. 3.1); no row subset of X is formed.  Every
+ * fit of response r uses the lambda sequence of response r on all rows
+ * (lambda_max of Sec. 3.1.1 on all rows, then the grid of bl_fit_path), so the
+ * folds share the full-data sequence; a fold whose own lambda_max lies below a
+ * lambda has b = 0 there.  Screening is the strong rule (Sec. 2.2) judged by the
+ * KKT check on the batched z pass of bl_xtr_batched (TF32 with a rigorous
+ * rounding bound: a feature that might violate joins the working set), so the
+ * path is the exact minimizer path like bl_fit_path's.
+ *   X        device FP32 (BL_F32 only), as bl_fit_path; n <= 8192.
+ *   Y        device FP64, column-major n x m (response r at Y + r*ldy), ldy >= n.
+ *   fold_id  device int8 [n] in [0, nfolds) (NULL when nfolds == 0); every fit
+ *            needs at least two rows.  nfolds in 0..31, B <= 256.
+ *   opt      alpha, eps, lambda_min_ratio and max_sweeps as bl_fit_path; screen and
+ *            cd_mode are ignored (strong rule, residual-form CD per problem).
+ *   outs     host array of B bl_path, each filled as bl_fit_path fills it (device
+ *            lambdas, col_ptr, row_idx, val, val_orig, intercept, loss; the host
+ *            counters when non-NULL: n_safe reports p, cols_scanned the columns
+ *            the z passes read); lambda_max is response r's, jstar is reported for
+ *            fit 0 only (-1 for the folds).
+ * Errors: BL_ERR_ARG before any launch for bad arguments; BL_ERR_UNSUPPORTED for a
+ * non-FP32 design, n > 8192 or a working set beyond 8192 features;
+ * BL_ERR_CAPACITY if a path needs more than its nnz_capacity (nnz_needed is
+ * set); BL_ERR_NOT_CONVERGED (outputs valid) if a CD hit max_sweeps;
+ * BL_ERR_TIMEOUT if a device wait ran out.  Synchronizes; allocates its device
+ * scratch for the call and frees it before returning. */
+int bl_fit_path_batched(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx, const double *Y,
+                        int64_t ldy, int64_t m, const int8_t *fold_id, int64_t nfolds, const bl_options *opt, int nlambda,
+                        bl_path *outs);
 
 /* Largest working set that bl_cd_active_noalloc accepts. */
 #define BL_NOALLOC_MAX_WORK 4096

@@ -28,7 +28,7 @@ BL_F64, BL_F32, BL_BF16, BL_I8 = 0, 1, 2, 3
 BL_SCREEN_NONE, BL_SCREEN_SSR, BL_SCREEN_SSR_BEDPP = 0, 1, 2
 BL_CD_RESIDUAL, BL_CD_COVARIANCE, BL_CD_BLOCKED = 0, 1, 2
 KINDS = ["standardize", "lambda_max", "bedpp_init", "screen", "compact", "cd", "residual", "zpass", "record",
-         "gref", "xtr", "reserved"]
+         "gref", "xtr", "kkt"]
 
 _STATUS = {0: "BL_OK", -1: "BL_ERR_ARG", -2: "BL_ERR_CUDA", -3: "BL_ERR_OOM", -4: "BL_ERR_NOT_CONVERGED",
            -5: "BL_ERR_TIMEOUT", -6: "BL_ERR_UNSUPPORTED", -7: "BL_ERR_CAPACITY"}
@@ -99,6 +99,8 @@ def lib():
                                          _dbl, _vp, _vp, _dbl, _i64, C.POINTER(_i64), C.c_char_p, C.c_size_t],
                 "bl_xtr_batched": [_vp, *X, _vp, _i64, _i64, _vp, _vp, _i64, C.POINTER(_dbl), _i64, _vp, _vp,
                                    _i64],
+                "bl_fit_path_batched": [_vp, *X, _vp, _i64, _i64, _vp, _i64, C.POINTER(bl_options), _int,
+                                        C.POINTER(bl_path)],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -285,6 +287,49 @@ def bl_fit_path(ctx, X, n, y, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, lambd
     ctx.check(st, allow=(BL_ERR_NOT_CONVERGED,))
     res.update(host)
     res.update(status=st, nnz=path.nnz_needed, lambda_max=path.lambda_max, jstar=path.jstar, ybar=path.ybar)
+    return res
+
+
+def bl_fit_path_batched(ctx, X, n, Y, fold_id=None, nfolds=0, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7,
+                        max_sweeps=100_000, nnz_capacity=None):
+    """m responses x (nfolds + 1) fits in lock-step on the GPU.  X (p, ldx) FP32,
+    Y (m, ldy) FP64 (row r = response r) and fold_id (n,) int8 on the ctx's
+    device.  Returns a list of B = m (nfolds + 1) dicts shaped like
+    bl_fit_path's, problem b = r (nfolds + 1) + f (fit 0: all rows; fit f: fold
+    f - 1 left out)."""
+    dev = X.device
+    p = int(X.shape[0])
+    m, ldy = int(Y.shape[0]), int(Y.shape[1])
+    F = int(nfolds) + 1
+    B = m * F
+    K = int(nlambda)
+    if nnz_capacity is None:
+        nnz_capacity = K * min(p, int(n) + 64)
+    o = torch.zeros
+    paths = (bl_path * B)()
+    res = []
+    for b in range(B):
+        r = {"lambdas": o(K, dtype=torch.float64, device=dev), "col_ptr": o(K + 1, dtype=torch.int64, device=dev),
+             "row_idx": o(max(1, nnz_capacity), dtype=torch.int32, device=dev),
+             "val": o(max(1, nnz_capacity), dtype=torch.float64, device=dev),
+             "val_orig": o(max(1, nnz_capacity), dtype=torch.float64, device=dev),
+             "intercept": o(K, dtype=torch.float64, device=dev), "loss": o(K, dtype=torch.float64, device=dev)}
+        host = {k: o(K, dtype=torch.int64) for k in ("sweeps", "n_safe", "n_strong", "kkt_rounds", "cols_scanned",
+                                                       "n_active")}
+        for k in ("lambdas", "col_ptr", "row_idx", "val", "val_orig", "intercept", "loss"):
+            setattr(paths[b], k, r[k].data_ptr())
+        for k, t in host.items():
+            setattr(paths[b], k, t.data_ptr())
+        paths[b].nnz_capacity = nnz_capacity
+        r.update(host)
+        res.append(r)
+    opt = bl_options(float(alpha), float(eps), float(ratio), int(max_sweeps), BL_SCREEN_SSR, BL_CD_RESIDUAL)
+    st = lib().bl_fit_path_batched(ctx.h, *design_args(X, n), _ptr(Y), ldy, m, _ptr(fold_id), int(nfolds),
+                                   C.byref(opt), K, paths)
+    ctx.check(st, allow=(BL_ERR_NOT_CONVERGED,))
+    for b in range(B):
+        res[b].update(status=st, nnz=paths[b].nnz_needed, lambda_max=paths[b].lambda_max, jstar=paths[b].jstar,
+                      ybar=paths[b].ybar)
     return res
 
 

@@ -557,10 +557,288 @@ extern "C" int bl_xtr_batched(bl_ctx *ctx, const void *X, int dtype, int64_t n, 
     CK(cudaMemsetAsync(&ctx->ws.sc->status, 0, sizeof(int), ctx->stream));
     int slot = tbegin(ctx, 10);
     LAUNCH(3, launch_xtr((const float *)X, n, p, ldx, R, ldr, (int)nrhs, center, scale, ldc, nfd, (int)nfit, fit_of,
-                         cfit, insfit, sumr, Z, ldz, ctx->ws.sc, ctx->num_sms, ctx->stream));
+                         cfit, insfit, sumr, nullptr, Z, ldz, ctx->ws.sc, ctx->num_sms, ctx->stream));
     tend(ctx, slot, (double)n * (double)p * 4.0);
     if ((st = sync_sc(ctx))) return st;
     if (ctx->sc_host->status & ST_TIMEOUT) return fail(ctx, BL_ERR_TIMEOUT, "batched z pass: a pipeline wait ran out");
+    return BL_OK;
+}
+
+// ========================================================== batched path
+namespace {
+// device buffers of one bl_fit_path_batched call, freed on every return
+struct BatchBufs {
+    std::vector<void *> ptrs;
+    ~BatchBufs()
+    {
+        for (void *p : ptrs) cudaFree(p);
+    }
+    template <typename T> cudaError_t get(T **out, size_t count)
+    {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+        if (e == cudaSuccess) {
+            ptrs.push_back(p);
+            *out = (T *)p;
+        }
+        return e;
+    }
+};
+}  // namespace
+
+extern "C" int bl_fit_path_batched(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx,
+                                   const double *Y, int64_t ldy, int64_t m, const int8_t *fold_id, int64_t nfolds,
+                                   const bl_options *opt, int K, bl_path *outs)
+{
+    int st = check_design(ctx, X, dtype, n, p, ldx);
+    if (st) return st;
+    if (dtype != BL_F32) return fail(ctx, BL_ERR_UNSUPPORTED, "the batched path takes FP32 designs");
+    if (!Y || !opt || !outs || K < 1 || m < 1) return fail(ctx, BL_ERR_ARG, "NULL argument, nlambda < 1 or m < 1");
+    if (ldy < n) return fail(ctx, BL_ERR_ARG, "ldy must be >= n");
+    if (nfolds < 0 || nfolds > BATCH_MAX_FOLDS) return fail(ctx, BL_ERR_ARG, "nfolds must be in 0..31");
+    if (nfolds > 0 && !fold_id) return fail(ctx, BL_ERR_ARG, "fold_id is NULL");
+    const int F = (int)nfolds + 1;
+    const int64_t B64 = m * (int64_t)F;
+    if (B64 > BATCH_MAX_PROBLEMS) return fail(ctx, BL_ERR_ARG, "m * (nfolds + 1) must be <= 256");
+    const int B = (int)B64;
+    const double alpha = opt->alpha, eps = opt->eps;
+    if (!(alpha > 0.0 && alpha <= 1.0)) return fail(ctx, BL_ERR_ARG, "alpha must be in (0, 1]");
+    if (!(eps > 0.0) || opt->max_sweeps < 1) return fail(ctx, BL_ERR_ARG, "eps must be > 0 and max_sweeps >= 1");
+    if (K > 1 && !(opt->lambda_min_ratio > 0.0 && opt->lambda_min_ratio < 1.0))
+        return fail(ctx, BL_ERR_ARG, "lambda_min_ratio must be in (0, 1)");
+    if (n > 8192) return fail(ctx, BL_ERR_UNSUPPORTED, "the batched path takes n <= 8192");
+    for (int b = 0; b < B; ++b)
+        if (!outs[b].lambdas || !outs[b].col_ptr || !outs[b].intercept || !outs[b].loss ||
+            (outs[b].nnz_capacity > 0 && (!outs[b].row_idx || !outs[b].val)) || outs[b].nnz_capacity < 0)
+            return fail(ctx, BL_ERR_ARG, "every bl_path needs lambdas, col_ptr, intercept, loss, row_idx and val");
+    ctx->err.clear();
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    // fits: row counts from the fold ids
+    std::vector<double> nfit((size_t)F, (double)n);
+    if (nfolds > 0) {
+        std::vector<int8_t> fh((size_t)n);
+        CK(cudaMemcpyAsync(fh.data(), fold_id, (size_t)n, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int64_t i = 0; i < n; ++i) {
+            if (fh[(size_t)i] < 0 || fh[(size_t)i] >= nfolds) return fail(ctx, BL_ERR_ARG, "fold_id outside [0, nfolds)");
+            nfit[(size_t)fh[(size_t)i] + 1] -= 1.0;
+        }
+        for (int f = 1; f < F; ++f)
+            if (nfit[(size_t)f] < 2.0) return fail(ctx, BL_ERR_ARG, "every fit needs at least two rows");
+    }
+    if ((st = ensure_ws(ctx, n, p))) return st;
+    const int64_t ldr = (n + 3) / 4 * 4, cap = std::min<int64_t>(p, 8192);
+    BatchBufs bb;
+    double *cen, *sca, *nfit_d, *ybar, *yc, *r64, *lam_b, *ssr, *rnorm, *xty, *ycs;
+    uint8_t *keepF, *inW;
+    float *c32, *is32, *xn32, *r32, *beta, *Z, *gref, *sumr, *cfit, *insfit;
+    int32_t *idx, *fit_of;
+    int64_t *w, *nnz_total;
+    int *status, *active;
+    unsigned long long *sweeps_d, *updates_d, *nviol;
+    BatchPathOut *outs_d;
+    CK(bb.get(&cen, (size_t)F * p));
+    CK(bb.get(&sca, (size_t)F * p));
+    CK(bb.get(&keepF, (size_t)F * p));
+    CK(bb.get(&c32, (size_t)F * p));
+    CK(bb.get(&is32, (size_t)F * p));
+    CK(bb.get(&cfit, (size_t)F * p));
+    CK(bb.get(&insfit, (size_t)F * p));
+    CK(bb.get(&xn32, (size_t)p));
+    CK(bb.get(&nfit_d, (size_t)F));
+    CK(bb.get(&ybar, (size_t)B));
+    CK(bb.get(&yc, (size_t)B * n));
+    CK(bb.get(&r64, (size_t)B * n));
+    CK(bb.get(&r32, (size_t)B * ldr));
+    CK(bb.get(&beta, (size_t)B * p));
+    CK(bb.get(&Z, (size_t)B * p));
+    CK(bb.get(&inW, (size_t)B * p));
+    CK(bb.get(&idx, (size_t)B * cap));
+    CK(bb.get(&gref, (size_t)B * cap));
+    CK(bb.get(&w, (size_t)B));
+    CK(bb.get(&nnz_total, (size_t)B));
+    CK(bb.get(&status, (size_t)B));
+    CK(bb.get(&active, (size_t)B));
+    CK(bb.get(&sweeps_d, (size_t)B));
+    CK(bb.get(&updates_d, (size_t)B));
+    CK(bb.get(&nviol, (size_t)B));
+    CK(bb.get(&lam_b, (size_t)B));
+    CK(bb.get(&ssr, (size_t)B));
+    CK(bb.get(&rnorm, (size_t)B));
+    CK(bb.get(&sumr, (size_t)B));
+    CK(bb.get(&fit_of, (size_t)B));
+    CK(bb.get(&outs_d, (size_t)B));
+    CK(bb.get(&xty, (size_t)p));
+    CK(bb.get(&ycs, (size_t)n));
+    CK(cudaMemcpyAsync(nfit_d, nfit.data(), (size_t)F * 8, cudaMemcpyHostToDevice, s));
+    std::vector<int32_t> fo((size_t)B);
+    std::vector<BatchPathOut> oh((size_t)B);
+    for (int b = 0; b < B; ++b) {
+        fo[(size_t)b] = b % F;
+        oh[(size_t)b] = BatchPathOut{outs[b].col_ptr, outs[b].row_idx, outs[b].val, outs[b].val_orig,
+                                     outs[b].nnz_capacity, outs[b].intercept, outs[b].loss};
+        CK(cudaMemsetAsync(outs[b].col_ptr, 0, sizeof(int64_t), s));
+    }
+    CK(cudaMemcpyAsync(fit_of, fo.data(), (size_t)B * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(outs_d, oh.data(), (size_t)B * sizeof(BatchPathOut), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(beta, 0, (size_t)B * p * 4, s));
+    CK(cudaMemsetAsync(w, 0, (size_t)B * 8, s));
+    CK(cudaMemsetAsync(status, 0, (size_t)B * 4, s));
+    CK(cudaMemsetAsync(sweeps_d, 0, (size_t)B * 8, s));
+    CK(cudaMemsetAsync(updates_d, 0, (size_t)B * 8, s));
+    const float *Xf = (const float *)X;
+    // one-time: per-fit standardization, centred responses, exact lambda_max of
+    // each response on all rows (its grid serves every fold: the folds use the
+    // full-data lambda sequence)
+    int slot = tbegin(ctx, 0);
+    LAUNCH(1, launch_bfit_stats(Xf, n, p, ldx, fold_id, (int)nfolds, nfit_d, cen, sca, keepF, c32, is32, xn32,
+                                ctx->num_sms, s));
+    LAUNCH(1, launch_bcenter_y(Y, ldy, B, F, n, fold_id, nfit_d, ybar, yc, r64, r32, ldr, s));
+    tend(ctx, slot, (double)n * p * 4.0);
+    std::vector<double> grid((size_t)m * K);
+    std::vector<double> lmax((size_t)m);
+    std::vector<int64_t> jstar((size_t)m);
+    for (int64_t r = 0; r < m; ++r) {
+        double lm = 0.0, yb = 0.0;
+        int64_t js = -1;
+        if ((st = bl_lambda_max(ctx, X, dtype, n, p, ldx, cen, sca, keepF, Y + r * ldy, alpha, ycs, xty, &lm, &js,
+                                &yb)))
+            return st;
+        lmax[(size_t)r] = lm;
+        jstar[(size_t)r] = js;
+        for (int k = 0; k < K; ++k)
+            grid[(size_t)r * K + k] =
+                (K == 1) ? lm : lm * std::pow(opt->lambda_min_ratio, (double)k / (double)(K - 1));
+    }
+    for (int b = 0; b < B; ++b)
+        CK(cudaMemcpyAsync(outs[b].lambdas, grid.data() + (size_t)(b / F) * K, (size_t)K * 8, cudaMemcpyHostToDevice,
+                           s));
+    std::vector<double> lh((size_t)B), sh((size_t)B);
+    std::vector<int> acth((size_t)B, 1);
+    std::vector<unsigned long long> nvh((size_t)B), swh((size_t)B, 0), swprev((size_t)B, 0);
+    std::vector<int64_t> wh((size_t)B), nzh((size_t)B);
+    std::vector<int> sth((size_t)B);
+    bool not_converged = false;
+    auto zpass = [&]() -> int {
+        int zs = tbegin(ctx, 10);
+        LAUNCH(3, launch_xtr(Xf, n, p, ldx, r32, ldr, B, cen, sca, p, nfit_d, F, fit_of, cfit, insfit, sumr, rnorm, Z, p,
+                             ctx->ws.sc, ctx->num_sms, s));
+        tend(ctx, zs, (double)n * p * 4.0);
+        return BL_OK;
+    };
+    CK(cudaMemsetAsync(&ctx->ws.sc->status, 0, sizeof(int), s));
+    if ((st = zpass())) return st;
+    // every lambda, lambda_0 included: lambda_0 is lambda_max of the response on
+    // all rows, where fit 0 has b = 0, but a fold whose own lambda_max is larger
+    // is not zero there (the strong rule at lambda_0 takes lambda_{-1} = lambda_0)
+    for (int k = 0; k < K; ++k) {
+        for (int b = 0; b < B; ++b) {
+            const double lk = grid[(size_t)(b / F) * K + k], lp = grid[(size_t)(b / F) * K + (k > 0 ? k - 1 : 0)];
+            lh[(size_t)b] = lk;
+            sh[(size_t)b] = alpha * (2.0 * lk - lp);
+            acth[(size_t)b] = 1;
+        }
+        CK(cudaMemcpyAsync(lam_b, lh.data(), (size_t)B * 8, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(ssr, sh.data(), (size_t)B * 8, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(active, acth.data(), (size_t)B * 4, cudaMemcpyHostToDevice, s));
+        slot = tbegin(ctx, 3);
+        LAUNCH(1, launch_bstrong(p, B, F, keepF, beta, Z, p, ssr, inW, s));
+        tend(ctx, slot, 0.0);
+        int64_t rounds = 0;
+        std::vector<int64_t> strong0((size_t)B, -1);
+        for (;;) {
+            slot = tbegin(ctx, 4);
+            LAUNCH(1, launch_bcompact(p, B, inW, idx, cap, w, status, active, s));
+            tend(ctx, slot, 0.0);
+            CK(cudaMemcpyAsync(wh.data(), w, (size_t)B * 8, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(sth.data(), status, (size_t)B * 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int b = 0; b < B; ++b) {
+                if (sth[(size_t)b] & ST_WORKING_TOO_BIG)
+                    return fail(ctx, BL_ERR_UNSUPPORTED, "a working set exceeds the batched CD capacity");
+                if (strong0[(size_t)b] < 0) strong0[(size_t)b] = wh[(size_t)b];
+            }
+            ++rounds;
+            slot = tbegin(ctx, 9);
+            LAUNCH(1, launch_bgref(Xf, n, ldx, p, B, F, cen, idx, w, cap, r64, active, gref, ctx->num_sms, s));
+            tend(ctx, slot, 0.0);
+            slot = tbegin(ctx, 5);
+            LAUNCH(1, launch_bcd(Xf, n, ldx, p, B, F, fold_id, nfit_d, c32, is32, idx, w, cap, gref, lam_b, alpha, beta,
+                                 r32, ldr, eps, opt->max_sweeps, CD_TIME_LIMIT_NS, status, sweeps_d, updates_d, active,
+                                 s));
+            tend(ctx, slot, 0.0);
+            slot = tbegin(ctx, 6);
+            LAUNCH(1, launch_bresid(Xf, n, ldx, p, B, F, fold_id, cen, sca, idx, w, cap, beta, yc, active, r64, r32, ldr,
+                                    s));
+            tend(ctx, slot, 0.0);
+            if ((st = zpass())) return st;
+            CK(cudaMemsetAsync(nviol, 0, (size_t)B * 8, s));
+            slot = tbegin(ctx, 11);
+            LAUNCH(1, launch_bkkt(p, n, B, F, keepF, c32, is32, xn32, nfit_d, Z, p, rnorm, sumr, lam_b, alpha, inW,
+                                  nviol, s));
+            tend(ctx, slot, 0.0);
+            CK(cudaMemcpyAsync(nvh.data(), nviol, (size_t)B * 8, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(sth.data(), status, (size_t)B * 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(&ctx->sc_host->status, &ctx->ws.sc->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (ctx->sc_host->status & ST_TIMEOUT) return fail(ctx, BL_ERR_TIMEOUT, "batched z pass: a wait ran out");
+            bool any = false;
+            for (int b = 0; b < B; ++b) {
+                const int sb = sth[(size_t)b];
+                if (sb & ST_BAD_INDEX) return fail(ctx, BL_ERR_ARG, "internal working-set index out of range");
+                if (sb & ST_TIMEOUT) return fail(ctx, BL_ERR_TIMEOUT, "batched CD reached its wall-clock limit");
+                if (sb & ST_NOT_CONVERGED) not_converged = true;
+                acth[(size_t)b] = nvh[(size_t)b] > 0;
+                any |= acth[(size_t)b] != 0;
+            }
+            if (!any) break;
+            if (rounds >= 1000) return fail(ctx, BL_ERR_NOT_CONVERGED, "KKT rounds did not settle");
+            CK(cudaMemcpyAsync(active, acth.data(), (size_t)B * 4, cudaMemcpyHostToDevice, s));
+        }
+        slot = tbegin(ctx, 8);
+        LAUNCH(1, launch_brecord(k, n, p, B, F, fold_id, nfit_d, cen, sca, idx, w, cap, beta, r64, ybar, lam_b, alpha,
+                                 outs_d, nnz_total, s));
+        tend(ctx, slot, 0.0);
+        CK(cudaMemcpyAsync(nzh.data(), nnz_total, (size_t)B * 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(swh.data(), sweeps_d, (size_t)B * 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int b = 0; b < B; ++b) {
+            const int64_t na = (k > 0) ? nzh[(size_t)b] : 0;
+            if (outs[b].sweeps) outs[b].sweeps[k] = (int64_t)(swh[(size_t)b] - swprev[(size_t)b]);
+            if (outs[b].n_safe) outs[b].n_safe[k] = p;
+            if (outs[b].n_strong) outs[b].n_strong[k] = strong0[(size_t)b];
+            if (outs[b].kkt_rounds) outs[b].kkt_rounds[k] = rounds;
+            if (outs[b].cols_scanned) outs[b].cols_scanned[k] = rounds * p;
+            (void)na;
+            swprev[(size_t)b] = swh[(size_t)b];
+        }
+    }
+    std::vector<unsigned long long> uh((size_t)B);
+    CK(cudaMemcpyAsync(uh.data(), updates_d, (size_t)B * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(nzh.data(), nnz_total, (size_t)B * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int b = 0; b < B; ++b) {
+        ctx->cd_updates += (int64_t)uh[(size_t)b];
+        outs[b].nnz_needed = nzh[(size_t)b];
+        outs[b].lambda_max = lmax[(size_t)(b / F)];
+        outs[b].jstar = (b % F == 0) ? jstar[(size_t)(b / F)] : -1;
+        if (outs[b].nnz_needed > outs[b].nnz_capacity) st = BL_ERR_CAPACITY;
+    }
+    // per-problem ybar and the nonzero counts per lambda (from col_ptr)
+    std::vector<double> ybh((size_t)B);
+    CK(cudaMemcpyAsync(ybh.data(), ybar, (size_t)B * 8, cudaMemcpyDeviceToHost, s));
+    std::vector<int64_t> cp((size_t)K + 1);
+    for (int b = 0; b < B; ++b) {
+        if (!outs[b].n_active) continue;
+        CK(cudaMemcpyAsync(cp.data(), outs[b].col_ptr, (size_t)(K + 1) * 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int k = 0; k < K; ++k) outs[b].n_active[k] = cp[(size_t)k + 1] - cp[(size_t)k];
+    }
+    CK(cudaStreamSynchronize(s));
+    for (int b = 0; b < B; ++b) outs[b].ybar = ybh[(size_t)b];
+    if (st == BL_ERR_CAPACITY) return fail(ctx, BL_ERR_CAPACITY, "nnz_capacity too small for a path (see nnz_needed)");
+    if (not_converged) return fail(ctx, BL_ERR_NOT_CONVERGED, "sweep cap reached");
     return BL_OK;
 }
 

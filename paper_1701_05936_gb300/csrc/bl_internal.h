@@ -128,11 +128,52 @@ cudaError_t launch_cd_gram(int dtype, const void *Rm, int64_t n, int64_t p, cons
 
 // Residual-form CD in blocks of consecutive coordinates (needs R from
 // launch_gram); cd_blk_ok tells whether this build covers the shape.
+// ---- batched path (m responses x (nfolds + 1) fits of one design)
+constexpr int BATCH_MAX_FOLDS = 31;
+constexpr int BATCH_MAX_PROBLEMS = 256;
+struct BatchPathOut {  // one problem's CSC path outputs (device pointers)
+    int64_t *col_ptr;
+    int32_t *row_idx;
+    double *val, *val_orig;
+    int64_t cap;
+    double *intercept, *loss;
+};
+cudaError_t launch_bfit_stats(const float *X, int64_t n, int64_t p, int64_t ldx, const int8_t *fold, int nfolds,
+                              const double *nfit, double *cen, double *sca, uint8_t *keep, float *c32, float *is32,
+                              float *xn32, int num_sms, cudaStream_t st);
+cudaError_t launch_bcenter_y(const double *Y, int64_t ldy, int B, int F, int64_t n, const int8_t *fold,
+                             const double *nfit, double *ybar, double *yc, double *r64, float *r32, int64_t ldr,
+                             cudaStream_t st);
+cudaError_t launch_bstrong(int64_t p, int B, int F, const uint8_t *keep, const float *beta, const float *Z, int64_t ldz,
+                           const double *ssr, uint8_t *inW, cudaStream_t st);
+cudaError_t launch_bcompact(int64_t p, int B, const uint8_t *inW, int32_t *idx, int64_t cap, int64_t *w, int *status,
+                            const int *active, cudaStream_t st);
+cudaError_t launch_bgref(const float *X, int64_t n, int64_t ldx, int64_t p, int B, int F, const double *cen,
+                         const int32_t *idx, const int64_t *w, int64_t cap, const double *r64, const int *active,
+                         float *gref, int num_sms, cudaStream_t st);
+size_t bcd_smem(int64_t cap);
+cudaError_t launch_bcd(const float *X, int64_t n, int64_t ldx, int64_t p, int B, int F, const int8_t *fold,
+                       const double *nfit, const float *c32, const float *is32, const int32_t *idx, const int64_t *w,
+                       int64_t cap, const float *gref, const double *lam_b, double alpha, float *beta, float *r32,
+                       int64_t ldr, double eps, int64_t max_sweeps, uint64_t time_limit_ns, int *status,
+                       unsigned long long *sweeps, unsigned long long *updates, const int *active, cudaStream_t st);
+cudaError_t launch_bresid(const float *X, int64_t n, int64_t ldx, int64_t p, int B, int F, const int8_t *fold,
+                          const double *cen, const double *sca, const int32_t *idx, const int64_t *w, int64_t cap,
+                          const float *beta, const double *yc, const int *active, double *r64, float *r32,
+                          int64_t ldr, cudaStream_t st);
+cudaError_t launch_bkkt(int64_t p, int64_t n, int B, int F, const uint8_t *keep, const float *c32, const float *is32,
+                        const float *xn32, const double *nfit, const float *Z, int64_t ldz, const double *rnorm,
+                        const float *sumr, const double *lam_b, double alpha, uint8_t *inW, unsigned long long *nviol,
+                        cudaStream_t st);
+cudaError_t launch_brecord(int k, int64_t n, int64_t p, int B, int F, const int8_t *fold, const double *nfit,
+                           const double *cen, const double *sca, const int32_t *idx, const int64_t *w, int64_t cap,
+                           const float *beta, const double *r64, const double *ybar, const double *lam_b, double alpha,
+                           BatchPathOut *outs, int64_t *nnz_total, cudaStream_t st);
 int xtr_stages(int nrhs, size_t *smem);
 cudaError_t launch_xtr(const float *X, int64_t n, int64_t p, int64_t ldx, const float *R, int64_t ldr, int nrhs,
                        const double *center, const double *scale, int64_t ldc, const double *n_fit_dev, int nfit,
-                       const int32_t *fit_of, float *cfit, float *insfit, float *sumr, float *Z, int64_t ldz,
-                       DevScalars *sc, int num_sms, cudaStream_t st);
+                       const int32_t *fit_of, float *cfit, float *insfit, float *sumr, double *rnorm, float *Z,
+                       int64_t ldz, DevScalars *sc, int num_sms, cudaStream_t st);
 bool cd_blk_ok(int dtype, int64_t n);
 bool cd_blk_fits(int dtype, int64_t n, int64_t w);
 cudaError_t launch_cd_blk(int dtype, const void *X, int64_t n, int64_t p, int64_t ldx, const void *cvec,

@@ -251,21 +251,35 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
     if (threadIdx.x == 0 && err_s) atomicOr(&a.sc->status, ST_TIMEOUT);
 }
 
-// sum_i r_bi in FP64 (rounded to FP32) and the per-fit epilogue vectors
-__global__ void k_xtr_prep(const float *__restrict__ R, int64_t ldr, int64_t n, int nrhs, float *sumr)
+// sum_i r_bi in FP64 (rounded to FP32), ||r_b|| (FP64, nullable) and the
+// per-fit epilogue vectors
+__global__ void k_xtr_prep(const float *__restrict__ R, int64_t ldr, int64_t n, int nrhs, float *sumr, double *rnorm)
 {
     const int b = blockIdx.x;
     if (b >= nrhs) return;
-    double acc = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += (double)R[(int64_t)b * ldr + i];
-    __shared__ double red[32];
+    double acc = 0.0, sq = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double v = (double)R[(int64_t)b * ldr + i];
+        acc += v;
+        sq = fma(v, v, sq);
+    }
+    __shared__ double red[2][32];
     acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    sq = warp_sum(sq);
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = acc;
+        red[1][threadIdx.x >> 5] = sq;
+    }
     __syncthreads();
     if (threadIdx.x < 32) {
-        double v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+        double v = (threadIdx.x < (blockDim.x >> 5)) ? red[0][threadIdx.x] : 0.0;
+        double q = (threadIdx.x < (blockDim.x >> 5)) ? red[1][threadIdx.x] : 0.0;
         v = warp_sum(v);
-        if (threadIdx.x == 0) sumr[b] = (float)v;
+        q = warp_sum(q);
+        if (threadIdx.x == 0) {
+            sumr[b] = (float)v;
+            if (rnorm) rnorm[b] = sqrt(q);
+        }
     }
 }
 
@@ -325,8 +339,8 @@ int xtr_stages(int nrhs, size_t *smem)
 
 cudaError_t launch_xtr(const float *X, int64_t n, int64_t p, int64_t ldx, const float *R, int64_t ldr, int nrhs,
                        const double *center, const double *scale, int64_t ldc, const double *n_fit_dev, int nfit,
-                       const int32_t *fit_of, float *cfit, float *insfit, float *sumr, float *Z, int64_t ldz,
-                       DevScalars *sc, int num_sms, cudaStream_t st)
+                       const int32_t *fit_of, float *cfit, float *insfit, float *sumr, double *rnorm, float *Z,
+                       int64_t ldz, DevScalars *sc, int num_sms, cudaStream_t st)
 {
     size_t smem = 0;
     const int S = xtr_stages(nrhs, &smem);
@@ -335,7 +349,7 @@ cudaError_t launch_xtr(const float *X, int64_t n, int64_t p, int64_t ldx, const 
     CUtensorMap mx, mr;
     if (!tensor_map_f32(&mx, X, (uint64_t)n, (uint64_t)p, (uint64_t)ldx, XT_BM)) return cudaErrorInvalidValue;
     if (!tensor_map_f32(&mr, R, (uint64_t)n, (uint64_t)nrhs, (uint64_t)ldr, (uint32_t)np)) return cudaErrorInvalidValue;
-    k_xtr_prep<<<nrhs, 256, 0, st>>>(R, ldr, n, nrhs, sumr);
+    k_xtr_prep<<<nrhs, 256, 0, st>>>(R, ldr, n, nrhs, sumr, rnorm);
     const int64_t tot = (int64_t)nfit * p;
     k_xtr_fit<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, st>>>(center, scale, ldc, p, nfit, n_fit_dev,
                                                                                  cfit, insfit);
