@@ -198,11 +198,18 @@ def run_reference(args):
     return 0
 
 
-def batched_zpass(local: int, reps: int = 20, plain_rhs: int = 8):
-    """The batched z pass (Sec. 3.1.2, formula (3)) on the cross-validation
-    workload: 2000 x 200,000 FP32 AR(1), 16 responses x (10 folds + all rows) =
-    176 residuals, timed with CUDA events on the ctx stream (1.6 GB of X per
-    pass, larger than L2), beside the plain FP32 single-residual z pass."""
+def batched(local: int, reps: int = 20, plain_rhs: int = 8, path_steps: int = 2):
+    """The batched form (Sec. 3.1.2) on the cross-validation workload: 2000 x
+    200,000 FP32 AR(1), 16 responses x (10 folds + all rows) = 176 problems.
+
+    * batched_zpass: one X'R pass for all 176 residuals (TF32 tensor cores,
+      formula-(3) epilogue), CUDA events on the ctx stream (1.6 GB of X per
+      pass, larger than L2), beside the plain FP32 single-residual z pass.
+    * batched_path: all 176 100-lambda paths in lock-step (bl_fit_path_batched),
+      beside the plain form: bl_fit_path per problem (blocked CD, strong rule)
+      on that problem's rows, timed on two problems and scaled to 176, with the
+      largest coefficient difference between the two forms."""
+    import numpy as np
     import torch
     from paper_1701_05936_gb300 import bl, synth
     dev = torch.device("cuda", local)
@@ -214,6 +221,7 @@ def batched_zpass(local: int, reps: int = 20, plain_rhs: int = 8):
     cen = torch.zeros((F, bp.p), dtype=torch.float64, device=dev)
     sca = torch.zeros((F, bp.p), dtype=torch.float64, device=dev)
     nfit = []
+    fold_X = {}
     for f in range(F):   # each fit's c and s from bl_standardize on its rows (setup, untimed)
         rows = torch.from_numpy(bp.fit_rows(f)).to(dev)
         nf = int(rows.numel())
@@ -223,7 +231,10 @@ def batched_zpass(local: int, reps: int = 20, plain_rhs: int = 8):
         xn = torch.zeros(bp.p, dtype=torch.float64, device=dev)
         keep = torch.zeros(bp.p, dtype=torch.uint8, device=dev)
         bl.bl_standardize(ctx, Xf, nf, cen[f], sca[f], xn, keep)
-        del Xf
+        if f <= 1:
+            fold_X[f] = (Xf, nf)
+        else:
+            del Xf
         nfit.append(nf)
     Rd = torch.from_numpy(R).to(dev)
     fo = torch.from_numpy(fit_of).to(dev)
@@ -238,30 +249,28 @@ def batched_zpass(local: int, reps: int = 20, plain_rhs: int = 8):
     torch.cuda.synchronize()
     t = ctx.timing()["xtr"]
     ms = t["ms"] / max(1, t["launches"])
-    # the plain form: the FP32 z pass of a single residual (k_zpass), on the
-    # fits' own statistics, for a few residuals
-    xn = torch.zeros(bp.p, dtype=torch.float64, device=dev)
-    keep = torch.ones(bp.p, dtype=torch.uint8, device=dev)
-    scan = torch.ones(bp.p, dtype=torch.uint8, device=dev)
+    # the plain z pass: FP32 single-residual z pass (k_zpass) per residual
+    keep1 = torch.ones(bp.p, dtype=torch.uint8, device=dev)
     working = torch.zeros(bp.p, dtype=torch.uint8, device=dev)
     zp = torch.empty(bp.p, dtype=torch.float32, device=dev)
     xnorm = torch.sqrt((X[:, :bp.n].double() ** 2).sum(dim=1))
     ctx.set_timing(True)
     for b in range(plain_rhs):
         f = int(fit_of[b])
-        bl.bl_kkt_check(ctx, X, bp.n, cen[f], sca[f], xnorm, keep, Rd[b], 1.0, 1.0, scan, scan, working, zp)
+        bl.bl_kkt_check(ctx, X, bp.n, cen[f], sca[f], xnorm, keep1, Rd[b], 1.0, 1.0, keep1, keep1, working, zp)
     torch.cuda.synchronize()
     tp = ctx.timing()["zpass"]
     plain_ms = tp["ms"] / max(1, tp["launches"])
-    ctx.close()
+    del Z, Rd
     peaks, which = measured_peaks()
     tf32_peak = peaks["bf16_tflops"] * (1.1 / 2.25)
     bytes_alg = 4.0 * (bp.n * bp.p + bp.n * nrhs + nrhs * bp.p + 2 * F * bp.p)
     flops = 2.0 * bp.n * bp.p * nrhs
     gbs = bytes_alg / 1e9 / (ms / 1e3)
     tfs = flops / 1e12 / (ms / 1e3)
-    return {
-        "workload": f"ar1_{bp.n}x{bp.p}_f32_rho0.3, {bp.m} responses x ({bp.nfolds} folds + all rows) = {nrhs} residuals",
+    wl = f"ar1_{bp.n}x{bp.p}_f32_rho0.3, {bp.m} responses x ({bp.nfolds} folds + all rows) = {nrhs} problems"
+    zobj = {
+        "workload": wl,
         "kernel": "k_xtr_tf32 (tcgen05 TF32, TMEM accumulators, TMA tiles, formula-(3) epilogue)",
         "ms_per_pass": ms, "passes": reps,
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -272,6 +281,55 @@ def batched_zpass(local: int, reps: int = 20, plain_rhs: int = 8):
         "plain_form": {"form": "FP32 single-residual z pass (k_zpass) per residual", "ms_per_residual": plain_ms,
                        "ms_for_all": plain_ms * nrhs, "chosen_over_plain": plain_ms * nrhs / ms},
     }
+    # the batched path
+    Y = torch.from_numpy(np.ascontiguousarray(bp.Y)).to(dev)
+    fid = torch.from_numpy(bp.fold_id).to(dev)
+    kw = dict(alpha=bp.alpha, ratio=bp.ratio, nlambda=bp.nlambda, eps=bp.eps)
+    res = bl.bl_fit_path_batched(ctx, X, bp.n, Y, fid, bp.nfolds, **kw)
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(path_steps):
+        res = bl.bl_fit_path_batched(ctx, X, bp.n, Y, fid, bp.nfolds, **kw)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    bms = e0.elapsed_time(e1) / path_steps
+    tim = ctx.timing()
+    breakdown = {k: round(v["ms"] / path_steps, 3) for k, v in tim.items() if isinstance(v, dict) and v["launches"]}
+    # the plain form on problem 0 (response 0, all rows) and problem 1 (fold 0 left out)
+    pms, diff = [], 0.0
+    for b in (0, 1):
+        Xf, nf = fold_X[b]
+        rows = torch.from_numpy(bp.fit_rows(b)).to(dev)
+        yf = Y[0].index_select(0, rows).contiguous()
+        lam = res[0]["lambdas"].cpu().numpy() if b == 1 else None
+        kwp = dict(alpha=bp.alpha, eps=bp.eps, screen=bl.BL_SCREEN_SSR, cd_mode=bl.BL_CD_BLOCKED)
+        if lam is None:
+            kwp.update(ratio=bp.ratio, nlambda=bp.nlambda)
+        else:
+            kwp.update(lambdas=lam)
+        bl.bl_fit_path(ctx, Xf, nf, yf, **kwp)
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(ctx.stream)
+        single = bl.bl_fit_path(ctx, Xf, nf, yf, **kwp)
+        p1.record(ctx.stream)
+        torch.cuda.synchronize()
+        pms.append(p0.elapsed_time(p1))
+        diff = max(diff, float((bl.path_dense(single, bp.p) - bl.path_dense(res[b], bp.p)).abs().max()))
+    ctx.close()
+    nB = len(res)
+    plain_all = sum(pms) / len(pms) * nB
+    pobj = {
+        "workload": wl + f", {bp.nlambda} lambdas to {bp.ratio} lambda_max, alpha {bp.alpha}",
+        "value": nB / (bms / 1e3), "unit": "paths/s", "ms_per_step": bms, "steps": path_steps,
+        "kernel_ms_per_step": breakdown,
+        "plain_form": {"form": "bl_fit_path per problem on its rows (blocked CD, strong rule), 2 problems timed",
+                       "ms_per_problem": pms, "ms_for_all": plain_all, "chosen_over_plain": plain_all / bms,
+                       "max_abs_coef_diff_chosen_vs_plain": diff},
+    }
+    return zobj, pobj
 
 
 def config(prob):
@@ -424,7 +482,7 @@ def run_ours(args):
         "kernel_ms_per_step": breakdown, "status": res["status"],
     }
     if rank == 0 and not args.no_batched:
-        line["batched_zpass"] = batched_zpass(local)
+        line["batched_zpass"], line["batched_path"] = batched(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob)
     ctx.close()

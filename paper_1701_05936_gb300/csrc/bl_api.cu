@@ -754,17 +754,21 @@ extern "C" int bl_fit_path_batched(bl_ctx *ctx, const void *X, int dtype, int64_
             CK(cudaMemcpyAsync(wh.data(), w, (size_t)B * 8, cudaMemcpyDeviceToHost, s));
             CK(cudaMemcpyAsync(sth.data(), status, (size_t)B * 4, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
+            int64_t wmax = 0;
             for (int b = 0; b < B; ++b) {
                 if (sth[(size_t)b] & ST_WORKING_TOO_BIG)
                     return fail(ctx, BL_ERR_UNSUPPORTED, "a working set exceeds the batched CD capacity");
                 if (strong0[(size_t)b] < 0) strong0[(size_t)b] = wh[(size_t)b];
+                if (acth[(size_t)b]) wmax = std::max(wmax, wh[(size_t)b]);
             }
+            // the CD's shared memory is sized by the largest working set of the round
+            const int64_t lds = std::min<int64_t>(cap, std::max<int64_t>(32, (wmax + 31) / 32 * 32));
             ++rounds;
             slot = tbegin(ctx, 9);
             LAUNCH(1, launch_bgref(Xf, n, ldx, p, B, F, cen, idx, w, cap, r64, active, gref, ctx->num_sms, s));
             tend(ctx, slot, 0.0);
             slot = tbegin(ctx, 5);
-            LAUNCH(1, launch_bcd(Xf, n, ldx, p, B, F, fold_id, nfit_d, c32, is32, idx, w, cap, gref, lam_b, alpha, beta,
+            LAUNCH(1, launch_bcd(Xf, n, ldx, p, B, F, fold_id, nfit_d, c32, is32, idx, w, cap, lds, gref, lam_b, alpha, beta,
                                  r32, ldr, eps, opt->max_sweeps, CD_TIME_LIMIT_NS, status, sweeps_d, updates_d, active,
                                  s));
             tend(ctx, slot, 0.0);

@@ -226,7 +226,7 @@ template <int RPT>
 __global__ void __launch_bounds__(256, 1)
     k_bcd(const float *__restrict__ X, int64_t n, int64_t ldx, int64_t p, int F, const int8_t *__restrict__ fold,
           const double *__restrict__ nfit, const float *__restrict__ c32, const float *__restrict__ is32,
-          const int32_t *__restrict__ idx_all, const int64_t *__restrict__ w_all, int64_t cap,
+          const int32_t *__restrict__ idx_all, const int64_t *__restrict__ w_all, int64_t cap, int64_t lds,
           const float *__restrict__ gref_all, const double *__restrict__ lam_b, double alpha, float *beta_all,
           float *r32, int64_t ldr, double eps, int64_t max_sweeps, uint64_t time_limit_ns, int *status_all,
           unsigned long long *sweeps_all, unsigned long long *updates_all, const int *__restrict__ active)
@@ -236,17 +236,21 @@ __global__ void __launch_bounds__(256, 1)
     const int b = blockIdx.x, f = b % F;
     if (!active[b]) return;
     const int64_t w = w_all[b];
+    if (w > lds) {  // shared memory sized below this working set: touch nothing
+        if (threadIdx.x == 0) atomicOr(&status_all[b], ST_WORKING_TOO_BIG);
+        return;
+    }
     const int32_t *idx = idx_all + (int64_t)b * cap;
     const float *gref = gref_all + (int64_t)b * cap;
     float *beta = beta_all + (int64_t)b * p;
     const float *cvec = c32 + (int64_t)f * p, *isvec = is32 + (int64_t)f * p;
     extern __shared__ __align__(16) unsigned char smem[];
-    float *c_s = reinterpret_cast<float *>(smem);
-    float *is_s = c_s + cap;
-    float *g_s = is_s + cap;
-    float *beta_s = g_s + cap;
-    int32_t *idx_s = reinterpret_cast<int32_t *>(beta_s + cap);
-    uint16_t *act_s = reinterpret_cast<uint16_t *>(idx_s + cap);
+    float *c_s = reinterpret_cast<float *>(smem);  // lds entries each
+    float *is_s = c_s + lds;
+    float *g_s = is_s + lds;
+    float *beta_s = g_s + lds;
+    int32_t *idx_s = reinterpret_cast<int32_t *>(beta_s + lds);
+    uint16_t *act_s = reinterpret_cast<uint16_t *>(idx_s + lds);
     __shared__ float red[2][NW];
     __shared__ unsigned int scan_s[NW + 1];
     __shared__ int flag_s;
@@ -626,21 +630,21 @@ cudaError_t launch_bgref(const float *X, int64_t n, int64_t ldx, int64_t p, int 
     return cudaGetLastError();
 }
 
-size_t bcd_smem(int64_t cap) { return (size_t)cap * (4 * 4 + 4 + 2); }
+size_t bcd_smem(int64_t lds) { return (size_t)lds * (4 * 4 + 4 + 2); }
 
 cudaError_t launch_bcd(const float *X, int64_t n, int64_t ldx, int64_t p, int B, int F, const int8_t *fold,
                        const double *nfit, const float *c32, const float *is32, const int32_t *idx, const int64_t *w,
-                       int64_t cap, const float *gref, const double *lam_b, double alpha, float *beta, float *r32,
-                       int64_t ldr, double eps, int64_t max_sweeps, uint64_t time_limit_ns, int *status,
+                       int64_t cap, int64_t lds, const float *gref, const double *lam_b, double alpha, float *beta,
+                       float *r32, int64_t ldr, double eps, int64_t max_sweeps, uint64_t time_limit_ns, int *status,
                        unsigned long long *sweeps, unsigned long long *updates, const int *active, cudaStream_t st)
 {
-    const size_t smem = bcd_smem(cap);
+    const size_t smem = bcd_smem(lds);
     const int64_t nch = (n + 3) / 4;
 #define BL_BCD(RPT_)                                                                                               \
     do {                                                                                                           \
         cudaError_t e = cudaFuncSetAttribute(k_bcd<RPT_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e;                                                                            \
-        k_bcd<RPT_><<<B, 256, smem, st>>>(X, n, ldx, p, F, fold, nfit, c32, is32, idx, w, cap, gref, lam_b, alpha, \
+        k_bcd<RPT_><<<B, 256, smem, st>>>(X, n, ldx, p, F, fold, nfit, c32, is32, idx, w, cap, lds, gref, lam_b, alpha, \
                                           beta, r32, ldr, eps, max_sweeps, time_limit_ns, status, sweeps, updates,  \
                                           active);                                                                 \
         return cudaGetLastError();                                                                                 \

@@ -151,10 +151,10 @@ cudaError_t launch_bcompact(int64_t p, int B, const uint8_t *inW, int32_t *idx, 
 cudaError_t launch_bgref(const float *X, int64_t n, int64_t ldx, int64_t p, int B, int F, const double *cen,
                          const int32_t *idx, const int64_t *w, int64_t cap, const double *r64, const int *active,
                          float *gref, int num_sms, cudaStream_t st);
-size_t bcd_smem(int64_t cap);
+size_t bcd_smem(int64_t lds);
 cudaError_t launch_bcd(const float *X, int64_t n, int64_t ldx, int64_t p, int B, int F, const int8_t *fold,
                        const double *nfit, const float *c32, const float *is32, const int32_t *idx, const int64_t *w,
-                       int64_t cap, const float *gref, const double *lam_b, double alpha, float *beta, float *r32,
+                       int64_t cap, int64_t lds, const float *gref, const double *lam_b, double alpha, float *beta, float *r32,
                        int64_t ldr, double eps, int64_t max_sweeps, uint64_t time_limit_ns, int *status,
                        unsigned long long *sweeps, unsigned long long *updates, const int *active, cudaStream_t st);
 cudaError_t launch_bresid(const float *X, int64_t n, int64_t ldx, int64_t p, int B, int F, const int8_t *fold,
