@@ -69,6 +69,10 @@ def lib():
             L.orc_objective.restype = C.c_double
             L.orc_fit_path.argtypes = [_dp, i64, i64, i64, _dp, C.c_double, _dp, C.c_int, C.c_int,
                                        C.c_double, i64, _dp, _dp, _dp, _dp, _i64p]
+            L.orc_mlp_nparam.argtypes = []
+            L.orc_mlp_forward.argtypes = [_dp, _dp, i64, _dp]
+            L.orc_mlp_loss_grad.argtypes = [_dp, _dp, _u8p, i64, _dp]
+            L.orc_mlp_loss_grad.restype = C.c_double
             _lib = L
     return _lib
 
@@ -229,6 +233,31 @@ def fit_path(X, y, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, lambdas=None,
     return dict(lambdas=lambdas, beta=beta, beta_orig=beta_orig, intercept=icpt, loss=loss,
                 sweeps=sweeps, status=st, lmax=lmax, jstar=jstar, c=c, s=s, keep=keep,
                 ybar=ybar, xty=xty)
+
+
+def mlp_nparam():
+    """Parameter count of the proposer's 5 -> 64 -> 64 -> 1 perceptron."""
+    return lib().orc_mlp_nparam()
+
+
+def mlp_forward(w, F):
+    """Logits of the proposer's perceptron for each feature row (N x 5), FP64."""
+    w, F = _f64(w), _f64(F)
+    N = F.shape[0]
+    out = np.empty(N)
+    lib().orc_mlp_forward(_p(w), _p(np.ascontiguousarray(F)), N, _p(out))
+    return out
+
+
+def mlp_loss_grad(w, F, y):
+    """Mean binary cross-entropy of the logits against labels y and its analytic
+    gradient with respect to every parameter, FP64."""
+    w, F = _f64(w), _f64(F)
+    N = F.shape[0]
+    g = np.empty(w.size)
+    yy = np.ascontiguousarray(y, dtype=np.uint8)
+    loss = lib().orc_mlp_loss_grad(_p(w), _p(np.ascontiguousarray(F)), _p(yy, _u8p), N, _p(g))
+    return loss, g
 
 
 class PathRunner:

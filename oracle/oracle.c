@@ -386,3 +386,87 @@ done:
     free(idx);
     return status;
 }
+
+/* ------------------------------------------------------------------------
+ * The learned working-set proposer's model: a 5 -> 64 -> 64 -> 1 perceptron
+ * with ReLU hidden layers and a logistic output, trained by binary
+ * cross-entropy.  Parameters, in order (4609 values):
+ *   W1[64][5] (row h: weights of hidden unit h), b1[64],
+ *   W2[64][64] (row o: weights of second-layer unit o), b2[64],
+ *   W3[64], b3.
+ * orc_mlp_forward: logit o(f) for each of N feature rows f (N x 5).
+ * orc_mlp_loss_grad: mean over the N samples of
+ *   max(o, 0) - y o + log(1 + exp(-|o|))   (= -y log s(o) - (1-y) log(1-s(o)))
+ * and its gradient with respect to every parameter, by the chain rule
+ * (dL/do = s(o) - y, back through each layer; ReLU passes where its input > 0).
+ * ---------------------------------------------------------------------- */
+#define MLP_IN 5
+#define MLP_H 64
+#define MLP_NPARAM (MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1)
+
+static void mlp_layers(const double *w, const double *f, double *a1, double *h1, double *a2, double *h2, double *o)
+{
+    const double *W1 = w, *b1 = W1 + MLP_H * MLP_IN, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H;
+    const double *W3 = b2 + MLP_H, *b3 = W3 + MLP_H;
+    for (int h = 0; h < MLP_H; ++h) {
+        double s = b1[h];
+        for (int i = 0; i < MLP_IN; ++i) s += W1[h * MLP_IN + i] * f[i];
+        a1[h] = s;
+        h1[h] = s > 0.0 ? s : 0.0;
+    }
+    for (int u = 0; u < MLP_H; ++u) {
+        double s = b2[u];
+        for (int h = 0; h < MLP_H; ++h) s += W2[u * MLP_H + h] * h1[h];
+        a2[u] = s;
+        h2[u] = s > 0.0 ? s : 0.0;
+    }
+    double s = b3[0];
+    for (int u = 0; u < MLP_H; ++u) s += W3[u] * h2[u];
+    *o = s;
+}
+
+int orc_mlp_nparam(void) { return MLP_NPARAM; }
+
+void orc_mlp_forward(const double *w, const double *F, i64 N, double *logit)
+{
+    double a1[MLP_H], h1[MLP_H], a2[MLP_H], h2[MLP_H];
+    for (i64 s = 0; s < N; ++s) mlp_layers(w, F + (size_t)s * MLP_IN, a1, h1, a2, h2, &logit[s]);
+}
+
+double orc_mlp_loss_grad(const double *w, const double *F, const uint8_t *y, i64 N, double *grad)
+{
+    const double *W2 = w + MLP_H * MLP_IN + MLP_H, *W3 = W2 + MLP_H * MLP_H + MLP_H;
+    double *gW1 = grad, *gb1 = gW1 + MLP_H * MLP_IN, *gW2 = gb1 + MLP_H, *gb2 = gW2 + MLP_H * MLP_H;
+    double *gW3 = gb2 + MLP_H, *gb3 = gW3 + MLP_H;
+    for (int t = 0; t < MLP_NPARAM; ++t) grad[t] = 0.0;
+    double loss = 0.0;
+    double a1[MLP_H], h1[MLP_H], a2[MLP_H], h2[MLP_H], d2[MLP_H], d1[MLP_H];
+    for (i64 s = 0; s < N; ++s) {
+        const double *f = F + (size_t)s * MLP_IN;
+        double o;
+        mlp_layers(w, f, a1, h1, a2, h2, &o);
+        const double yy = y[s] ? 1.0 : 0.0;
+        loss += (o > 0.0 ? o : 0.0) - yy * o + log1p(exp(-fabs(o)));
+        const double sig = 1.0 / (1.0 + exp(-o));
+        const double dout = (sig - yy) / (double)N;
+        gb3[0] += dout;
+        for (int u = 0; u < MLP_H; ++u) {
+            gW3[u] += dout * h2[u];
+            d2[u] = (a2[u] > 0.0) ? dout * W3[u] : 0.0;
+        }
+        for (int u = 0; u < MLP_H; ++u) {
+            gb2[u] += d2[u];
+            for (int h = 0; h < MLP_H; ++h) gW2[u * MLP_H + h] += d2[u] * h1[h];
+        }
+        for (int h = 0; h < MLP_H; ++h) {
+            double s2 = 0.0;
+            for (int u = 0; u < MLP_H; ++u) s2 += W2[u * MLP_H + h] * d2[u];
+            d1[h] = (a1[h] > 0.0) ? s2 : 0.0;
+        }
+        for (int h = 0; h < MLP_H; ++h) {
+            gb1[h] += d1[h];
+            for (int i = 0; i < MLP_IN; ++i) gW1[h * MLP_IN + i] += d1[h] * f[i];
+        }
+    }
+    return loss / (double)N;
+}

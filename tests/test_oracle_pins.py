@@ -375,6 +375,67 @@ def test_cd_on_subset_matches_brute_force_on_subdesign():
         np.testing.assert_allclose(r, yc - Xt.T @ beta, atol=1e-12)
 
 
+# ------------------------------------------- learned proposer's perceptron ---
+def _mlp_case(seed, N=37):
+    """Random weights and features with no ReLU input within 1e-4 of its kink
+    (so central differences do not straddle one)."""
+    rng = np.random.default_rng(seed)
+    while True:
+        w = rng.standard_normal(oracle.mlp_nparam()) * 0.3
+        F = rng.standard_normal((N, 5))
+        y = rng.random(N) < 0.4
+        W1, b1 = w[:320].reshape(64, 5), w[320:384]
+        W2, b2 = w[384:4480].reshape(64, 64), w[4480:4544]
+        a1 = F @ W1.T + b1
+        a2 = np.maximum(a1, 0) @ W2.T + b2
+        if np.abs(a1).min() > 1e-4 and np.abs(a2).min() > 1e-4:
+            return w, F, y
+
+
+def test_mlp_gradient_matches_central_differences():
+    # every parameter's analytic derivative against (L(w + h e) - L(w - h e)) / 2h
+    w, F, y = _mlp_case(5)
+    loss, g = oracle.mlp_loss_grad(w, F, y)
+    logit = oracle.mlp_forward(w, F)
+    ref = np.mean(np.maximum(logit, 0) - y * logit + np.log1p(np.exp(-np.abs(logit))))
+    assert abs(loss - ref) < 1e-13 * max(1.0, abs(ref))
+    h = 1e-5
+    num = np.empty_like(g)
+    for t in range(w.size):
+        wp, wm = w.copy(), w.copy()
+        wp[t] += h
+        wm[t] -= h
+        num[t] = (oracle.mlp_loss_grad(wp, F, y)[0] - oracle.mlp_loss_grad(wm, F, y)[0]) / (2 * h)
+    err = np.abs(num - g) / (np.abs(g) + 1e-4)
+    assert err.max() < 1e-6, err.max()
+
+
+def test_mlp_closed_form_network():
+    # weights that compute logit = 2 relu(f0) + 0.5 relu(-f1) - 1 exactly
+    w = np.zeros(oracle.mlp_nparam())
+    W1 = w[:320].reshape(64, 5)
+    W2 = w[384:4480].reshape(64, 64)
+    W1[0, 0], W1[1, 1] = 1.0, -1.0
+    W2[0, 0], W2[1, 1] = 1.0, 1.0
+    w[4544], w[4545], w[4608] = 2.0, 0.5, -1.0
+    F = np.array([[0.7, 0.2, 0, 0, 0], [-0.3, -1.5, 9, 9, 9], [1.25, -0.5, -2, 3, 1]])
+    y = np.array([1, 0, 1], dtype=np.uint8)
+    o = oracle.mlp_forward(w, F)
+    expect = 2 * np.maximum(F[:, 0], 0) + 0.5 * np.maximum(-F[:, 1], 0) - 1
+    np.testing.assert_array_equal(o, expect)
+    loss, g = oracle.mlp_loss_grad(w, F, y)
+    sig = 1 / (1 + np.exp(-expect))
+    d = (sig - y) / 3
+    assert abs(g[4608] - d.sum()) < 1e-15                                  # b3
+    assert abs(g[4544] - (d * np.maximum(F[:, 0], 0)).sum()) < 1e-15      # W3[0] sees h2_0 = relu(f0)
+    for i in range(5):   # W1[0][i] through W2[0][0] = 1, W3[0] = 2; W1[1][i] through W2[1][1] = 1, W3[1] = 0.5
+        assert abs(g[i] - (d * 2 * F[:, i] * (F[:, 0] > 0)).sum()) < 1e-15
+        assert abs(g[5 + i] - (d * 0.5 * F[:, i] * (-F[:, 1] > 0)).sum()) < 1e-15
+    assert np.all(g[10:320] == 0) and np.all(g[322:384] == 0)   # hidden units 2..63 never open (input exactly 0)
+    gW2 = g[384:4480].reshape(64, 64)
+    assert gW2[0, 0] != 0 and np.all(gW2[2:] == 0) and np.all(gW2[:, 2:] == 0)
+
+
 # ------------------------------------------------------- planted mistakes ---
 _MUTATIONS = {
     "dropped_ridge_term": ("den = 1.0 + lam * (1.0 - alpha);", "den = 1.0;"),
@@ -383,6 +444,8 @@ _MUTATIONS = {
                           "s[j] = varies ? sqrt(ss / (double)(n - 1)) : 0.0;"),
     "bedpp_sign_flip": ("- (lmax - lam) * sstar * lmax * xtxstar[j]",
                         "+ (lmax - lam) * sstar * lmax * xtxstar[j]"),
+    "mlp_relu_mask_dropped": ("d2[u] = (a2[u] > 0.0) ? dout * W3[u] : 0.0;", "d2[u] = dout * W3[u];"),
+    "mlp_transposed_backprop": ("s2 += W2[u * MLP_H + h] * d2[u];", "s2 += W2[h * MLP_H + u] * d2[u];"),
 }
 
 
@@ -406,6 +469,8 @@ def test_planted_mistake_in_oracle_copy_is_caught(name, monkeypatch):
                 test_bedpp_matches_vector_form_edpp()
             elif name == "sample_sd_divisor":
                 test_standardize_invariants_and_constant_columns()
+            elif name.startswith("mlp_"):
+                test_mlp_gradient_matches_central_differences()
             else:
                 test_brute_force_support_enumeration(0.5, 0.3, 6)
         except AssertionError:
