@@ -71,7 +71,11 @@ typedef enum {
 typedef enum {
     BL_SCREEN_NONE = 0,      /* every kept feature is scanned and enters CD */
     BL_SCREEN_SSR = 1,       /* strong rule + KKT check over all features */
-    BL_SCREEN_SSR_BEDPP = 2  /* hybrid rule of Sec. 2.2 (default) */
+    BL_SCREEN_SSR_BEDPP = 2, /* hybrid rule of Sec. 2.2 (default) */
+    BL_SCREEN_LEARNED = 3    /* BEDPP safe set (Sec. 2.2); the working set is the previous
+                                active set plus the features a trained perceptron proposes
+                                (bl_mlp_*), in place of the strong rule; the KKT check
+                                judges, so the path stays exact */
 } bl_screen_rule;
 
 typedef struct bl_ctx bl_ctx;
@@ -89,6 +93,9 @@ typedef struct {
     int64_t max_sweeps;      /* cap on CD sweeps per lambda (e.g. 100000) */
     int32_t screen;          /* bl_screen_rule */
     int32_t cd_mode;         /* bl_cd_mode (0 = residual updates) */
+    const float *proposer;   /* device [BL_MLP_NPARAM] perceptron parameters for
+                                BL_SCREEN_LEARNED (NULL otherwise) */
+    double proposer_tau;     /* proposal threshold on the predicted probability, in (0, 1) */
 } bl_options;
 
 /* Outputs of bl_fit_path.  Pointers marked device are caller-allocated device
@@ -116,6 +123,15 @@ typedef struct {
     double lambda_max;     /* out (host) */
     int64_t jstar;         /* out (host): column attaining lambda_max, -1 if none */
     double ybar;           /* out (host): mean(y) */
+    /* Proposer training capture (bl_fit_path only; all NULL / 0 to skip): at each
+     * lambda_k the features of every proposal candidate (see bl_mlp_train) and, once
+     * lambda_k is solved, its label b_j(lambda_k) != 0.  Rows past prop_cap are
+     * counted in prop_count but not written. */
+    float *prop_feat;      /* device [prop_cap x 5] */
+    int32_t *prop_idx;     /* device [prop_cap]: the candidate's feature index j */
+    uint8_t *prop_label;   /* device [prop_cap] */
+    int64_t prop_cap;
+    int64_t prop_count;    /* out (host): candidates seen */
 } bl_path;
 
 /* Per-kernel timing collected with CUDA events on the ctx stream while timing
@@ -331,6 +347,50 @@ int bl_xtr_batched(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, 
 int bl_fit_path_batched(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx, const double *Y,
                         int64_t ldy, int64_t m, const int8_t *fold_id, int64_t nfolds, const bl_options *opt, int nlambda,
                         bl_path *outs);
+
+/* ------------------------------------------------ learned working-set proposer
+ * A perceptron 5 -> 64 -> 64 -> 1 (ReLU hidden layers, logistic output) that
+ * proposes, at lambda_k, the features to add to the working set in place of the
+ * strong rule of Sec. 2.2 (bl_options.screen = BL_SCREEN_LEARNED).  The paper has
+ * no such proposer: it is a learned replacement for the strong rule's heuristic,
+ * and the KKT check of Sec. 2.2 keeps every path exact.
+ * Parameters (BL_MLP_NPARAM FP32 values, in order): W1[64][5] (row h = hidden
+ * unit h), b1[64], W2[64][64] (row u = second-layer unit u), b2[64], W3[64], b3.
+ * Candidates at lambda_k: kept, BEDPP-safe features with b_j(lambda_{k-1}) = 0 and
+ * abs(z_j(lambda_{k-1})) >= 0.5 alpha lambda_k, where z is the z pass of Sec. 3.1.1.
+ * Features: abs(z_j) at lambda_{k-1}, lambda_{k-2}, lambda_{k-3}, each divided by
+ * alpha lambda_k; (abs(z_j(lambda_{k-1})) - abs(z_j(lambda_{k-2}))) /
+ * (lambda_{k-2} - lambda_{k-1}) (0 if equal); lambda_k / lambda_{k-1}; lambdas and
+ * z before the first solved lambda are those of that lambda.  A candidate is
+ * proposed when its predicted probability exceeds proposer_tau. */
+#define BL_MLP_NPARAM 4609
+
+/* logit[s] of each feature row F[s] (device FP32, N x 5 row-major); w device.
+ * BL_ERR_ARG on NULL or N < 0.  Synchronizes. */
+int bl_mlp_predict(bl_ctx *ctx, const float *w, const float *F, int64_t N, float *logit);
+
+/* Mean logistic loss of the logits against labels y (device uint8 [N], 0/1) and
+ * its gradient (device FP32 [BL_MLP_NPARAM]) with respect to every parameter;
+ * *loss (host, nullable).  Deterministic.  BL_ERR_ARG on NULL or N < 1. */
+int bl_mlp_loss_grad(bl_ctx *ctx, const float *w, const float *F, const uint8_t *y, int64_t N, float *grad,
+                     double *loss);
+
+/* Train the perceptron in place (w device, in: initial parameters, out: trained)
+ * by Adam (lr, beta1 0.9, beta2 0.999, eps 1e-8) on minibatches of `batch` rows
+ * of (F, y), the order shuffled every epoch from `seed`; loss_per_epoch (host
+ * [epochs], nullable) receives each epoch's mean loss.  Deterministic for a
+ * given seed.  BL_ERR_ARG on bad arguments.  Allocates and frees its scratch. */
+int bl_mlp_train(bl_ctx *ctx, const float *F, const uint8_t *y, int64_t N, float *w, int epochs, int64_t batch,
+                 double lr, uint64_t seed, double *loss_per_epoch);
+
+/* Write the BL_MLP_NPARAM parameters held in host memory to a text file: a
+ * header line "biglasso-proposer 5 64 64 1" and one value per line (%.9g, exact
+ * for FP32).  BL_ERR_ARG when the file cannot be written.  No context needed. */
+int bl_mlp_save(const float *w_host, const char *path);
+
+/* Read parameters written by bl_mlp_save into host memory (BL_MLP_NPARAM values).
+ * BL_ERR_ARG when the file cannot be opened or its header or length differ. */
+int bl_mlp_load(float *w_host, const char *path);
 
 /* Largest working set that bl_cd_active_noalloc accepts. */
 #define BL_NOALLOC_MAX_WORK 4096

@@ -25,7 +25,8 @@ from . import build as _build
 BL_OK, BL_ERR_ARG, BL_ERR_CUDA, BL_ERR_OOM = 0, -1, -2, -3
 BL_ERR_NOT_CONVERGED, BL_ERR_TIMEOUT, BL_ERR_UNSUPPORTED, BL_ERR_CAPACITY = -4, -5, -6, -7
 BL_F64, BL_F32, BL_BF16, BL_I8 = 0, 1, 2, 3
-BL_SCREEN_NONE, BL_SCREEN_SSR, BL_SCREEN_SSR_BEDPP = 0, 1, 2
+BL_SCREEN_NONE, BL_SCREEN_SSR, BL_SCREEN_SSR_BEDPP, BL_SCREEN_LEARNED = 0, 1, 2, 3
+BL_MLP_NPARAM = 4609
 BL_CD_RESIDUAL, BL_CD_COVARIANCE, BL_CD_BLOCKED = 0, 1, 2
 KINDS = ["standardize", "lambda_max", "bedpp_init", "screen", "compact", "cd", "residual", "zpass", "record",
          "gref", "xtr", "kkt"]
@@ -43,7 +44,8 @@ class BLError(RuntimeError):
 
 class bl_options(C.Structure):
     _fields_ = [("alpha", C.c_double), ("eps", C.c_double), ("lambda_min_ratio", C.c_double),
-                ("max_sweeps", C.c_int64), ("screen", C.c_int32), ("cd_mode", C.c_int32)]
+                ("max_sweeps", C.c_int64), ("screen", C.c_int32), ("cd_mode", C.c_int32),
+                ("proposer", C.c_void_p), ("proposer_tau", C.c_double)]
 
 
 class bl_path(C.Structure):
@@ -52,7 +54,9 @@ class bl_path(C.Structure):
                 ("nnz_needed", C.c_int64), ("intercept", C.c_void_p), ("loss", C.c_void_p),
                 ("sweeps", C.c_void_p), ("n_safe", C.c_void_p), ("n_strong", C.c_void_p),
                 ("kkt_rounds", C.c_void_p), ("cols_scanned", C.c_void_p), ("n_active", C.c_void_p),
-                ("lambda_max", C.c_double), ("jstar", C.c_int64), ("ybar", C.c_double)]
+                ("lambda_max", C.c_double), ("jstar", C.c_int64), ("ybar", C.c_double),
+                ("prop_feat", C.c_void_p), ("prop_idx", C.c_void_p), ("prop_label", C.c_void_p),
+                ("prop_cap", C.c_int64), ("prop_count", C.c_int64)]
 
 
 class bl_timing(C.Structure):
@@ -101,6 +105,11 @@ def lib():
                                    _i64],
                 "bl_fit_path_batched": [_vp, *X, _vp, _i64, _i64, _vp, _i64, C.POINTER(bl_options), _int,
                                         C.POINTER(bl_path)],
+                "bl_mlp_predict": [_vp, _vp, _vp, _i64, _vp],
+                "bl_mlp_loss_grad": [_vp, _vp, _vp, _vp, _i64, _vp, C.POINTER(_dbl)],
+                "bl_mlp_train": [_vp, _vp, _vp, _i64, _vp, _int, _i64, _dbl, C.c_uint64, C.POINTER(_dbl)],
+                "bl_mlp_save": [_vp, C.c_char_p],
+                "bl_mlp_load": [_vp, C.c_char_p],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -252,10 +261,14 @@ def bl_cd_active_noalloc(device, stream, X, n, center, scale, work_idx, lam, alp
 
 
 def bl_fit_path(ctx, X, n, y, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, lambdas=None,
-                screen=BL_SCREEN_SSR_BEDPP, max_sweeps=100_000, nnz_capacity=None, cd_mode=BL_CD_RESIDUAL):
+                screen=BL_SCREEN_SSR_BEDPP, max_sweeps=100_000, nnz_capacity=None, cd_mode=BL_CD_RESIDUAL,
+                proposer=None, proposer_tau=0.5, capture=0):
     """The whole path on the GPU.  X (p, ldx) and y (n, float64) on the ctx's
     device.  Returns a dict of device tensors (lambdas, col_ptr, row_idx, val,
-    val_orig, intercept, loss) and host tensors (per-lambda counters)."""
+    val_orig, intercept, loss) and host tensors (per-lambda counters).
+    proposer: device FP32 parameters for screen=BL_SCREEN_LEARNED; capture > 0
+    returns up to that many proposer candidates (prop_feat, prop_idx,
+    prop_label, prop_count)."""
     dev = X.device
     p = int(X.shape[0])
     K = int(nlambda if lambdas is None else len(lambdas))
@@ -279,15 +292,66 @@ def bl_fit_path(ctx, X, n, y, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, lambd
     for k, t in host.items():
         setattr(path, k, t.data_ptr())
     path.nnz_capacity = nnz_capacity
-    opt = bl_options(float(alpha), float(eps), float(ratio), int(max_sweeps), int(screen), int(cd_mode))
+    if capture > 0:
+        res["prop_feat"] = o((capture, 5), dtype=torch.float32, device=dev)
+        res["prop_idx"] = o(capture, dtype=torch.int32, device=dev)
+        res["prop_label"] = o(capture, dtype=torch.uint8, device=dev)
+        path.prop_feat = res["prop_feat"].data_ptr()
+        path.prop_idx = res["prop_idx"].data_ptr()
+        path.prop_label = res["prop_label"].data_ptr()
+        path.prop_cap = int(capture)
+    opt = bl_options(float(alpha), float(eps), float(ratio), int(max_sweeps), int(screen), int(cd_mode),
+                     None if proposer is None else proposer.data_ptr(), float(proposer_tau))
     lam_arr = None
     if lambdas is not None:
         lam_arr = (C.c_double * K)(*[float(v) for v in lambdas])
     st = lib().bl_fit_path(ctx.h, *design_args(X, n), _ptr(y), C.byref(opt), lam_arr, K, C.byref(path))
     ctx.check(st, allow=(BL_ERR_NOT_CONVERGED,))
     res.update(host)
-    res.update(status=st, nnz=path.nnz_needed, lambda_max=path.lambda_max, jstar=path.jstar, ybar=path.ybar)
+    res.update(status=st, nnz=path.nnz_needed, lambda_max=path.lambda_max, jstar=path.jstar, ybar=path.ybar,
+               prop_count=path.prop_count)
     return res
+
+
+def bl_mlp_predict(ctx, w, F):
+    """Logits of the proposer's perceptron (parameters w) for feature rows F (N, 5)."""
+    N = int(F.shape[0])
+    out = torch.empty(N, dtype=torch.float32, device=F.device)
+    ctx.check(lib().bl_mlp_predict(ctx.h, _ptr(w), _ptr(F), N, _ptr(out)))
+    return out
+
+
+def bl_mlp_loss_grad(ctx, w, F, y):
+    """(mean logistic loss, gradient) of the perceptron on rows F with labels y."""
+    g = torch.empty(BL_MLP_NPARAM, dtype=torch.float32, device=F.device)
+    loss = C.c_double()
+    ctx.check(lib().bl_mlp_loss_grad(ctx.h, _ptr(w), _ptr(F), _ptr(y), int(F.shape[0]), _ptr(g), C.byref(loss)))
+    return loss.value, g
+
+
+def bl_mlp_train(ctx, F, y, w, epochs=20, batch=4096, lr=1e-3, seed=0):
+    """Train w (device FP32, in place) on (F, y); returns the mean loss of each epoch."""
+    losses = (C.c_double * max(1, int(epochs)))()
+    ctx.check(lib().bl_mlp_train(ctx.h, _ptr(F), _ptr(y), int(F.shape[0]), _ptr(w), int(epochs), int(batch),
+                                 float(lr), int(seed) & ((1 << 64) - 1), losses))
+    return list(losses)[: int(epochs)]
+
+
+def mlp_save(w: torch.Tensor, path: str):
+    """Write proposer parameters (any device) to a text file."""
+    h = w.detach().to("cpu", torch.float32).contiguous()
+    st = lib().bl_mlp_save(C.c_void_p(h.data_ptr()), path.encode())
+    if st != BL_OK:
+        raise BLError(st, f"bl_mlp_save({path}) failed")
+
+
+def mlp_load(path: str) -> torch.Tensor:
+    """Read proposer parameters written by mlp_save (host FP32 tensor)."""
+    h = torch.empty(BL_MLP_NPARAM, dtype=torch.float32)
+    st = lib().bl_mlp_load(C.c_void_p(h.data_ptr()), path.encode())
+    if st != BL_OK:
+        raise BLError(st, f"bl_mlp_load({path}) failed")
+    return h
 
 
 def bl_fit_path_batched(ctx, X, n, Y, fold_id=None, nfolds=0, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7,

@@ -6,6 +6,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -56,6 +57,8 @@ struct bl_ctx {
     size_t gram_bytes = 0;
     void *xtr = nullptr;       // batched z pass: per-fit epilogue vectors, sum r, row counts
     size_t xtr_bytes = 0;
+    void *hist = nullptr;      // learned proposer: z at the three previous lambdas
+    size_t hist_bytes = 0;
     int64_t kernels = 0;
     int64_t cd_updates = 0;
 };
@@ -278,6 +281,7 @@ extern "C" int bl_ctx_destroy(bl_ctx *ctx)
     if (ctx->ws.base) cudaFree(ctx->ws.base);
     if (ctx->gram) cudaFree(ctx->gram);
     if (ctx->xtr) cudaFree(ctx->xtr);
+    if (ctx->hist) cudaFree(ctx->hist);
     if (ctx->sc_host) cudaFreeHost(ctx->sc_host);
     delete ctx;
     return BL_OK;
@@ -562,6 +566,148 @@ extern "C" int bl_xtr_batched(bl_ctx *ctx, const void *X, int dtype, int64_t n, 
     if ((st = sync_sc(ctx))) return st;
     if (ctx->sc_host->status & ST_TIMEOUT) return fail(ctx, BL_ERR_TIMEOUT, "batched z pass: a pipeline wait ran out");
     return BL_OK;
+}
+
+// ======================================================= learned proposer
+extern "C" int bl_mlp_predict(bl_ctx *ctx, const float *w, const float *F, int64_t N, float *logit)
+{
+    if (!ctx) return BL_ERR_ARG;
+    if (!w || !F || !logit || N < 0) return fail(ctx, BL_ERR_ARG, "NULL argument or N < 0");
+    ctx->err.clear();
+    if (N == 0) return BL_OK;
+    CK(cudaSetDevice(ctx->device));
+    LAUNCH(1, launch_mlp_forward(w, F, N, logit, ctx->num_sms, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return BL_OK;
+}
+
+namespace {
+struct MlpScratch {  // device scratch of one training / gradient call
+    float *part = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    double *lpart = nullptr, *loss = nullptr;
+    int32_t *order = nullptr;
+    ~MlpScratch()
+    {
+        cudaFree(part);
+        cudaFree(grad);
+        cudaFree(m);
+        cudaFree(v);
+        cudaFree(lpart);
+        cudaFree(loss);
+        cudaFree(order);
+    }
+};
+constexpr int MLP_GRAD_BLOCKS = 152;
+}  // namespace
+
+extern "C" int bl_mlp_loss_grad(bl_ctx *ctx, const float *w, const float *F, const uint8_t *y, int64_t N, float *grad,
+                                double *loss)
+{
+    if (!ctx) return BL_ERR_ARG;
+    if (!w || !F || !y || !grad || N < 1) return fail(ctx, BL_ERR_ARG, "NULL argument or N < 1");
+    ctx->err.clear();
+    CK(cudaSetDevice(ctx->device));
+    MlpScratch m;
+    CK(cudaMalloc(&m.part, (size_t)MLP_GRAD_BLOCKS * MLP_NPARAM * 4));
+    CK(cudaMalloc(&m.lpart, (size_t)MLP_GRAD_BLOCKS * 8));
+    CK(cudaMalloc(&m.loss, 8));
+    LAUNCH(2, launch_mlp_grad(w, F, y, nullptr, 0, N, (float)(1.0 / (double)N), m.part, m.lpart, MLP_GRAD_BLOCKS, grad,
+                              m.loss, ctx->stream));
+    double l = 0.0;
+    CK(cudaMemcpyAsync(&l, m.loss, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (loss) *loss = l / (double)N;
+    return BL_OK;
+}
+
+extern "C" int bl_mlp_train(bl_ctx *ctx, const float *F, const uint8_t *y, int64_t N, float *w, int epochs,
+                            int64_t batch, double lr, uint64_t seed, double *loss_per_epoch)
+{
+    if (!ctx) return BL_ERR_ARG;
+    if (!F || !y || !w || N < 1 || epochs < 0 || batch < 1 || !(lr > 0.0))
+        return fail(ctx, BL_ERR_ARG, "NULL argument, N < 1, epochs < 0, batch < 1 or lr <= 0");
+    if (N > 2147483647LL) return fail(ctx, BL_ERR_UNSUPPORTED, "N must fit in int32");
+    ctx->err.clear();
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    MlpScratch m;
+    CK(cudaMalloc(&m.part, (size_t)MLP_GRAD_BLOCKS * MLP_NPARAM * 4));
+    CK(cudaMalloc(&m.grad, (size_t)MLP_NPARAM * 4));
+    CK(cudaMalloc(&m.m, (size_t)MLP_NPARAM * 4));
+    CK(cudaMalloc(&m.v, (size_t)MLP_NPARAM * 4));
+    CK(cudaMalloc(&m.lpart, (size_t)MLP_GRAD_BLOCKS * 8));
+    CK(cudaMalloc(&m.loss, 8));
+    CK(cudaMalloc(&m.order, (size_t)N * 4));
+    CK(cudaMemsetAsync(m.m, 0, (size_t)MLP_NPARAM * 4, s));
+    CK(cudaMemsetAsync(m.v, 0, (size_t)MLP_NPARAM * 4, s));
+    // sample order per epoch: Fisher-Yates on a splitmix64 stream (host), so a
+    // run is reproducible from its seed
+    std::vector<int32_t> ord((size_t)N);
+    for (int64_t i = 0; i < N; ++i) ord[(size_t)i] = (int32_t)i;
+    uint64_t st = seed;
+    auto next = [&]() {
+        uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    int64_t step = 0;
+    for (int e = 0; e < epochs; ++e) {
+        for (int64_t i = N - 1; i > 0; --i) std::swap(ord[(size_t)i], ord[(size_t)(next() % (uint64_t)(i + 1))]);
+        CK(cudaMemcpyAsync(m.order, ord.data(), (size_t)N * 4, cudaMemcpyHostToDevice, s));
+        double esum = 0.0;
+        for (int64_t b0 = 0; b0 < N; b0 += batch) {
+            const int64_t b1i = std::min(N, b0 + batch);
+            const int nblk = (int)std::min<int64_t>(MLP_GRAD_BLOCKS, (b1i - b0 + 127) / 128);
+            LAUNCH(2, launch_mlp_grad(w, F, y, m.order, b0, b1i, (float)(1.0 / (double)(b1i - b0)), m.part, m.lpart,
+                                      nblk, m.grad, m.loss, s));
+            ++step;
+            const float c1 = 1.f - (float)std::pow((double)b1, (double)step);
+            const float c2 = 1.f - (float)std::pow((double)b2, (double)step);
+            LAUNCH(1, launch_mlp_adam(w, m.grad, m.m, m.v, (float)lr, b1, b2, eps, c1, c2, s));
+            if (loss_per_epoch) {
+                double l = 0.0;
+                CK(cudaMemcpyAsync(&l, m.loss, 8, cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                esum += l;
+            }
+        }
+        if (loss_per_epoch) loss_per_epoch[e] = esum / (double)N;
+        CK(cudaStreamSynchronize(s));  // the order buffer is rewritten next epoch
+    }
+    CK(cudaStreamSynchronize(s));
+    return BL_OK;
+}
+
+extern "C" int bl_mlp_save(const float *w_host, const char *path)
+{
+    if (!w_host || !path) return BL_ERR_ARG;
+    FILE *f = std::fopen(path, "w");
+    if (!f) return BL_ERR_ARG;
+    std::fprintf(f, "biglasso-proposer %d %d %d 1\n", MLP_IN, MLP_HIDDEN, MLP_HIDDEN);
+    for (int t = 0; t < MLP_NPARAM; ++t) std::fprintf(f, "%.9g\n", (double)w_host[t]);
+    const bool ok = std::fclose(f) == 0;
+    return ok ? BL_OK : BL_ERR_ARG;
+}
+
+extern "C" int bl_mlp_load(float *w_host, const char *path)
+{
+    if (!w_host || !path) return BL_ERR_ARG;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return BL_ERR_ARG;
+    int a = 0, b = 0, c = 0, d = 0;
+    int st = BL_OK;
+    if (std::fscanf(f, "biglasso-proposer %d %d %d %d", &a, &b, &c, &d) != 4 || a != MLP_IN || b != MLP_HIDDEN ||
+        c != MLP_HIDDEN || d != 1)
+        st = BL_ERR_ARG;
+    for (int t = 0; st == BL_OK && t < MLP_NPARAM; ++t) {
+        double v = 0.0;
+        if (std::fscanf(f, "%lf", &v) != 1) st = BL_ERR_ARG;
+        w_host[t] = (float)v;
+    }
+    std::fclose(f);
+    return st;
 }
 
 // ========================================================== batched path
@@ -858,7 +1004,11 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
     if (!(alpha > 0.0 && alpha <= 1.0)) return fail(ctx, BL_ERR_ARG, "alpha must be in (0, 1]");
     if (!(eps > 0.0)) return fail(ctx, BL_ERR_ARG, "eps must be > 0");
     if (opt->max_sweeps < 1) return fail(ctx, BL_ERR_ARG, "max_sweeps must be >= 1");
-    if (opt->screen < 0 || opt->screen > 2) return fail(ctx, BL_ERR_ARG, "unknown screening rule");
+    if (opt->screen < 0 || opt->screen > 3) return fail(ctx, BL_ERR_ARG, "unknown screening rule");
+    if (opt->screen == BL_SCREEN_LEARNED && (!opt->proposer || !(opt->proposer_tau > 0.0 && opt->proposer_tau < 1.0)))
+        return fail(ctx, BL_ERR_ARG, "the learned rule needs proposer weights and 0 < proposer_tau < 1");
+    if (out->prop_cap > 0 && (!out->prop_feat || !out->prop_idx || !out->prop_label))
+        return fail(ctx, BL_ERR_ARG, "prop_feat, prop_idx and prop_label are needed when prop_cap > 0");
     if (opt->cd_mode < 0 || opt->cd_mode > 2) return fail(ctx, BL_ERR_ARG, "unknown cd_mode");
     if (!lambdas_in && K > 1 && !(opt->lambda_min_ratio > 0.0 && opt->lambda_min_ratio < 1.0))
         return fail(ctx, BL_ERR_ARG, "lambda_min_ratio must be in (0, 1)");
@@ -943,7 +1093,6 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
         if (ctx->gram_bytes < need) {
             CK(cudaStreamSynchronize(s));
             if (ctx->gram) cudaFree(ctx->gram);
-    if (ctx->xtr) cudaFree(ctx->xtr);
             ctx->gram = nullptr;
             ctx->gram_bytes = 0;
             CK(cudaMalloc(&ctx->gram, need));
@@ -974,6 +1123,25 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
     ra.intercept = out->intercept;
     ra.loss = out->loss;
 
+    const bool learned = opt->screen == BL_SCREEN_LEARNED;
+    const bool capture = out->prop_cap > 0;
+    float *hist = nullptr;  // z(lambda_{k-1}), z(lambda_{k-2}), z(lambda_{k-3}) in a ring of three
+    if (learned || capture) {
+        const size_t need = 3 * (size_t)p * sizeof(float);
+        if (ctx->hist_bytes < need) {
+            CK(cudaStreamSynchronize(s));
+            if (ctx->hist) cudaFree(ctx->hist);
+            ctx->hist = nullptr;
+            ctx->hist_bytes = 0;
+            CK(cudaMalloc(&ctx->hist, need));
+            ctx->hist_bytes = need;
+        }
+        hist = (float *)ctx->hist;
+        CK(cudaMemsetAsync(&w.sc->prop_pos, 0, sizeof(unsigned long long), s));
+    }
+    out->prop_count = 0;
+    const float logit_tau = learned ? (float)std::log(opt->proposer_tau / (1.0 - opt->proposer_tau)) : 0.f;
+    int hist_k = -1;  // lambda index whose z history is current
     for (int k = 0; k < K; ++k) {
         const double lam = L[k];
         ra.k = k;
@@ -1008,6 +1176,7 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
         sa.lam_next = lam_next;
         sa.alpha = alpha;
         sa.rule = use_bedpp ? BL_SCREEN_SSR_BEDPP : (opt->screen == BL_SCREEN_NONE ? BL_SCREEN_NONE : BL_SCREEN_SSR);
+        sa.strong_prev_only = learned ? 1 : 0;
         sa.z_prev = w.z;
         sa.beta_prev = w.beta;
         sa.beta_f64 = beta_f64;
@@ -1017,6 +1186,31 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
         slot = tbegin(ctx, 3);
         LAUNCH(1, launch_screen(sa, w.sc, s));
         tend(ctx, slot, (double)p * 40);
+        unsigned long long q0 = 0;
+        if (learned || capture) {
+            // z now holds z(lambda_{k-1}); lambdas and z before the first solved
+            // lambda are those of that lambda
+            float *z1 = hist + (size_t)(k % 3) * p;
+            if (hist_k < 0) {
+                for (int t = 0; t < 3; ++t)
+                    CK(cudaMemcpyAsync(hist + (size_t)t * p, w.z, (size_t)p * 4, cudaMemcpyDeviceToDevice, s));
+            } else {
+                CK(cudaMemcpyAsync(z1, w.z, (size_t)p * 4, cudaMemcpyDeviceToDevice, s));
+            }
+            const bool first = hist_k < 0;
+            hist_k = k;
+            const float *z2 = hist + (size_t)((k + 2) % 3) * p, *z3 = hist + (size_t)((k + 1) % 3) * p;
+            const double lam1 = lam_prev;
+            const double lam2 = (!first && k >= 2) ? std::fmin(L[k - 2], lmax) : lam1;
+            CK(cudaMemcpyAsync(&q0, &w.sc->prop_pos, sizeof(q0), cudaMemcpyDeviceToHost, s));
+            CK(cudaMemsetAsync(&w.sc->n_prop, 0, sizeof(unsigned long long), s));
+            slot = tbegin(ctx, 3);
+            LAUNCH(1, launch_propose(p, w.keep, w.safe, w.beta, beta_f64, z1, z2, z3, lam, lam1, lam2, alpha,
+                                     learned ? opt->proposer : nullptr, logit_tau, w.working,
+                                     capture ? out->prop_feat : nullptr, out->prop_idx, out->prop_cap, &w.sc->prop_pos,
+                                     &w.sc->n_prop, ctx->num_sms, s));
+            tend(ctx, slot, 0.0);
+        }
         int64_t rounds = 0, cols = 0;
         for (;;) {
             slot = tbegin(ctx, 4);
@@ -1076,9 +1270,15 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
         LAUNCH(1, launch_record(ra, w.sc, s));
         tend(ctx, slot, 0.0);
         const DevScalars &h = *ctx->sc_host;
+        if (capture) {  // labels of this lambda's candidates: b_j(lambda_k) != 0
+            const int64_t q1 = std::min<int64_t>((int64_t)h.prop_pos, out->prop_cap);
+            LAUNCH(1, launch_label(out->prop_idx, std::min<int64_t>((int64_t)q0, out->prop_cap), q1, w.beta, beta_f64,
+                                   out->prop_label, s));
+            out->prop_count = (int64_t)h.prop_pos;
+        }
         if (out->sweeps) out->sweeps[k] = (int64_t)h.sweeps;
         if (out->n_safe) out->n_safe[k] = (int64_t)h.n_safe;
-        if (out->n_strong) out->n_strong[k] = (int64_t)h.n_strong;
+        if (out->n_strong) out->n_strong[k] = (int64_t)(h.n_strong + (learned ? h.n_prop : 0));
         if (out->kkt_rounds) out->kkt_rounds[k] = rounds;
         if (out->cols_scanned) out->cols_scanned[k] = cols;
     }

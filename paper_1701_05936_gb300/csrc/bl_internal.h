@@ -33,6 +33,8 @@ struct DevScalars {
     unsigned long long n_viol, n_cols, n_safe, n_strong, n_scan, w, sweeps;
     unsigned long long nnz_total;
     unsigned long long cd_updates;  // coordinate updates run by CD (never reset by rounds)
+    unsigned long long prop_pos;    // proposer candidates captured so far in this path
+    unsigned long long n_prop;      // features the proposer added at this lambda
     int status;
     int pad;
 };
@@ -81,6 +83,7 @@ struct ScreenArgs {
     double lam, lam_prev, lam_next;  // lam_next < 0: no next lambda
     double alpha;
     int rule;          // bl_screen_rule
+    int strong_prev_only;  // strong set = safe and previously active (the learned rule adds the rest)
     const float *z_prev;
     const void *beta_prev;  // nullable
     int beta_f64;
@@ -128,6 +131,24 @@ cudaError_t launch_cd_gram(int dtype, const void *Rm, int64_t n, int64_t p, cons
 
 // Residual-form CD in blocks of consecutive coordinates (needs R from
 // launch_gram); cd_blk_ok tells whether this build covers the shape.
+// ---- learned working-set proposer
+constexpr int MLP_IN = 5, MLP_HIDDEN = 64;
+constexpr int MLP_NPARAM = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN + 1;
+cudaError_t launch_mlp_forward(const float *w, const float *F, int64_t N, float *logit, int num_sms, cudaStream_t st);
+size_t mlp_grad_smem();
+cudaError_t launch_mlp_grad(const float *w, const float *F, const uint8_t *y, const int32_t *order, int64_t s0,
+                            int64_t s1, float inv_n, float *part, double *loss_part, int nblk, float *grad,
+                            double *loss, cudaStream_t st);
+cudaError_t launch_mlp_adam(float *w, const float *g, float *m, float *v, float lr, float b1, float b2, float eps,
+                            float c1, float c2, cudaStream_t st);
+cudaError_t launch_propose(int64_t p, const uint8_t *keep, const uint8_t *safe, const void *beta_prev, int beta_f64,
+                           const float *z1, const float *z2, const float *z3, double lam, double lam1, double lam2,
+                           double alpha, const float *w, float logit_tau, uint8_t *strong, float *feat, int32_t *fidx,
+                           int64_t cap, unsigned long long *pos, unsigned long long *n_prop, int num_sms,
+                           cudaStream_t st);
+cudaError_t launch_label(const int32_t *fidx, int64_t q0, int64_t q1, const void *beta, int beta_f64, uint8_t *label,
+                         cudaStream_t st);
+
 // ---- batched path (m responses x (nfolds + 1) fits of one design)
 constexpr int BATCH_MAX_FOLDS = 31;
 constexpr int BATCH_MAX_PROBLEMS = 256;

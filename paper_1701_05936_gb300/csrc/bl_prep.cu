@@ -431,6 +431,8 @@ __global__ void __launch_bounds__(256) k_screen(ScreenArgs a, DevScalars *sc)
             sf = s_now;
             if (a.rule == 0)
                 sg = (b != 0.0);
+            else if (a.strong_prev_only)
+                sg = s_now && (b != 0.0);
             else
                 sg = s_now && (b != 0.0 || (double)fabsf(a.z_prev[j]) >= thr);
             sn = s_now || s_next;

@@ -4,6 +4,7 @@ only entry points that fail argument checks on the host before touching CUDA."""
 import ctypes as C
 import os
 import re
+import subprocess
 
 from paper_1701_05936_gb300 import bl, build
 
@@ -40,9 +41,24 @@ def test_host_side_argument_checks_need_no_gpu():
     assert L.bl_last_error(None) == b"null context"
 
 
-def test_struct_layouts_match_the_header():
-    # bl_options: 3 doubles + int64 + 2 int32
-    assert C.sizeof(bl.bl_options) == 40
-    # bl_path: 15 pointer/int64 fields + lambda_max, jstar, ybar
-    assert C.sizeof(bl.bl_path) == 18 * 8
-    assert C.sizeof(bl.bl_timing) == 12 * 8 * 3 + 16
+def test_struct_layouts_match_the_header(tmp_path):
+    # compile the public header with the host C compiler and compare every
+    # field's offset and each struct's size with the ctypes mirror in bl.py
+    structs = {"bl_options": bl.bl_options, "bl_path": bl.bl_path, "bl_timing": bl.bl_timing}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "biglasso_gpu.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f in cls._fields_:
+            lines.append(f'printf("{name} {f[0]} %zu\\n", offsetof({name}, {f[0]}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.check_call(["gcc", "-std=c11", "-I", inc, str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name, cls in structs.items():
+        assert got[(name, "size")] == C.sizeof(cls), name
+        for f in cls._fields_:
+            assert got[(name, f[0])] == getattr(cls, f[0]).offset, (name, f[0])
