@@ -48,7 +48,9 @@ def parse():
     ap.add_argument("--cd-mode", default="blocked", choices=["blocked", "covariance", "residual"],
                     help="coordinate-descent form of the timed (chosen) path")
     ap.add_argument("--no-batched", action="store_true",
-                    help="skip the batched z pass (cross-validation workload) object")
+                    help="skip the batched (cross-validation workload) objects")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-proposer (block-factor workload) object")
     ap.add_argument("--plain-steps", type=int, default=2,
                     help="steps of the plain form (residual-update CD) timed for comparison; 0 = skip")
     return ap.parse_args()
@@ -332,6 +334,52 @@ def batched(local: int, reps: int = 20, plain_rhs: int = 8, path_steps: int = 2)
     return zobj, pobj
 
 
+def learned(local: int):
+    """The learned working-set proposer (BL_SCREEN_LEARNED, trained by
+    paper_1701_05936_gb300.train_proposer) on the block-factor workload at
+    1000 x 1,000,000 FP32 (4 GB, larger than L2), beside the plain form: the
+    same path screened by the strong rule with BEDPP.  Both are exact (the KKT
+    check judges); the object reports each path's time, the working sets it
+    solved over and their coefficient difference."""
+    import torch
+    from paper_1701_05936_gb300 import bl, synth
+    dev = torch.device("cuda", local)
+    here = os.path.join(ROOT, "paper_1701_05936_gb300")
+    meta = json.load(open(os.path.join(here, "proposer_block100.json")))
+    w = bl.mlp_load(os.path.join(here, "proposer_block100.txt")).to(dev)
+    prob = synth.block_factor(replicate=2000)
+    X = torch.from_numpy(prob.X).to(dev)
+    y = torch.from_numpy(prob.y).to(dev)
+    ctx = bl.Context(local)
+    out = {}
+    paths = {}
+    for name, kw in (("plain", dict(screen=bl.BL_SCREEN_SSR_BEDPP)),
+                     ("learned", dict(screen=bl.BL_SCREEN_LEARNED, proposer=w, proposer_tau=meta["tau"]))):
+        base = dict(alpha=prob.alpha, ratio=prob.ratio, nlambda=prob.nlambda, eps=prob.eps, cd_mode=bl.BL_CD_BLOCKED,
+                    **kw)
+        bl.bl_fit_path(ctx, X, prob.n, y, **base)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        r = bl.bl_fit_path(ctx, X, prob.n, y, **base)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        paths[name] = r
+        out[name] = {"ms_per_path": ms, "paths_per_s": 1e3 / ms, "sum_working_set": int(r["n_strong"].sum()),
+                     "kkt_passes": int(r["kkt_rounds"].sum()), "sweeps": int(r["sweeps"].sum()),
+                     "active_at_lambda_min": int(r["n_active"][-1])}
+    diff = float((bl.path_dense(paths["plain"], prob.p) - bl.path_dense(paths["learned"], prob.p)).abs().max())
+    ctx.close()
+    return {"workload": f"blockfactor_{prob.n}x{prob.p}_f32_block100_rho0.6_k40_snr3, {prob.nlambda} lambdas to "
+                        f"{prob.ratio} lambda_max, alpha {prob.alpha}",
+            "proposer": f"5-64-64-1 perceptron, tau {meta['tau']}, trained on {meta['candidates']} candidates of "
+                        f"seeds {meta['train_seeds'][0]}..{meta['train_seeds'][1] - 1} at p = {meta['p']}",
+            "chosen": out["learned"], "plain_form": dict(out["plain"], form="strong rule with BEDPP (SSR-BEDPP)"),
+            "chosen_over_plain": out["plain"]["ms_per_path"] / out["learned"]["ms_per_path"],
+            "max_abs_coef_diff_chosen_vs_plain": diff}
+
+
 def config(prob):
     return {"workload": WORKLOAD_NAME if prob.p == 100_000 else f"ar1_{prob.n}x{prob.p}_f32_small",
             "n": prob.n, "p": prob.p, "ldx": prob.ldx, "nlambda": prob.nlambda, "lambda_min_ratio": prob.ratio,
@@ -483,6 +531,8 @@ def run_ours(args):
     }
     if rank == 0 and not args.no_batched:
         line["batched_zpass"], line["batched_path"] = batched(local)
+    if rank == 0 and not args.no_learned:
+        line["learned"] = learned(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob)
     ctx.close()

@@ -23,6 +23,9 @@ Sec. 4.2 simulated data and Table 2's real-data shapes):
   variance of X beta over sigma^2 equals the SNR.    (1000 x 100,000, FP32)
 * ``genotype``      -- x_ij ~ Binomial(2, MAF_j), MAF_j ~ U[0.05, 0.5], int8;
   k causal effects N(0, 0.3^2); sigma^2 = Var(g)(1-h2)/h2.  (5000 x 500,000)
+* ``block_factor``  -- blocks of 100 columns sharing a factor (correlation 0.6
+  within a block), 40 nonzero beta ~ +-U[0.3,1], SNR 3: the learned proposer's
+  workload.                                               (1000 x 1,000,000, FP32)
 * ``batched_ar1``   -- AR(1) rho=0.3 columns shared by m responses (k nonzero
   N(0,1) effects each, SNR 2) and balanced cross-validation folds: the
   batched z pass of Sec. 3.1.2.         (2000 x 200,000, 16 responses, 10 folds)
@@ -212,6 +215,37 @@ def batched_ar1(n=2000, p=200_000, m=16, nfolds=10, rho=0.3, k=30, snr=2.0,
     return BatchedProblem(name or f"batched_ar1_{n}x{p}_{m}resp_{nfolds}fold", X, Y, fold_id, n, p, ldx, m,
                           nfolds, dtype, betas, alpha, ratio, nlambda, eps,
                           {"rho": rho, "k": k, "snr": snr})
+
+
+def block_factor(n=1000, p=1_000_000, block=100, k=40, lo=0.3, hi=1.0, snr=3.0, dtype="f32", workload=5,
+                 replicate=0, alpha=1.0, ratio=0.02, nlambda=100, eps=1e-7, pad_value=0.0, name=None) -> Problem:
+    """Block-correlated columns: x_ij = sqrt(0.6) f_{i,b} + sqrt(0.4) e_ij for
+    column j in block b = j // block (f, e ~ N(0,1); correlation 0.6 within a
+    block), drawn a few blocks at a time; k nonzero beta ~ U[lo,hi] with random
+    sign at random indices; noise sd from the sample variance of X beta over
+    sigma^2 = SNR."""
+    g = rng_for(workload, replicate)
+    X, ldx = _alloc_x(n, p, dtype, pad_value)
+    a, c = np.sqrt(0.6), np.sqrt(0.4)
+    nb = (p + block - 1) // block
+    per = max(1, (1 << 23) // max(n * block, 1))   # blocks per draw
+    for b0 in range(0, nb, per):
+        b1 = min(nb, b0 + per)
+        j0, j1 = b0 * block, min(p, b1 * block)
+        f = g.standard_normal((b1 - b0, n))
+        e = g.standard_normal((j1 - j0, n))
+        rows = (np.arange(j0, j1) // block) - b0
+        X[j0:j1, :n] = a * f[rows] + c * e
+    beta = np.zeros(p)
+    k = min(k, p)
+    idx = g.choice(p, size=k, replace=False)
+    beta[idx] = np.where(g.random(k) < 0.5, -1.0, 1.0) * g.uniform(lo, hi, size=k)
+    signal = X[idx, :n].astype(np.float64).T @ beta[idx]
+    var_sig = float(np.var(signal))
+    sigma = np.sqrt(var_sig / snr) if var_sig > 0 else 1.0
+    y = signal + sigma * g.standard_normal(n)
+    return Problem(name or f"blockfactor_{n}x{p}_{dtype}", X, y, n, p, ldx, dtype, beta, alpha, ratio, nlambda, eps,
+                   {"block": block, "k": k, "snr": snr, "sigma": sigma})
 
 
 def batched_residuals(bp: BatchedProblem, replicate: int = 0):
