@@ -51,6 +51,7 @@ def parse():
                     help="skip the batched (cross-validation workload) objects")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-proposer (block-factor workload) object")
+    ap.add_argument("--no-many", action="store_true", help="skip the many-problems object")
     ap.add_argument("--plain-steps", type=int, default=2,
                     help="steps of the plain form (residual-update CD) timed for comparison; 0 = skip")
     return ap.parse_args()
@@ -380,6 +381,49 @@ def learned(local: int):
             "max_abs_coef_diff_chosen_vs_plain": diff}
 
 
+def many(local: int, nprob: int = 256, concurrency: int = 16):
+    """Independent problems at once (bl_fit_many): nprob lasso paths with n ~
+    U{100..1000}, p ~ U{1000..10000}, iid N(0,1) FP32, 10 nonzero +-1, unit noise,
+    100 lambdas to 0.05 lambda_max, alpha 1 -- the many-problems workload at a
+    tenth of its sizes so that it is drawn on the host in seconds.  Beside the
+    plain form: the same problems one after another through bl_fit_path."""
+    import numpy as np
+    import torch
+    from paper_1701_05936_gb300 import bl, synth
+    dev = torch.device("cuda", local)
+    rng = np.random.default_rng(20170404)
+    sizes = [(int(rng.integers(100, 1001)), int(rng.integers(1000, 10001))) for _ in range(nprob)]
+    probs = [synth.gaussian_iid(n=n, p=p, k=10, dtype="f32", workload=6, replicate=i, ratio=0.05)
+             for i, (n, p) in enumerate(sizes)]
+    dv = [(torch.from_numpy(q.X).to(dev), q.n, torch.from_numpy(q.y).to(dev)) for q in probs]
+    kw = dict(alpha=1.0, ratio=0.05, nlambda=100, eps=1e-7, cd_mode=bl.BL_CD_BLOCKED)
+    ctx = bl.Context(local)
+    bl.bl_fit_many(ctx, dv[:concurrency], concurrency=concurrency, **kw)   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = bl.bl_fit_many(ctx, dv, concurrency=concurrency, **kw)
+    torch.cuda.synchronize()
+    ms = 1e3 * (time.perf_counter() - t0)
+    ok = sum(r["status"] == bl.BL_OK for r in res)
+    # plain: one after another, on a sample of problems, scaled to all
+    sample = list(range(0, nprob, max(1, nprob // 16)))
+    t0 = time.perf_counter()
+    for i in sample:
+        X, n, y = dv[i]
+        bl.bl_fit_path(ctx, X, n, y, **kw)
+    torch.cuda.synchronize()
+    plain_ms = 1e3 * (time.perf_counter() - t0) * nprob / len(sample)
+    ctx.close()
+    total_bytes = sum(4.0 * n * p for n, p in sizes)
+    return {"workload": f"{nprob} problems, n ~ U{{100..1000}}, p ~ U{{1000..10000}}, iid N(0,1) FP32, 10 nonzero, "
+                        f"100 lambdas to 0.05 lambda_max", "concurrency": concurrency,
+            "value": nprob / (ms / 1e3), "unit": "problems/s", "ms": ms, "problems_ok": ok,
+            "design_bytes": total_bytes,
+            "note": "wall clock around the call (host workers and their streams inside)",
+            "plain_form": {"form": "bl_fit_path one problem after another", "ms_for_all": plain_ms,
+                           "sampled_problems": len(sample), "chosen_over_plain": plain_ms / ms}}
+
+
 def config(prob):
     return {"workload": WORKLOAD_NAME if prob.p == 100_000 else f"ar1_{prob.n}x{prob.p}_f32_small",
             "n": prob.n, "p": prob.p, "ldx": prob.ldx, "nlambda": prob.nlambda, "lambda_min_ratio": prob.ratio,
@@ -533,6 +577,8 @@ def run_ours(args):
         line["batched_zpass"], line["batched_path"] = batched(local)
     if rank == 0 and not args.no_learned:
         line["learned"] = learned(local)
+    if rank == 0 and not args.no_many:
+        line["many"] = many(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob)
     ctx.close()

@@ -392,6 +392,31 @@ int bl_mlp_save(const float *w_host, const char *path);
  * BL_ERR_ARG when the file cannot be opened or its header or length differ. */
 int bl_mlp_load(float *w_host, const char *path);
 
+/* One problem of bl_fit_many: a design, a response and its path outputs. */
+typedef struct {
+    const void *X;          /* device design, as bl_fit_path */
+    int32_t dtype;          /* bl_dtype */
+    int32_t nlambda;        /* K */
+    int64_t n, p, ldx;
+    const double *y;        /* device FP64 [n] */
+    const double *lambdas;  /* host [K], nullable: the grid of bl_fit_path */
+    bl_path *out;           /* host pointer to this problem's outputs (as bl_fit_path) */
+    int32_t status;         /* out: this problem's bl_status */
+    int32_t reserved;
+} bl_problem;
+
+/* Many independent paths at once (the same solver as bl_fit_path for each
+ * problem; problems may differ in n, p and dtype).  `concurrency` host workers
+ * (0: min(nprob, 16), at most 64), each with its own context and non-blocking
+ * CUDA stream on ctx's device and a workspace sized for the largest problem,
+ * take problems from a shared queue, so the paths' kernels overlap on the GPU
+ * (each coordinate descent runs on one SM; z passes interleave).  opt applies to
+ * every problem.  Returns BL_OK when every problem returned BL_OK, else the first
+ * problem's error in queue order (every problem's own status is in its
+ * bl_problem.status; outputs of the problems that succeeded are valid).
+ * BL_ERR_ARG before any launch for NULL pointers or nprob < 1.  Synchronizes. */
+int bl_fit_many(bl_ctx *ctx, bl_problem *probs, int nprob, const bl_options *opt, int concurrency);
+
 /* Largest working set that bl_cd_active_noalloc accepts. */
 #define BL_NOALLOC_MAX_WORK 4096
 

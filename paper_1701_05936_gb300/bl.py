@@ -59,6 +59,12 @@ class bl_path(C.Structure):
                 ("prop_cap", C.c_int64), ("prop_count", C.c_int64)]
 
 
+class bl_problem(C.Structure):
+    _fields_ = [("X", C.c_void_p), ("dtype", C.c_int32), ("nlambda", C.c_int32), ("n", C.c_int64),
+                ("p", C.c_int64), ("ldx", C.c_int64), ("y", C.c_void_p), ("lambdas", C.c_void_p),
+                ("out", C.c_void_p), ("status", C.c_int32), ("reserved", C.c_int32)]
+
+
 class bl_timing(C.Structure):
     _fields_ = [("launches", C.c_int64 * len(KINDS)), ("ms", C.c_double * len(KINDS)),
                 ("bytes", C.c_double * len(KINDS)),
@@ -106,6 +112,7 @@ def lib():
                 "bl_fit_path_batched": [_vp, *X, _vp, _i64, _i64, _vp, _i64, C.POINTER(bl_options), _int,
                                         C.POINTER(bl_path)],
                 "bl_mlp_predict": [_vp, _vp, _vp, _i64, _vp],
+                "bl_fit_many": [_vp, C.POINTER(bl_problem), _int, C.POINTER(bl_options), _int],
                 "bl_mlp_loss_grad": [_vp, _vp, _vp, _vp, _i64, _vp, C.POINTER(_dbl)],
                 "bl_mlp_train": [_vp, _vp, _vp, _i64, _vp, _int, _i64, _dbl, C.c_uint64, C.POINTER(_dbl)],
                 "bl_mlp_save": [_vp, C.c_char_p],
@@ -310,6 +317,57 @@ def bl_fit_path(ctx, X, n, y, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, lambd
     res.update(host)
     res.update(status=st, nnz=path.nnz_needed, lambda_max=path.lambda_max, jstar=path.jstar, ybar=path.ybar,
                prop_count=path.prop_count)
+    return res
+
+
+def bl_fit_many(ctx, problems, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, screen=BL_SCREEN_SSR_BEDPP,
+                cd_mode=BL_CD_RESIDUAL, max_sweeps=100_000, concurrency=0):
+    """Independent paths at once.  problems: a list of (X (p, ldx) device, n, y
+    (n,) FP64 device).  Returns one bl_fit_path-shaped dict per problem, each
+    with its own status."""
+    nprob = len(problems)
+    arr = (bl_problem * nprob)()
+    keep = []
+    res = []
+    o = torch.zeros
+    for i, (X, n, y) in enumerate(problems):
+        dev = X.device
+        p = int(X.shape[0])
+        K = int(nlambda)
+        cap = K * min(p, int(n) + 64)
+        r = {"lambdas": o(K, dtype=torch.float64, device=dev), "col_ptr": o(K + 1, dtype=torch.int64, device=dev),
+             "row_idx": o(max(1, cap), dtype=torch.int32, device=dev),
+             "val": o(max(1, cap), dtype=torch.float64, device=dev),
+             "val_orig": o(max(1, cap), dtype=torch.float64, device=dev),
+             "intercept": o(K, dtype=torch.float64, device=dev), "loss": o(K, dtype=torch.float64, device=dev)}
+        host = {k: o(K, dtype=torch.int64) for k in ("sweeps", "n_safe", "n_strong", "kkt_rounds", "cols_scanned",
+                                                       "n_active")}
+        path = bl_path()
+        for k in ("lambdas", "col_ptr", "row_idx", "val", "val_orig", "intercept", "loss"):
+            setattr(path, k, r[k].data_ptr())
+        for k, t in host.items():
+            setattr(path, k, t.data_ptr())
+        path.nnz_capacity = cap
+        Xp, dt, n_, p_, ldx = design_args(X, n)
+        arr[i].X = Xp
+        arr[i].dtype = dt
+        arr[i].nlambda = K
+        arr[i].n, arr[i].p, arr[i].ldx = n_, p_, ldx
+        arr[i].y = y.data_ptr()
+        arr[i].out = C.cast(C.pointer(path), C.c_void_p)
+        keep.append(path)
+        r.update(host)
+        res.append(r)
+    opt = bl_options(float(alpha), float(eps), float(ratio), int(max_sweeps), int(screen), int(cd_mode))
+    st = lib().bl_fit_many(ctx.h, arr, nprob, C.byref(opt), int(concurrency))
+    if st not in (BL_OK, BL_ERR_NOT_CONVERGED):
+        bad = [i for i in range(nprob) if arr[i].status not in (BL_OK, BL_ERR_NOT_CONVERGED)]
+        if not bad:
+            ctx.check(st)
+    for i in range(nprob):
+        pth = keep[i]
+        res[i].update(status=arr[i].status, nnz=pth.nnz_needed, lambda_max=pth.lambda_max, jstar=pth.jstar,
+                      ybar=pth.ybar)
     return res
 
 

@@ -7,12 +7,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 using namespace bl;
@@ -708,6 +710,82 @@ extern "C" int bl_mlp_load(float *w_host, const char *path)
     }
     std::fclose(f);
     return st;
+}
+
+// ========================================================== many problems
+extern "C" int bl_fit_many(bl_ctx *ctx, bl_problem *probs, int nprob, const bl_options *opt, int concurrency)
+{
+    if (!ctx) return BL_ERR_ARG;
+    if (!probs || !opt || nprob < 1) return fail(ctx, BL_ERR_ARG, "NULL argument or nprob < 1");
+    for (int i = 0; i < nprob; ++i)
+        if (!probs[i].out || !probs[i].X || !probs[i].y || probs[i].nlambda < 1)
+            return fail(ctx, BL_ERR_ARG, "every problem needs X, y, out and nlambda >= 1");
+    if (concurrency <= 0) concurrency = std::min(nprob, 16);
+    concurrency = std::min({concurrency, nprob, 64});
+    ctx->err.clear();
+    CK(cudaSetDevice(ctx->device));
+    int64_t nmax = 1, pmax = 1;
+    bool any_f32 = false, any_f64 = false;
+    for (int i = 0; i < nprob; ++i) {
+        nmax = std::max(nmax, probs[i].n);
+        pmax = std::max(pmax, probs[i].p);
+        any_f64 |= probs[i].dtype == BL_F64;
+        any_f32 |= probs[i].dtype != BL_F64;
+        probs[i].status = BL_OK;
+    }
+    // workers: own context, stream and workspace (sized up front, so no worker
+    // frees device memory while the others run)
+    std::vector<bl_ctx *> wk((size_t)concurrency, nullptr);
+    std::vector<cudaStream_t> ws((size_t)concurrency, nullptr);
+    auto cleanup = [&]() {
+        for (int t = 0; t < concurrency; ++t) {
+            if (wk[(size_t)t]) bl_ctx_destroy(wk[(size_t)t]);
+            if (ws[(size_t)t]) cudaStreamDestroy(ws[(size_t)t]);
+        }
+    };
+    const bool gram = opt->cd_mode == BL_CD_BLOCKED || opt->cd_mode == BL_CD_COVARIANCE;
+    size_t gneed = 0;
+    if (gram) {
+        if (any_f32) gneed = std::max(gneed, (size_t)MAX_WORKING * MAX_WORKING * 4);
+        if (any_f64) gneed = std::max(gneed, (size_t)MAX_WORKING_F64 * MAX_WORKING_F64 * 8);
+    }
+    for (int t = 0; t < concurrency; ++t) {
+        cudaError_t e = cudaStreamCreateWithFlags(&ws[(size_t)t], cudaStreamNonBlocking);
+        int st = (e == cudaSuccess) ? bl_ctx_create(&wk[(size_t)t], ctx->device, ws[(size_t)t]) : BL_ERR_CUDA;
+        if (st == BL_OK) st = ensure_ws(wk[(size_t)t], nmax, pmax);
+        if (st == BL_OK && gneed) {
+            e = cudaMalloc(&wk[(size_t)t]->gram, gneed);
+            if (e == cudaSuccess) wk[(size_t)t]->gram_bytes = gneed;
+            else st = (e == cudaErrorMemoryAllocation) ? BL_ERR_OOM : BL_ERR_CUDA;
+        }
+        if (st != BL_OK) {
+            cleanup();
+            return fail(ctx, st, "could not create the worker contexts");
+        }
+    }
+    std::atomic<int> next{0};
+    auto work = [&](int t) {
+        cudaSetDevice(ctx->device);
+        bl_ctx *c = wk[(size_t)t];
+        for (;;) {
+            const int i = next.fetch_add(1);
+            if (i >= nprob) break;
+            bl_problem &q = probs[i];
+            q.status = bl_fit_path(c, q.X, q.dtype, q.n, q.p, q.ldx, q.y, opt, q.lambdas, q.nlambda, q.out);
+        }
+    };
+    std::vector<std::thread> th;
+    th.reserve((size_t)concurrency);
+    for (int t = 0; t < concurrency; ++t) th.emplace_back(work, t);
+    for (auto &x : th) x.join();
+    for (int t = 0; t < concurrency; ++t) {
+        ctx->kernels += wk[(size_t)t]->kernels;
+        ctx->cd_updates += wk[(size_t)t]->cd_updates;
+    }
+    cleanup();
+    for (int i = 0; i < nprob; ++i)
+        if (probs[i].status != BL_OK) return fail(ctx, probs[i].status, "a problem failed (see bl_problem.status)");
+    return BL_OK;
 }
 
 // ========================================================== batched path
