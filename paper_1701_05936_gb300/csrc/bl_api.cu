@@ -12,9 +12,11 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 using namespace bl;
@@ -711,6 +713,29 @@ extern "C" int bl_mlp_load(float *w_host, const char *path)
     std::fclose(f);
     return st;
 }
+
+// ============================================== shared-memory limits per kernel
+namespace bl {
+cudaError_t allow_smem_raw(const void *kern, size_t need)
+{
+    static std::mutex mu;
+    static std::unordered_map<const void *, int> done;  // kernel -> dynamic limit set
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = done.find(kern);
+    if (it == done.end()) {
+        int dev = 0, mx = 0;
+        cudaFuncAttributes fa{};
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+        const int lim = mx - (int)fa.sharedSizeBytes;
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        if (e != cudaSuccess) return e;
+        it = done.emplace(kern, lim).first;
+    }
+    return need <= (size_t)it->second ? cudaSuccess : cudaErrorInvalidValue;
+}
+}  // namespace bl
 
 // ========================================================== many problems
 extern "C" int bl_fit_many(bl_ctx *ctx, bl_problem *probs, int nprob, const bl_options *opt, int concurrency)

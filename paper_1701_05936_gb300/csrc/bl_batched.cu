@@ -642,7 +642,7 @@ cudaError_t launch_bcd(const float *X, int64_t n, int64_t ldx, int64_t p, int B,
     const int64_t nch = (n + 3) / 4;
 #define BL_BCD(RPT_)                                                                                               \
     do {                                                                                                           \
-        cudaError_t e = cudaFuncSetAttribute(k_bcd<RPT_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        cudaError_t e = allow_smem(k_bcd<RPT_>, smem);                                                  \
         if (e != cudaSuccess) return e;                                                                            \
         k_bcd<RPT_><<<B, 256, smem, st>>>(X, n, ldx, p, F, fold, nfit, c32, is32, idx, w, cap, lds, gref, lam_b, alpha, \
                                           beta, r32, ldr, eps, max_sweeps, time_limit_ns, status, sweeps, updates,  \

@@ -640,7 +640,7 @@ static cudaError_t cd_launch(const T *X, int64_t n, int64_t ldx, const void *cve
         if (S >= 4) {
             const size_t smem_r = ring_off + (size_t)S * stage_bytes + (size_t)S * 8;
             auto kr = k_cd_ring<T, NW, RPT, WIDX>;
-            cudaError_t e = cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
+            cudaError_t e = allow_smem(kr, smem_r);
             if (e != cudaSuccess) return e;
             kr<<<1, 32 * NW, smem_r, st>>>(X, n, ldx, (const A *)cvec, (const A *)isvec, idx, w_host, cap, p,
                                           (const A *)gref, lam, alpha, (R *)beta, (R *)r, eps, max_sweeps, tl, sc, S,
@@ -650,7 +650,7 @@ static cudaError_t cd_launch(const T *X, int64_t n, int64_t ldx, const void *cve
     }
     const size_t smem = meta;
     auto kern = k_cd<T, NW, RPT, D, WIDX>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_smem(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<1, 32 * NW, smem, st>>>(X, n, ldx, (const A *)cvec, (const A *)isvec, idx, w_host, cap, p, (const A *)gref,
                                    lam, alpha, (R *)beta, (R *)r, eps, max_sweeps, tl, sc);

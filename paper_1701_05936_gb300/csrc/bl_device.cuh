@@ -8,6 +8,19 @@
 
 namespace bl {
 
+// Let a kernel take as much dynamic shared memory as the device allows it (the
+// opt-in maximum per block less the kernel's static shared memory).  The limit
+// is a property of the kernel shared by every caller, so it is only ever raised
+// to that one value (never set to a launch's own size): launches of the same
+// kernel on other streams or threads then never meet a lower limit.  The value
+// is looked up once per kernel.  Fails only if `need` exceeds it.
+cudaError_t allow_smem_raw(const void *kern, size_t need);
+template <typename K> inline cudaError_t allow_smem(K kern, size_t need)
+{
+    return allow_smem_raw(reinterpret_cast<const void *>(kern), need);
+}
+
+
 // Element traits.  VEC is the number of stored elements in one 16-byte load;
 // acc is the arithmetic type of the data-parallel passes (FP32 for FP32 and
 // int8 designs, FP64 for FP64 designs); res is the type of the residual and

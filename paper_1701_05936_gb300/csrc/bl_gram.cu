@@ -340,7 +340,7 @@ static cudaError_t cd_gram_t(const void *Rm, int64_t n, const void *isvec, const
     const size_t smem = ring_off + (size_t)S * stage_stride + (size_t)S * 8;
     if (smem > budget + 1024) return cudaErrorInvalidValue;
     auto kern = k_cd_gram<T>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_smem(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<1, 32, smem, st>>>((const A *)Rm, n, (const A *)isvec, idx, w, p, (const A *)gref, lam, alpha, (R *)beta, eps,
                               max_sweeps, tl, sc, S, stage_stride, (uint32_t)ring_off);
@@ -853,7 +853,7 @@ static cudaError_t cd_blk_t(const T *X, int64_t n, int64_t ldx, const void *cvec
     const size_t smem = stage_off + 2 * (size_t)B * col_stride + 16;
     if (smem > 227 * 1024 - 1024) return cudaErrorInvalidValue;  // caller falls back
     auto kern = k_cd_blk<T, RPT, B>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_smem(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<1, 256, smem, st>>>(X, n, ldx, (const A *)cvec, (const A *)isvec, idx, w, p, (const A *)gref,
                                (const A *)Rm, lam, alpha, (R *)beta, (R *)r, eps, max_sweeps, tl, sc, copy_bytes,

@@ -281,7 +281,7 @@ cudaError_t launch_mlp_grad(const float *w, const float *F, const uint8_t *y, co
                             double *loss, cudaStream_t st)
 {
     const size_t smem = mlp_grad_smem();
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_smem(k_mlp_grad, smem);
     if (e != cudaSuccess) return e;
     k_mlp_grad<<<nblk, MLP_CHUNK, smem, st>>>(w, F, y, order, s0, s1, inv_n, part, loss_part);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

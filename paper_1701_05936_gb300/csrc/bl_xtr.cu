@@ -374,7 +374,7 @@ cudaError_t launch_xtr(const float *X, int64_t n, int64_t p, int64_t ldx, const 
     a.sumr = sumr;
     a.Z = Z;
     a.sc = sc;
-    cudaError_t e = cudaFuncSetAttribute(k_xtr_tf32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_smem(k_xtr_tf32, smem);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<int64_t>(a.ntiles, num_sms);
     k_xtr_tf32<<<grid, XT_THREADS, smem, st>>>(mx, mr, a);

@@ -231,12 +231,13 @@ static cudaError_t zpass_reg_t(const ZpassArgs &a, DevScalars *sc, int num_sms, 
     using A = typename elem<T>::acc;
     using R = typename elem<T>::res;
     auto kern = k_zpass_reg<T, RPL>;
-    static int per_sm = 0;  // resident blocks per SM, looked up once per instantiation
-    if (per_sm == 0) {
+    // resident blocks per SM, looked up once per instantiation (the static's
+    // initialization is thread-safe)
+    static const int per_sm = [&]() {
         int v = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, 256, 0) != cudaSuccess || v < 1) v = 1;
-        per_sm = v;
-    }
+        return v;
+    }();
     const A *cv = sizeof(A) == 8 ? (const A *)a.center : (const A *)a.c32;
     const A *iv = sizeof(A) == 8 ? (const A *)a.inv_scale : (const A *)a.is32;
     const A *xv = sizeof(A) == 8 ? (const A *)a.xnorm : (const A *)a.xn32;
@@ -271,7 +272,7 @@ static cudaError_t zpass_t(const ZpassArgs &a, DevScalars *sc, int grid, cudaStr
     const size_t smem = zpass_smem(sizeof(T) == 8 ? 0 : (sizeof(T) == 4 ? 1 : 3), a.n);
     auto kern = k_zpass<T, U>;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = allow_smem(kern, smem);
         if (e != cudaSuccess) return e;
     }
     kern<<<grid, 256, smem, st>>>((const T *)a.X, a.n, a.p, a.ldx, a.center, a.inv_scale, a.xnorm, (const R *)a.r, sc,
@@ -303,7 +304,7 @@ int zpass_grid(int dtype, int64_t n, int num_sms)
     int per_sm = 0;
     cudaError_t e = cudaErrorInvalidValue;
     auto occ = [&](auto kern) {
-        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (smem > 48 * 1024) allow_smem(kern, smem);
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
     };
     switch (dtype) {
