@@ -543,7 +543,9 @@ def run_ours(args):
                  for k, v in tim.items() if isinstance(v, dict)}
     cd = tim["cd"]
     nlam = prob.nlambda - 1  # lambda_max itself needs no descent
-    cd_info = {"bound": "latency (one CTA, sequential coordinates)",
+    pair = mode == bl.BL_CD_BLOCKED and prob.dtype == "f32" and prob.n <= 1024
+    cd_info = {"bound": "latency (sequential coordinates; chain and dots on a 2-SM cluster)" if pair
+               else "latency (one CTA, sequential coordinates)",
                "updates_per_step": tim["cd_updates"] / args.steps,
                "ns_per_update": 1e6 * cd["ms"] / max(1, tim["cd_updates"]),
                "updates_per_s": tim["cd_updates"] / max(1e-9, cd["ms"] / 1e3),
@@ -567,7 +569,8 @@ def run_ours(args):
         "value_excl_init": {"value": value_excl_init, "unit": "paths/s",
                             "excludes": "standardization, lambda_max and BEDPP init (one-time per design)"},
         "gpu_launches": int(tim["kernel_launches"]), "clocks": clk, "cd": cd_info,
-        "chosen_form": {bl.BL_CD_BLOCKED: "residual-update CD in blocks of 16 coordinates",
+        "chosen_form": {bl.BL_CD_BLOCKED: "residual-update CD in blocks of 16 coordinates"
+                        + (", chain and dots on an SM pair (k_cd_pair)" if pair else " (k_cd_blk)"),
                         bl.BL_CD_COVARIANCE: "covariance-form CD",
                         bl.BL_CD_RESIDUAL: "residual-update CD"}[mode],
         "plain_form": plain,

@@ -8,6 +8,9 @@
 
 namespace bl {
 
+// Leading dimension of the working set's correlation matrix (rows of 16 bytes).
+__host__ __device__ __forceinline__ int64_t gram_ld(int64_t w) { return (w + 3) & ~(int64_t)3; }
+
 // Let a kernel take as much dynamic shared memory as the device allows it (the
 // opt-in maximum per block less the kernel's static shared memory).  The limit
 // is a property of the kernel shared by every caller, so it is only ever raised

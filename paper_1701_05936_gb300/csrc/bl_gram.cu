@@ -17,8 +17,6 @@
 
 namespace bl {
 
-__host__ __device__ __forceinline__ int64_t gram_ld(int64_t w) { return (w + 3) & ~(int64_t)3; }
-
 // ------------------------------------------------------------ R = Xt_W'Xt_W/n
 // Persistent tiled kernel: 64 x 64 tiles of R, 256 threads, 4 x 4 outputs per
 // thread, 32-row slabs of the two column blocks staged in shared memory and

@@ -131,6 +131,14 @@ cudaError_t launch_cd_gram(int dtype, const void *Rm, int64_t n, int64_t p, cons
 
 // Residual-form CD in blocks of consecutive coordinates (needs R from
 // launch_gram); cd_blk_ok tells whether this build covers the shape.
+// ---- blocked CD on a pair of SMs (cluster of two CTAs; FP32, n <= 1024)
+size_t cd_pair_smem(int64_t w);
+bool cd_pair_ok(int dtype, int64_t n, int64_t w);
+cudaError_t launch_cd_pair(const float *X, int64_t n, int64_t p, int64_t ldx, const float *cvec, const float *isvec,
+                           const int32_t *idx, int64_t w, const float *gref, const float *Rm, double lam, double alpha,
+                           float *beta, double eps, int64_t max_sweeps, uint64_t time_limit_ns, DevScalars *sc,
+                           float *Xw, float *Xa, int num_sms, cudaStream_t st);
+
 // ---- learned working-set proposer
 constexpr int MLP_IN = 5, MLP_HIDDEN = 64;
 constexpr int MLP_NPARAM = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN + 1;

@@ -270,6 +270,23 @@ def test_fit_path_elastic_net_and_screen_rules_agree(ctx):
     assert np.abs(bl.path_dense(g1, prob.p).cpu().numpy() - bl.path_dense(g2, prob.p).cpu().numpy()).max() <= 2e-6
 
 
+@pytest.mark.parametrize("n,ratio", [(17, 0.5), (1024, 0.05), (1025, 0.05)])
+def test_blocked_form_across_the_sm_pair_limit(ctx, n, ratio):
+    """FP32 blocked CD runs on an SM pair up to n = 1024 rows (each of 512 data
+    threads holds two rows) and in one CTA above; a few rows, the last pair size
+    and the first one-CTA size give the oracle's path, lasso and elastic net
+    (the 17-row case stops at half of lambda_max, where its solution is well
+    conditioned)."""
+    prob = synth.gaussian_ar1(n=n, p=611, k=8, dtype="f32", replicate=40 + n, pad_value=np.nan)
+    X, y = to_dev(prob)
+    for alpha in (1.0, 0.6):
+        o = oracle.fit_path(prob.dense_f64(), prob.y, alpha=alpha, ratio=ratio, nlambda=50, eps=1e-7)
+        g = bl.bl_fit_path(ctx, X, prob.n, y, alpha=alpha, ratio=ratio, nlambda=50, eps=1e-7,
+                           cd_mode=bl.BL_CD_BLOCKED)
+        assert g["status"] == bl.BL_OK
+        compare_paths(prob, g, o, tol_coef(prob))
+
+
 def test_fit_path_user_lambdas_and_fp64_workload(ctx):
     prob = synth.workload(1)
     X, y = to_dev(prob)
