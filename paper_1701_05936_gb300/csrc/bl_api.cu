@@ -63,7 +63,7 @@ struct bl_ctx {
     size_t xtr_bytes = 0;
     void *hist = nullptr;      // learned proposer: z at the three previous lambdas
     size_t hist_bytes = 0;
-    float *packed = nullptr;   // blocked CD on an SM pair: packed working-set and active columns
+    float *packed = nullptr;   // blocked CD on an SM cluster: packed working-set and active columns
     int64_t kernels = 0;
     int64_t cd_updates = 0;
 };
@@ -785,7 +785,7 @@ extern "C" int bl_fit_many(bl_ctx *ctx, bl_problem *probs, int nprob, const bl_o
             if (e == cudaSuccess) wk[(size_t)t]->gram_bytes = gneed;
             else st = (e == cudaErrorMemoryAllocation) ? BL_ERR_OOM : BL_ERR_CUDA;
         }
-        if (st == BL_OK && opt->cd_mode == BL_CD_BLOCKED && any_f32) {  // the SM-pair form's packed columns
+        if (st == BL_OK && opt->cd_mode == BL_CD_BLOCKED && any_f32) {  // the SM-cluster form's packed columns
             e = cudaMalloc(&wk[(size_t)t]->packed, 2 * (size_t)MAX_WORKING * 4096);
             if (e != cudaSuccess) st = (e == cudaErrorMemoryAllocation) ? BL_ERR_OOM : BL_ERR_CUDA;
         }
@@ -1339,13 +1339,14 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
                     LAUNCH(1, launch_gram(dtype, X, n, ldx, cvec, isvec, w.idx, wh, w.sc, ctx->gram, ctx->num_sms, s));
                     LAUNCH(1, launch_cd_gram(dtype, ctx->gram, n, p, isvec, w.idx, wh, w.gref, lam, alpha, w.beta, eps,
                                              opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc, s));
-                } else if (cd_pair_ok(dtype, n, wh)) {  // chain and data on two SMs
+                } else if (cd_clu_ok(dtype, n, wh)) {  // chain on one SM, row halves on two more (bl_clu.cu)
                     if (!ctx->packed) CK(cudaMalloc(&ctx->packed, 2 * (size_t)MAX_WORKING * 4096));
                     LAUNCH(1, launch_gram(dtype, X, n, ldx, cvec, isvec, w.idx, wh, w.sc, ctx->gram, ctx->num_sms, s));
-                    LAUNCH(2, launch_cd_pair((const float *)X, n, p, ldx, (const float *)cvec, (const float *)isvec,
-                                             w.idx, wh, (const float *)w.gref, (const float *)ctx->gram, lam, alpha,
-                                             (float *)w.beta, eps, opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc,
-                                             ctx->packed, ctx->packed + (size_t)MAX_WORKING * 1024, ctx->num_sms, s));
+                    LAUNCH(2, launch_cd_clu((const float *)X, n, p, ldx, (const float *)cvec, (const float *)isvec,
+                                            w.idx, wh, (const float *)w.gref, (const float *)ctx->gram, lam, alpha,
+                                            (float *)w.beta, eps, opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc,
+                                            ctx->packed, ctx->packed + (size_t)MAX_WORKING * 1024,
+                                            (int64_t)MAX_WORKING * 512, ctx->num_sms, s));
                 } else if (cd_blk_fits(dtype, n, wh)) {
                     LAUNCH(1, launch_gram(dtype, X, n, ldx, cvec, isvec, w.idx, wh, w.sc, ctx->gram, ctx->num_sms, s));
                     LAUNCH(1, launch_cd_blk(dtype, X, n, p, ldx, cvec, isvec, w.idx, wh, w.gref, ctx->gram, lam, alpha,

@@ -129,15 +129,14 @@ cudaError_t launch_cd_gram(int dtype, const void *Rm, int64_t n, int64_t p, cons
                            int64_t w, const void *gref, double lam, double alpha, void *beta, double eps,
                            int64_t max_sweeps, uint64_t time_limit_ns, DevScalars *sc, cudaStream_t st);
 
-// Residual-form CD in blocks of consecutive coordinates (needs R from
-// launch_gram); cd_blk_ok tells whether this build covers the shape.
-// ---- blocked CD on a pair of SMs (cluster of two CTAs; FP32, n <= 1024)
-size_t cd_pair_smem(int64_t w);
-bool cd_pair_ok(int dtype, int64_t n, int64_t w);
-cudaError_t launch_cd_pair(const float *X, int64_t n, int64_t p, int64_t ldx, const float *cvec, const float *isvec,
-                           const int32_t *idx, int64_t w, const float *gref, const float *Rm, double lam, double alpha,
-                           float *beta, double eps, int64_t max_sweeps, uint64_t time_limit_ns, DevScalars *sc,
-                           float *Xw, float *Xa, int num_sms, cudaStream_t st);
+// ---- blocked CD on three SMs (two data CTAs of 512 rows, one chain CTA;
+// FP32, n <= 1024); Xw, Xa hold two row halves hstride floats apart
+size_t cd_clu_smem(int64_t w);
+bool cd_clu_ok(int dtype, int64_t n, int64_t w);
+cudaError_t launch_cd_clu(const float *X, int64_t n, int64_t p, int64_t ldx, const float *cvec, const float *isvec,
+                          const int32_t *idx, int64_t w, const float *gref, const float *Rm, double lam, double alpha,
+                          float *beta, double eps, int64_t max_sweeps, uint64_t time_limit_ns, DevScalars *sc,
+                          float *Xw, float *Xa, int64_t hstride, int num_sms, cudaStream_t st);
 
 // ---- learned working-set proposer
 constexpr int MLP_IN = 5, MLP_HIDDEN = 64;
@@ -203,6 +202,8 @@ cudaError_t launch_xtr(const float *X, int64_t n, int64_t p, int64_t ldx, const 
                        const double *center, const double *scale, int64_t ldc, const double *n_fit_dev, int nfit,
                        const int32_t *fit_of, float *cfit, float *insfit, float *sumr, double *rnorm, float *Z,
                        int64_t ldz, DevScalars *sc, int num_sms, cudaStream_t st);
+// Residual-form CD in blocks of consecutive coordinates in one CTA (needs R
+// from launch_gram); cd_blk_ok tells whether this build covers the shape.
 bool cd_blk_ok(int dtype, int64_t n);
 bool cd_blk_fits(int dtype, int64_t n, int64_t w);
 cudaError_t launch_cd_blk(int dtype, const void *X, int64_t n, int64_t p, int64_t ldx, const void *cvec,

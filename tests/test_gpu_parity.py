@@ -271,10 +271,10 @@ def test_fit_path_elastic_net_and_screen_rules_agree(ctx):
 
 
 @pytest.mark.parametrize("n,ratio", [(17, 0.5), (1024, 0.05), (1025, 0.05)])
-def test_blocked_form_across_the_sm_pair_limit(ctx, n, ratio):
-    """FP32 blocked CD runs on an SM pair up to n = 1024 rows (each of 512 data
-    threads holds two rows) and in one CTA above; a few rows, the last pair size
-    and the first one-CTA size give the oracle's path, lasso and elastic net
+def test_blocked_form_across_the_cluster_limit(ctx, n, ratio):
+    """FP32 blocked CD runs on a 3-SM cluster up to n = 1024 rows (two data CTAs
+    of 512 rows) and in one CTA above; a few rows, the last cluster size and the
+    first one-CTA size give the oracle's path, lasso and elastic net
     (the 17-row case stops at half of lambda_max, where its solution is well
     conditioned)."""
     prob = synth.gaussian_ar1(n=n, p=611, k=8, dtype="f32", replicate=40 + n, pad_value=np.nan)
