@@ -49,6 +49,8 @@ def parse():
                     help="coordinate-descent form of the timed (chosen) path")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched (cross-validation workload) objects")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the precision form (BF16 z pass with FP32 recheck) beside the main path")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-proposer (block-factor workload) object")
     ap.add_argument("--no-many", action="store_true", help="skip the many-problems object")
@@ -424,6 +426,38 @@ def many(local: int, nprob: int = 256, concurrency: int = 16):
                            "sampled_problems": len(sample), "chosen_over_plain": plain_ms / ms}}
 
 
+def precision_form(ctx, X, y, prob, kw, res_native, native_zpass_ms, steps: int = 3):
+    """The same path with the precision form of the z pass (BL_XPREC_BF16): a BF16
+    copy of the design, FP32 accumulation, and the columns the rounding bound
+    leaves open recomputed from the FP32 design."""
+    import torch
+    from paper_1701_05936_gb300 import bl
+    kwp = dict(kw, xprec=bl.BL_XPREC_BF16)
+    res = bl.bl_fit_path(ctx, X, prob.n, y, **kwp)
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(steps):
+        res = bl.bl_fit_path(ctx, X, prob.n, y, **kwp)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    t = ctx.timing()
+    ctx.set_timing(False)
+    zp = t["zpass"]
+    peak = measured_peaks()[0].get("hbm_gbs")
+    gbs = zp["bytes"] / (zp["ms"] / 1e3) / 1e9 if zp["ms"] > 0 else None
+    diff = (bl.path_dense(res, prob.p) - bl.path_dense(res_native, prob.p)).abs().max().item()
+    return {"form": "BF16 copy of X read by the z pass, FP32 accumulation, open columns recomputed from FP32",
+            "value": steps / (ms / 1e3), "unit": "paths/s", "ms_per_path": ms / steps,
+            "zpass_ms_per_path": zp["ms"] / steps, "native_zpass_ms_per_path": native_zpass_ms,
+            "zpass_achieved_gbs": gbs, "zpass_frac_of_measured_hbm": (gbs / peak) if (gbs and peak) else None,
+            "recheck_cols_per_path": t["recheck_cols"] / steps,
+            "cols_scanned_per_path": float(res["cols_scanned"].sum()),
+            "max_abs_coef_diff_vs_native": diff, "status": res["status"]}
+
+
 def config(prob):
     return {"workload": WORKLOAD_NAME if prob.p == 100_000 else f"ar1_{prob.n}x{prob.p}_f32_small",
             "n": prob.n, "p": prob.p, "ldx": prob.ldx, "nlambda": prob.nlambda, "lambda_min_ratio": prob.ratio,
@@ -576,6 +610,8 @@ def run_ours(args):
         "plain_form": plain,
         "kernel_ms_per_step": breakdown, "status": res["status"],
     }
+    if rank == 0 and not args.no_precision and prob.dtype == "f32" and prob.n <= 1024:
+        line["precision_form"] = precision_form(ctx, X, y, prob, kw, res, tim["zpass"]["ms"] / args.steps)
     if rank == 0 and not args.no_batched:
         line["batched_zpass"], line["batched_path"] = batched(local)
     if rank == 0 and not args.no_learned:

@@ -78,6 +78,20 @@ typedef enum {
                                 judges, so the path stays exact */
 } bl_screen_rule;
 
+typedef enum {
+    BL_XPREC_NATIVE = 0, /* the z pass reads the design as given */
+    BL_XPREC_BF16 = 1    /* the precision form of the z pass (FP32 designs with
+                            n <= 1024): it reads a BF16 copy of X, made once per
+                            path (2 bytes per element instead of 4), with FP32
+                            accumulation.  The per-column bound
+                            |z_bf16 - z| <= (2^-8 + (1 + 2^-8) gamma_m) ||x_j|| ||r|| / (n s_j)
+                            + 8u terms decides the KKT test of Sec. 2.2 where it
+                            can; the columns within the bound of lambda alpha are
+                            recomputed from the FP32 design, so the path is the one
+                            BL_XPREC_NATIVE gives.  The strong rule (Sec. 2.2) at
+                            the next lambda uses the BF16 z. */
+} bl_xprec;
+
 typedef struct bl_ctx bl_ctx;
 
 /* Largest working set (features entering coordinate descent at one lambda)
@@ -96,6 +110,10 @@ typedef struct {
     const float *proposer;   /* device [BL_MLP_NPARAM] perceptron parameters for
                                 BL_SCREEN_LEARNED (NULL otherwise) */
     double proposer_tau;     /* proposal threshold on the predicted probability, in (0, 1) */
+    int32_t xprec;           /* bl_xprec: the design precision the z pass reads
+                                (bl_fit_path and bl_fit_many; ignored by
+                                bl_fit_path_batched) */
+    int32_t reserved;        /* 0 */
 } bl_options;
 
 /* Outputs of bl_fit_path.  Pointers marked device are caller-allocated device
@@ -150,6 +168,8 @@ typedef struct {
                                         created or timing was last enabled
                                         (counted whether or not timing is on) */
     int64_t cd_updates;              /* coordinate updates run by CD, same span */
+    int64_t recheck_cols;            /* BL_XPREC_BF16: columns recomputed from the FP32
+                                        design (counted while timing is on) */
 } bl_timing;
 
 /* ---------------------------------------------------------------- context -- */
@@ -241,6 +261,22 @@ int bl_kkt_check(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, in
                  const uint8_t *keep, const void *r, double lam, double alpha,
                  const uint8_t *scan, const uint8_t *safe, uint8_t *working, float *z,
                  int64_t *n_viol);
+
+/* The precision form of bl_kkt_check (BL_XPREC_BF16 of bl_fit_path) for an
+ * FP32 design with n <= 1024: X is copied to BF16 (rounded to nearest even, in
+ * the ctx's workspace), the pass reads the copy with FP32 accumulation, and the
+ * per-column bound
+ *   |z_bf16 - z| <= (2^-8 + (1 + 2^-8) gamma_m) ||x_j|| ||r|| / (n s_j) + 8u terms
+ * decides the KKT test of Sec. 2.2 where it can: a violator when |z| exceeds
+ * lam*alpha by more than the bound, cleared when it falls short by more.  The
+ * columns in between are recomputed from X in FP32 and take bl_kkt_check's
+ * one-sided test; their z entries hold the FP32 values.  *n_recheck (host,
+ * nullable) = the columns recomputed.  Arguments and errors as bl_kkt_check;
+ * BL_ERR_UNSUPPORTED for n > 1024. */
+int bl_kkt_check_bf16(bl_ctx *ctx, const float *X, int64_t n, int64_t p, int64_t ldx, const double *center,
+                      const double *scale, const double *xnorm, const uint8_t *keep, const float *r, double lam,
+                      double alpha, const uint8_t *scan, const uint8_t *safe, uint8_t *working, float *z,
+                      int64_t *n_viol, int64_t *n_recheck);
 
 /* Cyclic coordinate descent at one lambda over the working set (Sec. 1 and
  * Sec. 3.1.1: pathwise CD with residual updates and active-set cycling):

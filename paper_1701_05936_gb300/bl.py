@@ -28,6 +28,7 @@ BL_F64, BL_F32, BL_BF16, BL_I8 = 0, 1, 2, 3
 BL_SCREEN_NONE, BL_SCREEN_SSR, BL_SCREEN_SSR_BEDPP, BL_SCREEN_LEARNED = 0, 1, 2, 3
 BL_MLP_NPARAM = 4609
 BL_CD_RESIDUAL, BL_CD_COVARIANCE, BL_CD_BLOCKED = 0, 1, 2
+BL_XPREC_NATIVE, BL_XPREC_BF16 = 0, 1
 KINDS = ["standardize", "lambda_max", "bedpp_init", "screen", "compact", "cd", "residual", "zpass", "record",
          "gref", "xtr", "kkt"]
 
@@ -45,7 +46,8 @@ class BLError(RuntimeError):
 class bl_options(C.Structure):
     _fields_ = [("alpha", C.c_double), ("eps", C.c_double), ("lambda_min_ratio", C.c_double),
                 ("max_sweeps", C.c_int64), ("screen", C.c_int32), ("cd_mode", C.c_int32),
-                ("proposer", C.c_void_p), ("proposer_tau", C.c_double)]
+                ("proposer", C.c_void_p), ("proposer_tau", C.c_double), ("xprec", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class bl_path(C.Structure):
@@ -68,7 +70,7 @@ class bl_problem(C.Structure):
 class bl_timing(C.Structure):
     _fields_ = [("launches", C.c_int64 * len(KINDS)), ("ms", C.c_double * len(KINDS)),
                 ("bytes", C.c_double * len(KINDS)),
-                ("kernel_launches", C.c_int64), ("cd_updates", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("cd_updates", C.c_int64), ("recheck_cols", C.c_int64)]
 
 
 _lib = None
@@ -101,6 +103,8 @@ def lib():
                               _vp, _vp, C.POINTER(_i64), C.POINTER(_i64)],
                 "bl_kkt_check": [_vp, *X, _vp, _vp, _vp, _vp, _vp, _dbl, _dbl, _vp, _vp, _vp, _vp,
                                  C.POINTER(_i64)],
+                "bl_kkt_check_bf16": [_vp, _vp, _i64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _dbl, _dbl, _vp, _vp,
+                                      _vp, _vp, C.POINTER(_i64), C.POINTER(_i64)],
                 "bl_cd_active": [_vp, *X, _vp, _vp, _vp, _i64, _dbl, _dbl, _vp, _vp, _dbl, _i64,
                                  C.POINTER(_i64)],
                 "bl_fit_path": [_vp, *X, _vp, C.POINTER(bl_options), C.POINTER(_dbl), _int,
@@ -181,6 +185,7 @@ class Context:
                for i, k in enumerate(KINDS)}
         out["kernel_launches"] = int(t.kernel_launches)
         out["cd_updates"] = int(t.cd_updates)
+        out["recheck_cols"] = int(t.recheck_cols)
         return out
 
 
@@ -229,6 +234,18 @@ def bl_kkt_check(ctx, X, n, center, scale, xnorm, keep, r, lam, alpha, scan, saf
     return nv.value
 
 
+def bl_kkt_check_bf16(ctx, X, n, center, scale, xnorm, keep, r, lam, alpha, scan, safe, working, z):
+    """The precision form of bl_kkt_check; returns (violators, columns rechecked in FP32)."""
+    if X.dtype != torch.float32:
+        raise BLError(BL_ERR_ARG, "bl_kkt_check_bf16 takes an FP32 design")
+    nv, nr = C.c_int64(), C.c_int64()
+    ctx.check(lib().bl_kkt_check_bf16(ctx.h, C.c_void_p(X.data_ptr()), int(n), int(X.shape[0]), int(X.stride(0)),
+                                      _ptr(center), _ptr(scale), _ptr(xnorm), _ptr(keep), _ptr(r), float(lam),
+                                      float(alpha), _ptr(scan), _ptr(safe), _ptr(working), _ptr(z), C.byref(nv),
+                                      C.byref(nr)))
+    return nv.value, nr.value
+
+
 def bl_cd_active(ctx, X, n, center, scale, work_idx, lam, alpha, beta, r, eps, max_sweeps=100_000):
     sw = C.c_int64()
     st = lib().bl_cd_active(ctx.h, *design_args(X, n), _ptr(center), _ptr(scale), _ptr(work_idx),
@@ -269,7 +286,7 @@ def bl_cd_active_noalloc(device, stream, X, n, center, scale, work_idx, lam, alp
 
 def bl_fit_path(ctx, X, n, y, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, lambdas=None,
                 screen=BL_SCREEN_SSR_BEDPP, max_sweeps=100_000, nnz_capacity=None, cd_mode=BL_CD_RESIDUAL,
-                proposer=None, proposer_tau=0.5, capture=0):
+                proposer=None, proposer_tau=0.5, capture=0, xprec=BL_XPREC_NATIVE):
     """The whole path on the GPU.  X (p, ldx) and y (n, float64) on the ctx's
     device.  Returns a dict of device tensors (lambdas, col_ptr, row_idx, val,
     val_orig, intercept, loss) and host tensors (per-lambda counters).
@@ -308,7 +325,7 @@ def bl_fit_path(ctx, X, n, y, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, lambd
         path.prop_label = res["prop_label"].data_ptr()
         path.prop_cap = int(capture)
     opt = bl_options(float(alpha), float(eps), float(ratio), int(max_sweeps), int(screen), int(cd_mode),
-                     None if proposer is None else proposer.data_ptr(), float(proposer_tau))
+                     None if proposer is None else proposer.data_ptr(), float(proposer_tau), int(xprec))
     lam_arr = None
     if lambdas is not None:
         lam_arr = (C.c_double * K)(*[float(v) for v in lambdas])

@@ -64,6 +64,11 @@ struct bl_ctx {
     void *hist = nullptr;      // learned proposer: z at the three previous lambdas
     size_t hist_bytes = 0;
     float *packed = nullptr;   // blocked CD on an SM cluster: packed working-set and active columns
+    uint16_t *xbf = nullptr;   // precision form: the BF16 copy of the design, and the recheck list
+    size_t xbf_bytes = 0;
+    int32_t *rlist = nullptr;
+    size_t rlist_bytes = 0;
+    int64_t recheck_cols = 0;
     int64_t kernels = 0;
     int64_t cd_updates = 0;
 };
@@ -239,8 +244,8 @@ int reset_counters(bl_ctx *ctx)
 
 int reset_round(bl_ctx *ctx)
 {
-    const size_t off = offsetof(DevScalars, n_viol);
-    CK(cudaMemsetAsync((char *)ctx->ws.sc + off, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    const size_t off = offsetof(DevScalars, n_viol);  // n_viol, n_cols, n_recheck
+    CK(cudaMemsetAsync((char *)ctx->ws.sc + off, 0, 3 * sizeof(unsigned long long), ctx->stream));
     return BL_OK;
 }
 
@@ -288,6 +293,8 @@ extern "C" int bl_ctx_destroy(bl_ctx *ctx)
     if (ctx->xtr) cudaFree(ctx->xtr);
     if (ctx->hist) cudaFree(ctx->hist);
     if (ctx->packed) cudaFree(ctx->packed);
+    if (ctx->xbf) cudaFree(ctx->xbf);
+    if (ctx->rlist) cudaFree(ctx->rlist);
     if (ctx->sc_host) cudaFreeHost(ctx->sc_host);
     delete ctx;
     return BL_OK;
@@ -311,6 +318,7 @@ extern "C" int bl_ctx_set_timing(bl_ctx *ctx, int enable)
     ctx->totals = bl_timing{};
     ctx->kernels = 0;
     ctx->cd_updates = 0;
+    ctx->recheck_cols = 0;
     return BL_OK;
 }
 
@@ -323,6 +331,7 @@ extern "C" int bl_ctx_get_timing(bl_ctx *ctx, bl_timing *out)
     *out = ctx->totals;
     out->kernel_launches = ctx->kernels;
     out->cd_updates = ctx->cd_updates;
+    out->recheck_cols = ctx->recheck_cols;
     return BL_OK;
 }
 
@@ -454,6 +463,25 @@ extern "C" int bl_screen(bl_ctx *ctx, int64_t n, int64_t p, const double *xty, c
     return BL_OK;
 }
 
+// The precision form's buffers: the BF16 copy of an n x p design and the list
+// of columns its bound leaves open.
+static int ensure_prec(bl_ctx *ctx, int64_t n, int64_t p)
+{
+    const size_t need = (size_t)p * (size_t)bf16_ld(n) * 2, lneed = (size_t)p * 4;
+    if (ctx->xbf_bytes >= need && ctx->rlist_bytes >= lneed) return BL_OK;
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->xbf) cudaFree(ctx->xbf);
+    if (ctx->rlist) cudaFree(ctx->rlist);
+    ctx->xbf = nullptr;
+    ctx->rlist = nullptr;
+    ctx->xbf_bytes = ctx->rlist_bytes = 0;
+    CK(cudaMalloc(&ctx->xbf, need));
+    CK(cudaMalloc(&ctx->rlist, lneed));
+    ctx->xbf_bytes = need;
+    ctx->rlist_bytes = lneed;
+    return BL_OK;
+}
+
 extern "C" int bl_kkt_check(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx,
                             const double *center, const double *scale, const double *xnorm, const uint8_t *keep,
                             const void *r, double lam, double alpha, const uint8_t *scan, const uint8_t *safe,
@@ -482,6 +510,47 @@ extern "C" int bl_kkt_check(bl_ctx *ctx, const void *X, int dtype, int64_t n, in
         if ((st = sync_sc(ctx))) return st;
         if (n_viol) *n_viol = (int64_t)ctx->sc_host->n_viol;
         if (slot >= 0) ctx->launches[slot].bytes = (double)ctx->sc_host->n_cols * n * elem_size(dtype);
+    }
+    return BL_OK;
+}
+
+extern "C" int bl_kkt_check_bf16(bl_ctx *ctx, const float *X, int64_t n, int64_t p, int64_t ldx,
+                                 const double *center, const double *scale, const double *xnorm, const uint8_t *keep,
+                                 const float *r, double lam, double alpha, const uint8_t *scan, const uint8_t *safe,
+                                 uint8_t *working, float *z, int64_t *n_viol, int64_t *n_recheck)
+{
+    int st = check_design(ctx, X, BL_F32, n, p, ldx);
+    if (st) return st;
+    if (!center || !scale || !xnorm || !keep || !r || !scan || !working || !z)
+        return fail(ctx, BL_ERR_ARG, "NULL argument");
+    if (!(lam > 0.0) || !(alpha > 0.0 && alpha <= 1.0)) return fail(ctx, BL_ERR_ARG, "bad lam or alpha");
+    if (!zpass_bf16_ok(n)) return fail(ctx, BL_ERR_UNSUPPORTED, "the BF16 z pass needs n <= 1024");
+    ctx->err.clear();
+    CK(cudaSetDevice(ctx->device));
+    if ((st = ensure_ws(ctx, n, p))) return st;
+    if ((st = ensure_prec(ctx, n, p))) return st;
+    Workspace &w = ctx->ws;
+    LAUNCH(1, launch_rstats(BL_F32, r, n, w.sc, ctx->stream));
+    if ((st = reset_round(ctx))) return st;
+    CK(launch_derive(center, scale, p, w.inv_scale, w.c32, w.is32, ctx->stream, xnorm, w.xn32));
+    ctx->kernels += 1;
+    LAUNCH(1, launch_to_bf16(X, n, p, ldx, ctx->xbf, ctx->num_sms, ctx->stream));
+    ZpassArgs za{ctx->xbf, n, p, bf16_ld(n), center, w.inv_scale, xnorm, w.c32, w.is32, w.xn32, r, lam, alpha, 0.0,
+                 zpass_bf16_gamma(n), scan, safe ? safe : scan, working, z, ctx->rlist};
+    (void)keep;
+    int slot = tbegin(ctx, 7);
+    LAUNCH(2, launch_zpass_bf16(za, X, ldx, gamma_for(BL_F32, n) + 8.0 * std::ldexp(1.0, -24), w.sc, ctx->num_sms,
+                                ctx->stream));
+    tend(ctx, slot, 0.0);
+    if (n_viol || n_recheck || slot >= 0) {
+        if ((st = sync_sc(ctx))) return st;
+        const DevScalars &h = *ctx->sc_host;
+        if (n_viol) *n_viol = (int64_t)h.n_viol;
+        if (n_recheck) *n_recheck = (int64_t)h.n_recheck;
+        if (slot >= 0) {
+            ctx->launches[slot].bytes = (double)h.n_cols * n * 2 + (double)h.n_recheck * n * 4;
+            ctx->recheck_cols += (int64_t)h.n_recheck;
+        }
     }
     return BL_OK;
 }
@@ -1213,6 +1282,19 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
     const double gamma = gamma_for(dtype, n);
     const double gamma_reg = zpass_reg_gamma(dtype, n);
     const int zgrid = zpass_grid(dtype, n, ctx->num_sms);
+    // the precision form: the z pass reads a BF16 copy of the design, made here once
+    if (opt->xprec != BL_XPREC_NATIVE && opt->xprec != BL_XPREC_BF16) return fail(ctx, BL_ERR_ARG, "bad xprec");
+    const bool prec = opt->xprec == BL_XPREC_BF16;
+    if (prec) {
+        if (dtype != BL_F32 || !zpass_bf16_ok(n))
+            return fail(ctx, BL_ERR_UNSUPPORTED, "the BF16 z pass needs an FP32 design with n <= 1024");
+        if ((st = ensure_prec(ctx, n, p))) return st;
+        const int pslot = tbegin(ctx, 0);
+        LAUNCH(1, launch_to_bf16((const float *)X, n, p, ldx, ctx->xbf, ctx->num_sms, s));
+        tend(ctx, pslot, (double)n * p * 4);
+    }
+    const double gamma_bf = prec ? zpass_bf16_gamma(n) : 0.0;
+    const double gamma32 = gamma_for(BL_F32, n) + 8.0 * std::ldexp(1.0, -24);  // the recheck's one-sided test
     const int64_t wcap = max_w_for(dtype);
     bool not_converged = false;
 
@@ -1368,11 +1450,24 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
             ZpassArgs za{X, n, p, ldx, w.center, w.inv_scale, w.xnorm, w.c32, w.is32, w.xn32, w.r, lam, alpha,
                          gamma, gamma_reg, w.scan, w.safe, w.working, w.z};
             int zslot = tbegin(ctx, 7);
-            LAUNCH(1, launch_zpass(dtype, za, w.sc, zgrid, s));
+            if (prec) {
+                ZpassArgs zb = za;
+                zb.X = ctx->xbf;
+                zb.ldx = bf16_ld(n);
+                zb.gamma_reg = gamma_bf;
+                zb.recheck = ctx->rlist;
+                LAUNCH(2, launch_zpass_bf16(zb, (const float *)X, ldx, gamma32, w.sc, ctx->num_sms, s));
+            } else {
+                LAUNCH(1, launch_zpass(dtype, za, w.sc, zgrid, s));
+            }
             tend(ctx, zslot, 0.0);
             if ((st = sync_sc(ctx))) return st;
             const DevScalars &h = *ctx->sc_host;
-            if (zslot >= 0) ctx->launches[zslot].bytes = (double)h.n_cols * n * es;
+            if (zslot >= 0) {  // the stored elements read: BF16 columns, and the FP32 ones rechecked
+                ctx->launches[zslot].bytes = prec ? (double)h.n_cols * n * 2 + (double)h.n_recheck * n * 4
+                                                  : (double)h.n_cols * n * es;
+                ctx->recheck_cols += (int64_t)h.n_recheck;
+            }
             ++rounds;
             cols += (int64_t)h.n_cols;
             if (h.status & ST_WORKING_TOO_BIG)

@@ -47,6 +47,17 @@ template <> struct elem<int8_t> {
     using vec = int4;
     static constexpr int VEC = 16;
 };
+// BF16 storage of an FP32 design (the precision form of the z pass): the upper
+// 16 bits of the FP32 pattern, rounded to nearest even when the copy is made.
+struct bf16s {
+    uint16_t bits;
+};
+template <> struct elem<bf16s> {
+    using acc = float;
+    using res = float;
+    using vec = uint4;
+    static constexpr int VEC = 8;
+};
 
 // Unpack one 16-byte chunk into VEC values of type A.
 template <typename A> __device__ __forceinline__ void unpack(const float4 &v, A *o)
@@ -56,6 +67,15 @@ template <typename A> __device__ __forceinline__ void unpack(const float4 &v, A 
 template <typename A> __device__ __forceinline__ void unpack(const double2 &v, A *o)
 {
     o[0] = (A)v.x; o[1] = (A)v.y;
+}
+template <typename A> __device__ __forceinline__ void unpack(const uint4 &v, A *o)
+{
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {  // element 2q in the low half of word q
+        o[2 * q] = (A)__uint_as_float(w[q] << 16);
+        o[2 * q + 1] = (A)__uint_as_float(w[q] & 0xffff0000u);
+    }
 }
 template <typename A> __device__ __forceinline__ void unpack(const int4 &v, A *o)
 {
@@ -89,6 +109,13 @@ __device__ __forceinline__ int4 ld_stream(const int4 *p)
 {
     int4 v;
     asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint4 ld_stream(const uint4 *p)
+{
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
                  : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
     return v;
 }

@@ -30,7 +30,9 @@ struct DevScalars {
     double sum_xcs; // sum_i (x_i* - c_*) (BEDPP init)
     long long jstar;
     // per-round counters (reset by the host)
-    unsigned long long n_viol, n_cols, n_safe, n_strong, n_scan, w, sweeps;
+    unsigned long long n_viol, n_cols;
+    unsigned long long n_recheck;   // precision form: columns whose KKT test the BF16 bound left open
+    unsigned long long n_safe, n_strong, n_scan, w, sweeps;
     unsigned long long nnz_total;
     unsigned long long cd_updates;  // coordinate updates run by CD (never reset by rounds)
     unsigned long long prop_pos;    // proposer candidates captured so far in this path
@@ -231,6 +233,7 @@ struct ZpassArgs {
     const uint8_t *scan, *safe;
     uint8_t *working;
     float *z;
+    int32_t *recheck = nullptr;  // precision form: the list of columns the BF16 bound left open
 };
 // Rounding-bound factor of the register-resident z pass (gamma_m + 8u).
 double zpass_reg_gamma(int dtype, int64_t n);
@@ -238,6 +241,17 @@ cudaError_t launch_zpass(int dtype, const ZpassArgs &a, DevScalars *sc, int grid
 int zpass_grid(int dtype, int64_t n, int num_sms);  // resident blocks that fit at once
 size_t zpass_smem(int dtype, int64_t n);
 int zpass_depth(int dtype, int64_t n);  // accumulation depth for the rounding bound
+// ---- precision form of the z pass: a BF16 copy of an FP32 design
+int64_t bf16_ld(int64_t n);        // leading dimension of the copy (n rounded up to 8)
+bool zpass_bf16_ok(int64_t n);     // the register-resident BF16 pass covers n
+double zpass_bf16_gamma(int64_t n);  // rounding-bound factor: BF16 rounding + FP32 accumulation + 8u
+cudaError_t launch_to_bf16(const float *X, int64_t n, int64_t p, int64_t ldx, uint16_t *Xb, int num_sms,
+                           cudaStream_t st);
+// the BF16 pass (a.X the copy, a.ldx its leading dimension, a.gamma_reg from
+// zpass_bf16_gamma, a.recheck a list of p entries) and the FP32 recheck of the
+// columns it leaves open (X32, ldx32 the design; gam32 = gamma_m + 8u of that pass)
+cudaError_t launch_zpass_bf16(const ZpassArgs &a, const float *X32, int64_t ldx32, double gam32, DevScalars *sc,
+                              int num_sms, cudaStream_t st);
 
 struct RecordArgs {
     const int32_t *idx;

@@ -6,8 +6,11 @@
 // flight per lane), multiplies with r staged in shared memory, reduces with
 // warp shuffles, and applies the c/s correction in FP64 in the epilogue.
 // One warp per column; a persistent grid strides over the p columns.
+#include "biglasso_gpu.h"
 #include "bl_device.cuh"
 #include "bl_internal.h"
+
+#include <cuda_bf16.h>
 
 #include <cmath>
 
@@ -102,6 +105,11 @@ __global__ void __launch_bounds__(256)
 // parallel: lane k finishes column jb + k of its 32-column group.  The
 // epilogue is in the design's arithmetic type; its rounding is covered by the
 // bound passed in `gam` (gamma_m plus 8 unit roundoffs) and the 8u terms below.
+// With `recheck` NULL the KKT test is one-sided (anything the bound cannot
+// clear enters the working set); with a list (the precision form, X a BF16
+// copy and `gam` covering its rounding too) a column is a violator when
+// |z| > lam alpha + tau, cleared when |z| <= lam alpha - tau, and appended to
+// the list otherwise, for k_zrecheck to decide from the FP32 column.
 template <typename T, int RPL>
 __global__ void __launch_bounds__(256, 2)
     k_zpass_reg(const T *__restrict__ X, int64_t n, int64_t p, int64_t ldx,
@@ -109,7 +117,7 @@ __global__ void __launch_bounds__(256, 2)
                 const typename elem<T>::acc *__restrict__ xnvec, const typename elem<T>::res *__restrict__ r,
                 const DevScalars *__restrict__ sc_in, double lam, double alpha, double gam,
                 const uint8_t *__restrict__ scan, const uint8_t *__restrict__ safe, uint8_t *__restrict__ working,
-                float *__restrict__ z, DevScalars *sc)
+                float *__restrict__ z, DevScalars *sc, int32_t *__restrict__ recheck)
 {
     using E = elem<T>;
     using A = typename E::acc;
@@ -208,9 +216,16 @@ __global__ void __launch_bounds__(256, 2)
             ++cols;
             if (safe[jl] && !working[jl]) {
                 const A tau = g * xnvec[jl] * rnorm * f * (A)1.01 + (A)8 * U * (fabs(c * sum_r) * f + fabs(zj) + thr);
-                if (fabs(zj) > thr - tau) {
+                if (!recheck) {
+                    if (fabs(zj) > thr - tau) {
+                        working[jl] = 1;
+                        ++viol;
+                    }
+                } else if (fabs(zj) > thr + tau) {
                     working[jl] = 1;
                     ++viol;
+                } else if (fabs(zj) > thr - tau) {
+                    recheck[atomicAdd(&sc->n_recheck, 1ull)] = (int32_t)jl;
                 }
             }
         }
@@ -242,7 +257,7 @@ static cudaError_t zpass_reg_t(const ZpassArgs &a, DevScalars *sc, int num_sms, 
     const A *iv = sizeof(A) == 8 ? (const A *)a.inv_scale : (const A *)a.is32;
     const A *xv = sizeof(A) == 8 ? (const A *)a.xnorm : (const A *)a.xn32;
     kern<<<num_sms * per_sm, 256, 0, st>>>((const T *)a.X, a.n, a.p, a.ldx, cv, iv, xv, (const R *)a.r, sc, a.lam,
-                                           a.alpha, a.gamma_reg, a.scan, a.safe, a.working, a.z, sc);
+                                           a.alpha, a.gamma_reg, a.scan, a.safe, a.working, a.z, sc, a.recheck);
     return cudaGetLastError();
 }
 
@@ -345,6 +360,109 @@ cudaError_t launch_zpass(int dtype, const ZpassArgs &a, DevScalars *sc, int grid
     case 3: return zpass_t<int8_t>(a, sc, grid, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+// ------------------------------------------------------- precision form
+// The BF16 copy: Xb[j*ldb + i] = bf16_rn(X[j*ldx + i]) for i < n, 0 up to ldb
+// (a multiple of 8, so that every column starts on 16 bytes).
+__global__ void __launch_bounds__(256) k_to_bf16(const float *__restrict__ X, int64_t n, int64_t p, int64_t ldx,
+                                                 int64_t ldb, uint16_t *__restrict__ Xb)
+{
+    const int64_t total = p * ldb;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = e / ldb, i = e - j * ldb;
+        Xb[e] = (i < n) ? __bfloat16_as_ushort(__float2bfloat16_rn(X[j * ldx + i])) : (uint16_t)0;
+    }
+}
+
+// The columns the BF16 bound left open, decided from the FP32 design: z_j as
+// the FP32 pass computes it (one warp per column, 16-byte loads, one chain per
+// lane, then the warp sum) and its one-sided KKT test with that pass's bound
+// `gam` (gamma_m + 8u).  z[j] gets the FP32 value.
+__global__ void __launch_bounds__(256) k_zrecheck(const float *__restrict__ X, int64_t n, int64_t ldx,
+                                                  const float *__restrict__ cvec, const float *__restrict__ isvec,
+                                                  const float *__restrict__ xnvec, const float *__restrict__ r,
+                                                  const int32_t *__restrict__ list, double lam, double alpha,
+                                                  double gam, uint8_t *__restrict__ working, float *__restrict__ z,
+                                                  DevScalars *sc)
+{
+    constexpr float U = 5.9604644775390625e-08f;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t cnt = (int64_t)sc->n_recheck;
+    const float sum_r = (float)sc->sum_r, rnorm = (float)sc->rnorm;
+    const float thr = (float)(lam * alpha), inv_n = (float)(1.0 / (double)n), g = (float)gam;
+    const int64_t nfull = n / 4;
+    unsigned int viol = 0;
+    for (int64_t q = gw; q < cnt; q += nw) {
+        const int64_t j = list[q];
+        const float *col = X + j * ldx;
+        const float4 *colv = reinterpret_cast<const float4 *>(col);
+        const float4 *rv = reinterpret_cast<const float4 *>(r);
+        float acc = 0.f;
+        for (int64_t c = lane; c < nfull; c += 32) {
+            const float4 x = colv[c], rr = rv[c];
+            acc = fmaf(x.x, rr.x, acc);
+            acc = fmaf(x.y, rr.y, acc);
+            acc = fmaf(x.z, rr.z, acc);
+            acc = fmaf(x.w, rr.w, acc);
+        }
+        if (lane == 0)
+            for (int64_t i = nfull * 4; i < n; ++i) acc = fmaf(col[i], r[i], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            const float c = cvec[j], f = inv_n * isvec[j];
+            const float zj = (acc - c * sum_r) * f;
+            z[j] = zj;
+            const float tau = g * xnvec[j] * rnorm * f * 1.01f + 8.f * U * (fabsf(c * sum_r) * f + fabsf(zj) + thr);
+            if (fabsf(zj) > thr - tau) {
+                working[j] = 1;
+                ++viol;
+            }
+        }
+    }
+    viol = warp_sum(viol);
+    if (lane == 0 && viol) atomicAdd(&sc->n_viol, (unsigned long long)viol);
+}
+
+int64_t bf16_ld(int64_t n) { return (n + 7) & ~(int64_t)7; }
+
+// up to four 16-byte chunks per lane (n <= 1024): the eight-chunk variant spills
+bool zpass_bf16_ok(int64_t n) { return n >= 1 && n <= 32 * 4 * 8; }
+
+double zpass_bf16_gamma(int64_t n)
+{
+    // |fl(sum xb_i r_i) - sum x_i r_i| <= (u_b + (1 + u_b) gamma_m) ||x|| ||r||: the BF16
+    // rounding |xb_i - x_i| <= u_b |x_i| (u_b = 2^-8, round to nearest) plus the FP32
+    // accumulation of the rounded column (Cauchy-Schwarz on both)
+    const double ub = std::ldexp(1.0, -8);
+    return ub + (1.0 + ub) * zpass_reg_gamma(BL_BF16, n);
+}
+
+cudaError_t launch_to_bf16(const float *X, int64_t n, int64_t p, int64_t ldx, uint16_t *Xb, int num_sms,
+                           cudaStream_t st)
+{
+    k_to_bf16<<<num_sms * 8, 256, 0, st>>>(X, n, p, ldx, bf16_ld(n), Xb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zpass_bf16(const ZpassArgs &a, const float *X32, int64_t ldx32, double gam32, DevScalars *sc,
+                              int num_sms, cudaStream_t st)
+{
+    if (!a.recheck || !zpass_bf16_ok(a.n) || !a.c32 || !a.is32 || !a.xn32) return cudaErrorInvalidValue;
+    const int64_t rpl = ((a.n + 7) / 8 + 31) / 32;
+    cudaError_t e;
+    if (rpl <= 1)
+        e = zpass_reg_t<bf16s, 1>(a, sc, num_sms, st);
+    else if (rpl <= 2)
+        e = zpass_reg_t<bf16s, 2>(a, sc, num_sms, st);
+    else
+        e = zpass_reg_t<bf16s, 4>(a, sc, num_sms, st);
+    if (e != cudaSuccess) return e;
+    k_zrecheck<<<num_sms, 256, 0, st>>>(X32, a.n, ldx32, a.c32, a.is32, a.xn32, (const float *)a.r, a.recheck, a.lam,
+                                        a.alpha, gam32, a.working, a.z, sc);
+    return cudaGetLastError();
 }
 
 }  // namespace bl
