@@ -182,6 +182,20 @@ int bl_ctx_create(bl_ctx **ctx, int device, void *stream);
 /* Free the workspace (after synchronizing the stream) and the context. */
 int bl_ctx_destroy(bl_ctx *ctx);
 
+/* Size the ctx's workspace now for designs of up to n rows and p columns of
+ * type dtype, and, when opt is not NULL, the buffers bl_fit_path needs with
+ * those options: the working set's correlation matrix (BL_CD_BLOCKED,
+ * BL_CD_COVARIANCE), the packed columns of the clustered blocked form (FP32,
+ * n <= 1024), the z history of BL_SCREEN_LEARNED and the BF16 copy of
+ * BL_XPREC_BF16.  Later calls within those sizes and options allocate no
+ * device memory (the workspace only grows; bl_ctx_destroy frees it).
+ * Errors: BL_ERR_ARG, BL_ERR_UNSUPPORTED (BF16 designs), BL_ERR_CUDA,
+ * BL_ERR_OOM. */
+int bl_reserve(bl_ctx *ctx, int dtype, int64_t n, int64_t p, const bl_options *opt);
+
+/* Device bytes the ctx holds (workspace and the buffers above). */
+int bl_ctx_workspace_bytes(const bl_ctx *ctx, int64_t *bytes);
+
 /* Replace the stream used by later calls. */
 int bl_ctx_set_stream(bl_ctx *ctx, void *stream);
 

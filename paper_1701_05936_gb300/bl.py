@@ -94,6 +94,8 @@ def lib():
                 "bl_ctx_destroy": [_vp],
                 "bl_ctx_set_stream": [_vp, _vp],
                 "bl_ctx_set_timing": [_vp, _int],
+                "bl_reserve": [_vp, _int, _i64, _i64, C.POINTER(bl_options)],
+                "bl_ctx_workspace_bytes": [_vp, C.POINTER(_i64)],
                 "bl_ctx_get_timing": [_vp, C.POINTER(bl_timing)],
                 "bl_standardize": [_vp, *X, _vp, _vp, _vp, _vp],
                 "bl_lambda_max": [_vp, *X, _vp, _vp, _vp, _vp, _dbl, _vp, _vp, C.POINTER(_dbl),
@@ -177,6 +179,17 @@ class Context:
 
     def set_timing(self, on: bool):
         self.check(lib().bl_ctx_set_timing(self.h, 1 if on else 0))
+
+    def reserve(self, dtype: int, n: int, p: int, cd_mode: int = BL_CD_RESIDUAL, screen: int = BL_SCREEN_SSR_BEDPP,
+                xprec: int = BL_XPREC_NATIVE):
+        """Size the workspace for (n, p) designs and bl_fit_path with these options (bl_reserve)."""
+        opt = bl_options(1.0, 1e-7, 0.1, 100_000, int(screen), int(cd_mode), None, 0.5, int(xprec))
+        self.check(lib().bl_reserve(self.h, int(dtype), int(n), int(p), C.byref(opt)))
+
+    def workspace_bytes(self) -> int:
+        b = C.c_int64()
+        self.check(lib().bl_ctx_workspace_bytes(self.h, C.byref(b)))
+        return b.value
 
     def timing(self) -> dict:
         t = bl_timing()

@@ -64,6 +64,7 @@ struct bl_ctx {
     void *hist = nullptr;      // learned proposer: z at the three previous lambdas
     size_t hist_bytes = 0;
     float *packed = nullptr;   // blocked CD on an SM cluster: packed working-set and active columns
+    size_t packed_bytes = 0;
     uint16_t *xbf = nullptr;   // precision form: the BF16 copy of the design, and the recheck list
     size_t xbf_bytes = 0;
     int32_t *rlist = nullptr;
@@ -297,6 +298,59 @@ extern "C" int bl_ctx_destroy(bl_ctx *ctx)
     if (ctx->rlist) cudaFree(ctx->rlist);
     if (ctx->sc_host) cudaFreeHost(ctx->sc_host);
     delete ctx;
+    return BL_OK;
+}
+
+static int ensure_prec(bl_ctx *ctx, int64_t n, int64_t p);
+
+extern "C" int bl_reserve(bl_ctx *ctx, int dtype, int64_t n, int64_t p, const bl_options *opt)
+{
+    if (!ctx) return BL_ERR_ARG;
+    if (n < 1 || p < 1 || dtype < BL_F64 || dtype > BL_I8) return fail(ctx, BL_ERR_ARG, "bad dtype or shape");
+    if (dtype == BL_BF16) return fail(ctx, BL_ERR_UNSUPPORTED, "BF16 designs are not supported by this build");
+    ctx->err.clear();
+    CK(cudaSetDevice(ctx->device));
+    int st = ensure_ws(ctx, n, p);
+    if (st || !opt) return st;
+    const bool f64 = dtype == BL_F64;
+    if ((opt->cd_mode == BL_CD_BLOCKED && cd_blk_ok(dtype, n)) || opt->cd_mode == BL_CD_COVARIANCE) {
+        const int64_t cap = f64 ? MAX_WORKING_F64 : MAX_WORKING;
+        const size_t need = (size_t)cap * (size_t)cap * (f64 ? 8 : 4);
+        if (ctx->gram_bytes < need) {
+            CK(cudaStreamSynchronize(ctx->stream));
+            if (ctx->gram) cudaFree(ctx->gram);
+            ctx->gram = nullptr;
+            ctx->gram_bytes = 0;
+            CK(cudaMalloc(&ctx->gram, need));
+            ctx->gram_bytes = need;
+        }
+    }
+    if (opt->cd_mode == BL_CD_BLOCKED && dtype == BL_F32 && n <= 1024 && !ctx->packed) {
+        CK(cudaMalloc(&ctx->packed, 2 * (size_t)MAX_WORKING * 4096));
+        ctx->packed_bytes = 2 * (size_t)MAX_WORKING * 4096;
+    }
+    if (opt->screen == BL_SCREEN_LEARNED) {
+        const size_t need = 3 * (size_t)p * sizeof(float);
+        if (ctx->hist_bytes < need) {
+            CK(cudaStreamSynchronize(ctx->stream));
+            if (ctx->hist) cudaFree(ctx->hist);
+            ctx->hist = nullptr;
+            ctx->hist_bytes = 0;
+            CK(cudaMalloc(&ctx->hist, need));
+            ctx->hist_bytes = need;
+        }
+    }
+    if (opt->xprec == BL_XPREC_BF16 && dtype == BL_F32 && zpass_bf16_ok(n)) {
+        if ((st = ensure_prec(ctx, n, p))) return st;
+    }
+    return BL_OK;
+}
+
+extern "C" int bl_ctx_workspace_bytes(const bl_ctx *ctx, int64_t *bytes)
+{
+    if (!ctx || !bytes) return BL_ERR_ARG;
+    *bytes = (int64_t)(ctx->ws.size + ctx->gram_bytes + ctx->packed_bytes + ctx->xtr_bytes + ctx->hist_bytes +
+                       ctx->xbf_bytes + ctx->rlist_bytes);
     return BL_OK;
 }
 
@@ -856,7 +910,8 @@ extern "C" int bl_fit_many(bl_ctx *ctx, bl_problem *probs, int nprob, const bl_o
         }
         if (st == BL_OK && opt->cd_mode == BL_CD_BLOCKED && any_f32) {  // the SM-cluster form's packed columns
             e = cudaMalloc(&wk[(size_t)t]->packed, 2 * (size_t)MAX_WORKING * 4096);
-            if (e != cudaSuccess) st = (e == cudaErrorMemoryAllocation) ? BL_ERR_OOM : BL_ERR_CUDA;
+            if (e == cudaSuccess) wk[(size_t)t]->packed_bytes = 2 * (size_t)MAX_WORKING * 4096;
+            else st = (e == cudaErrorMemoryAllocation) ? BL_ERR_OOM : BL_ERR_CUDA;
         }
         if (st != BL_OK) {
             cleanup();
@@ -1422,7 +1477,10 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
                     LAUNCH(1, launch_cd_gram(dtype, ctx->gram, n, p, isvec, w.idx, wh, w.gref, lam, alpha, w.beta, eps,
                                              opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc, s));
                 } else if (cd_clu_ok(dtype, n, wh)) {  // chain on one SM, row halves on two more (bl_clu.cu)
-                    if (!ctx->packed) CK(cudaMalloc(&ctx->packed, 2 * (size_t)MAX_WORKING * 4096));
+                    if (!ctx->packed) {
+                        CK(cudaMalloc(&ctx->packed, 2 * (size_t)MAX_WORKING * 4096));
+                        ctx->packed_bytes = 2 * (size_t)MAX_WORKING * 4096;
+                    }
                     LAUNCH(1, launch_gram(dtype, X, n, ldx, cvec, isvec, w.idx, wh, w.sc, ctx->gram, ctx->num_sms, s));
                     LAUNCH(2, launch_cd_clu((const float *)X, n, p, ldx, (const float *)cvec, (const float *)isvec,
                                             w.idx, wh, (const float *)w.gref, (const float *)ctx->gram, lam, alpha,
