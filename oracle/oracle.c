@@ -46,7 +46,14 @@
  *     |(lmax+lam) xt_j'yc - (lmax-lam) s* lmax xt_j'xt_*|
  *         < 2 n lam lmax - (lmax-lam) sqrt(n ||yc||^2 - n^2 lmax^2).
  *   x_* itself is never discarded (its left side is identically 2 n lam lmax).
- *   For alpha < 1 no feature is discarded.
+ *   For alpha < 1 (the elastic net of Sec. 1) the same rule is applied to the
+ *   lasso the elastic net is at a fixed lam: design [Xt; sqrt(n lam (1-alpha)) I],
+ *   response [yc; 0], penalty n lam alpha (its lambda_max is the elastic net's,
+ *   max |xt_j'yc| / (n alpha), and x_* is the same).  With q = 1 + lam (1-alpha),
+ *   feature j != * is discarded at lam when
+ *     |(lmax+lam) xt_j'yc - (lmax-lam) (alpha lmax / q) s* xt_j'xt_*|
+ *         < 2 n alpha lam lmax - (lmax-lam) sqrt(n q ||yc||^2 - n^2 alpha^2 lmax^2),
+ *   which is the rule above at alpha = 1 (q = 1), term for term.
  *
  *   Sequential strong rule (Sec. 2.2, Tibshirani et al. 2012): keep j at
  *   lambda_k when |z_j(lambda_{k-1})| >= alpha (2 lambda_k - lambda_{k-1}), or when
@@ -192,28 +199,30 @@ void orc_bedpp_safe(const double *xty, const double *xtxstar, const uint8_t *kee
                     double lmax, i64 jstar, double ynorm2, double lam, double alpha,
                     uint8_t *safe)
 {
-    if (alpha < 1.0 || jstar < 0) {
+    if (jstar < 0) {
         for (i64 j = 0; j < p; ++j) safe[j] = keep[j];
         return;
     }
     double nn = (double)n;
     double sstar = (xty[jstar] >= 0.0) ? 1.0 : -1.0;
-    double rad = nn * ynorm2 - nn * nn * lmax * lmax;
+    double q = 1.0 + lam * (1.0 - alpha);
+    double rad = nn * q * ynorm2 - nn * nn * alpha * alpha * lmax * lmax;
     if (rad < 0.0) rad = 0.0;
-    double rhs = 2.0 * nn * lam * lmax - (lmax - lam) * sqrt(rad);
+    double rhs = 2.0 * nn * alpha * lam * lmax - (lmax - lam) * sqrt(rad);
+    double cstar = alpha * lmax / q;
     for (i64 j = 0; j < p; ++j) {
         if (!keep[j]) {
             safe[j] = 0;
             continue;
         }
         if (j == jstar) {
-            /* For x_* the left side equals 2 n lam lmax identically, which is at
-             * least the right side, so x_* is never discarded; the FP64 values of
+            /* For x_* the left side equals 2 n alpha lam lmax identically, which is
+             * at least the right side, so x_* is never discarded; the FP64 values of
              * the two sides tie at lam = lmax and must not be compared. */
             safe[j] = 1;
             continue;
         }
-        double lhs = fabs((lmax + lam) * xty[j] - (lmax - lam) * sstar * lmax * xtxstar[j]);
+        double lhs = fabs((lmax + lam) * xty[j] - (lmax - lam) * cstar * sstar * xtxstar[j]);
         safe[j] = (uint8_t)!(lhs < rhs);
     }
 }

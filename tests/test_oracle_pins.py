@@ -294,6 +294,90 @@ def test_bedpp_matches_vector_form_edpp():
     assert disagree == 0
 
 
+def edpp_vector_form_en(Xt, yc, lam, n, alpha):
+    """The basic EDPP rule in vector form on the lasso the elastic net is at
+    lam: design Z = [Xt'; sqrt(n lam (1-alpha)) I] (columns z_j), response
+    [yc; 0], penalty n lam alpha, in the 1/2 ||.||^2 scaling."""
+    p = Xt.shape[0]
+    Z = np.vstack([Xt.T, np.sqrt(n * lam * (1 - alpha)) * np.eye(p)])   # (n + p) x p
+    v = np.concatenate([yc, np.zeros(p)])
+    corr = Z.T @ v
+    js = int(np.argmax(np.abs(corr)))
+    mu_max, mu = abs(corr[js]), n * lam * alpha
+    theta0 = v / mu_max
+    v1 = np.sign(corr[js]) * Z[:, js]
+    v2 = v / mu - theta0
+    v2p = v2 - (v1 @ v2) / (v1 @ v1) * v1
+    lhs = np.abs(Z.T @ (theta0 + 0.5 * v2p))
+    rhs = 1.0 - 0.5 * np.linalg.norm(v2p) * np.linalg.norm(Z, axis=0)
+    return lhs < rhs, lhs, rhs
+
+
+def _en_closed_form(xty, xtxs, keep, n, lmax, js, yy, lam, alpha, drop_q=False):
+    """The closed form restated in numpy, with an optional planted mistake:
+    drop_q forgets the ridge part of the augmented columns (q = 1)."""
+    q = 1.0 if drop_q else 1.0 + lam * (1.0 - alpha)
+    sstar = 1.0 if xty[js] >= 0 else -1.0
+    rad = max(n * q * yy - n * n * alpha * alpha * lmax * lmax, 0.0)
+    rhs = 2 * n * alpha * lam * lmax - (lmax - lam) * np.sqrt(rad)
+    lhs = np.abs((lmax + lam) * xty - (lmax - lam) * (alpha * lmax / q) * sstar * xtxs)
+    safe = (~(lhs < rhs)).astype(np.uint8) * keep
+    safe[js] = keep[js]
+    return safe
+
+
+def test_elastic_net_bedpp_matches_vector_form_edpp_on_the_augmented_design():
+    rng = np.random.default_rng(13)
+    disagree = planted = 0
+    for trial in range(24):
+        n, p = int(rng.integers(6, 40)), int(rng.integers(3, 90))
+        X = corr_design(n, p, rng.uniform(0, 0.8), rng) if trial % 2 else rng.standard_normal((p, n))
+        y = X[: min(3, p)].T @ rng.standard_normal(min(3, p)) + rng.standard_normal(n)
+        c, s, keep = oracle.standardize(X)
+        Xt = oracle.standardized_matrix(X, c, s, keep)
+        yc, _ = oracle.center(y)
+        xty = oracle.xtv(Xt, yc)
+        for alpha in (0.3, 0.6, 0.9):
+            lmax, js = oracle.lambda_max(xty, keep, n, alpha)
+            xtxs, yy = oracle.bedpp_init(Xt, js, yc)
+            for frac in (0.99, 0.9, 0.7, 0.5, 0.3, 0.1):
+                lam = lmax * frac
+                safe = oracle.bedpp_safe(xty, xtxs, keep, n, lmax, js, yy, lam, alpha)
+                disc_v, lhs, rhs = edpp_vector_form_en(Xt[keep == 1], yc, lam, n, alpha)
+                clear = np.abs(lhs - rhs) > 1e-9 * np.maximum(1.0, np.abs(rhs))
+                disagree += int(np.sum(((safe[keep == 1] == 0) != disc_v) & clear))
+                # the numpy restatement agrees, and the planted mistake does not
+                assert np.array_equal(_en_closed_form(xty, xtxs, keep, n, lmax, js, yy, lam, alpha), safe)
+                wrong = _en_closed_form(xty, xtxs, keep, n, lmax, js, yy, lam, alpha, drop_q=True)
+                planted += int(np.sum(((wrong[keep == 1] == 0) != disc_v) & clear))
+    assert disagree == 0
+    assert planted > 0
+
+
+def test_elastic_net_bedpp_is_safe_on_random_paths():
+    rng = np.random.default_rng(14)
+    checked = discarded = 0
+    for trial in range(45):
+        n, p = int(rng.integers(8, 50)), int(rng.integers(5, 160))
+        X = corr_design(n, p, [0.0, 0.5, 0.9][trial % 3], rng)
+        b = np.zeros(p)
+        k = min(int(rng.integers(1, 6)), p)
+        b[rng.choice(p, k, replace=False)] = rng.standard_normal(k) * 2
+        y = X.T @ b + rng.uniform(0.1, 2.0) * rng.standard_normal(n)
+        alpha = [0.25, 0.5, 0.8][trial % 3]
+        res = oracle.fit_path(X, y, alpha=alpha, ratio=0.05, nlambda=25, eps=1e-10)
+        Xt = oracle.standardized_matrix(X, res["c"], res["s"], res["keep"])
+        yc, _ = oracle.center(y)
+        xtxs, yy = oracle.bedpp_init(Xt, res["jstar"], yc)
+        for kk, lam in enumerate(res["lambdas"]):
+            safe = oracle.bedpp_safe(res["xty"], xtxs, res["keep"], n, res["lmax"], res["jstar"], yy, lam, alpha)
+            active = res["beta"][kk] != 0
+            assert not np.any(active & (safe == 0)), (trial, kk)
+            discarded += int(res["keep"].sum() - safe.sum())
+            checked += 1
+    assert checked == 45 * 25 and discarded > 0
+
+
 def test_bedpp_is_safe_on_random_paths():
     rng = np.random.default_rng(11)
     checked = 0
@@ -342,8 +426,18 @@ def test_bedpp_power_and_nesting():
         sizes.append(int(safe.sum()))
     assert sizes[0] == 1                  # at lambda_max only x_* survives
     assert sizes[3] < 0.2 * p             # 0.93 lambda_max: most discarded
-    safe_en = oracle.bedpp_safe(xty, xtxs, keep, n, lmax, js, yy, lmax * 0.9, 0.5)
-    assert np.array_equal(safe_en, keep)  # no safe rule for alpha < 1
+    # the elastic net (alpha = 0.5): the rule on its augmented lasso keeps only
+    # x_* near its lambda_max, discards most features at half of it, and its safe
+    # sets nest as lambda decreases
+    lmax_en, js_en = oracle.lambda_max(xty, keep, n, 0.5)
+    assert js_en == js and lmax_en == pytest.approx(2 * lmax)
+    prev = None
+    for frac, lo, hi in ((0.9, 1, 1), (0.75, 1, 1), (0.55, 2, 0.05 * p), (0.4, 2, p)):
+        safe_en = oracle.bedpp_safe(xty, xtxs, keep, n, lmax_en, js, yy, lmax_en * frac, 0.5)
+        assert safe_en[js] == 1 and lo <= safe_en.sum() <= hi, (frac, int(safe_en.sum()))
+        if prev is not None:
+            assert np.all(safe_en >= prev)
+        prev = safe_en
 
 
 def test_strong_rule_definition():
@@ -442,8 +536,9 @@ _MUTATIONS = {
     "wrong_sign_warm_start": ("double zt = acc / (double)n + old;", "double zt = acc / (double)n - old;"),
     "sample_sd_divisor": ("s[j] = varies ? sqrt(ss / (double)n) : 0.0;",
                           "s[j] = varies ? sqrt(ss / (double)(n - 1)) : 0.0;"),
-    "bedpp_sign_flip": ("- (lmax - lam) * sstar * lmax * xtxstar[j]",
-                        "+ (lmax - lam) * sstar * lmax * xtxstar[j]"),
+    "bedpp_sign_flip": ("- (lmax - lam) * cstar * sstar * xtxstar[j]",
+                        "+ (lmax - lam) * cstar * sstar * xtxstar[j]"),
+    "en_bedpp_ridge_dropped": ("double q = 1.0 + lam * (1.0 - alpha);", "double q = 1.0;"),
     "mlp_relu_mask_dropped": ("d2[u] = (a2[u] > 0.0) ? dout * W3[u] : 0.0;", "d2[u] = dout * W3[u];"),
     "mlp_transposed_backprop": ("s2 += W2[u * MLP_H + h] * d2[u];", "s2 += W2[h * MLP_H + u] * d2[u];"),
 }
@@ -467,6 +562,8 @@ def test_planted_mistake_in_oracle_copy_is_caught(name, monkeypatch):
         try:
             if name == "bedpp_sign_flip":
                 test_bedpp_matches_vector_form_edpp()
+            elif name == "en_bedpp_ridge_dropped":
+                test_elastic_net_bedpp_matches_vector_form_edpp_on_the_augmented_design()
             elif name == "sample_sd_divisor":
                 test_standardize_invariants_and_constant_columns()
             elif name.startswith("mlp_"):
