@@ -246,7 +246,8 @@ int bl_bedpp_init(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, i
 /* ------------------------------------------------------------ per lambda -- */
 
 /* Screening at lam (Sec. 2.2).  safe[j] = 1 unless BEDPP (reference point
- * lambda_max, alpha = 1 only; for alpha < 1 every kept feature is safe)
+ * lambda_max; for alpha < 1 the rule of the lasso the elastic net is at lam:
+ * design [Xt; sqrt(n lam (1-alpha)) I], response [yc; 0], penalty n lam alpha)
  * discards j; BEDPP's discard test is tightened by a relative 1e-10 margin so
  * FP64 rounding can never discard a feature the exact test keeps, and x_* is
  * never discarded.  strong[j] = safe[j] && (beta_prev[j] != 0 ||

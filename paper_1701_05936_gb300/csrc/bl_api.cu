@@ -469,7 +469,7 @@ extern "C" int bl_screen(bl_ctx *ctx, int64_t n, int64_t p, const double *xty, c
     if (n < 1 || p < 1 || !xty || !keep || !z_prev || !safe || !strong) return fail(ctx, BL_ERR_ARG, "NULL argument or bad size");
     if (!(lam > 0.0) || !(lam < lam_prev)) return fail(ctx, BL_ERR_ARG, "need 0 < lam < lam_prev");
     if (!(alpha > 0.0 && alpha <= 1.0)) return fail(ctx, BL_ERR_ARG, "alpha must be in (0, 1]");
-    const bool bedpp = alpha >= 1.0 && jstar >= 0;
+    const bool bedpp = jstar >= 0;
     if (bedpp && (!xtxstar || jstar >= p)) return fail(ctx, BL_ERR_ARG, "xtxstar/jstar required for BEDPP");
     ctx->err.clear();
     CK(cudaSetDevice(ctx->device));
@@ -483,8 +483,8 @@ extern "C" int bl_screen(bl_ctx *ctx, int64_t n, int64_t p, const double *xty, c
         CK(cudaStreamSynchronize(ctx->stream));
         sstar = xs >= 0.0 ? 1.0 : -1.0;
     }
-    double rad = (double)n * ynorm2 - (double)n * (double)n * lambda_max * lambda_max;
     ScreenArgs a{};
+    bedpp_consts(n, alpha, lambda_max, ynorm2, lam, &a.cst_now, &a.rhs_now, &a.rmag_now);
     a.n = n;
     a.p = p;
     a.xty = xty;
@@ -492,7 +492,6 @@ extern "C" int bl_screen(bl_ctx *ctx, int64_t n, int64_t p, const double *xty, c
     a.keep = keep;
     a.lmax = lambda_max;
     a.sstar = sstar;
-    a.radius = rad > 0.0 ? std::sqrt(rad) : 0.0;
     a.jstar = jstar;
     a.lam = lam;
     a.lam_prev = lam_prev;
@@ -1297,8 +1296,8 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
     }
     CK(cudaMemcpyAsync(out->lambdas, L.data(), (size_t)K * sizeof(double), cudaMemcpyHostToDevice, s));
 
-    const bool use_bedpp = opt->screen == BL_SCREEN_SSR_BEDPP && alpha >= 1.0 && jstar >= 0 && lmax > 0.0;
-    double sstar = 1.0, radius = 0.0;
+    const bool use_bedpp = opt->screen == BL_SCREEN_SSR_BEDPP && jstar >= 0 && lmax > 0.0;
+    double sstar = 1.0;
     if (use_bedpp) {
         slot = tbegin(ctx, 2);
         LAUNCH(2, launch_xtxstar(dtype, X, n, p, ldx, w.center, w.scale, w.keep, jstar, w.xcs, w.sc, w.xtxstar,
@@ -1308,8 +1307,6 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
         CK(cudaMemcpyAsync(&xs, w.xty + jstar, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         sstar = xs >= 0.0 ? 1.0 : -1.0;
-        const double rad = (double)n * ynorm2 - (double)n * (double)n * lmax * lmax;
-        radius = rad > 0.0 ? std::sqrt(rad) : 0.0;
     }
     // state at lambda_max: b = 0, r = yc, z = xt'yc/n
     LAUNCH(1, launch_init_z(w.xty, w.keep, p, n, w.z, s));
@@ -1415,7 +1412,8 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
         sa.keep = w.keep;
         sa.lmax = lmax;
         sa.sstar = sstar;
-        sa.radius = radius;
+        bedpp_consts(n, alpha, lmax, ynorm2, lam, &sa.cst_now, &sa.rhs_now, &sa.rmag_now);
+        if (lam_next > 0.0) bedpp_consts(n, alpha, lmax, ynorm2, lam_next, &sa.cst_next, &sa.rhs_next, &sa.rmag_next);
         sa.jstar = jstar;
         sa.lam = lam;
         sa.lam_prev = lam_prev;

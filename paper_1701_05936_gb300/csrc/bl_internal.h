@@ -80,7 +80,10 @@ struct ScreenArgs {
     int64_t n, p;
     const double *xty, *xtxstar;
     const uint8_t *keep;
-    double lmax, sstar, radius;  // radius = sqrt(n ||yc||^2 - n^2 lmax^2)
+    double lmax, sstar;
+    // BEDPP constants at lam and at lam_next (bedpp_consts): the coefficient of
+    // s* xt_j'xt_*, the right side, and the magnitude of its two terms
+    double cst_now, rhs_now, rmag_now, cst_next, rhs_next, rmag_next;
     int64_t jstar;
     double lam, lam_prev, lam_next;  // lam_next < 0: no next lambda
     double alpha;
@@ -91,6 +94,14 @@ struct ScreenArgs {
     int beta_f64;
     uint8_t *safe, *strong, *scan;  // scan nullable
 };
+// BEDPP (Sec. 2.2) at lam for the elastic net with mixing alpha, as the lasso
+// it is at a fixed lam (design [Xt; sqrt(n lam (1-alpha)) I], response [yc; 0],
+// penalty n lam alpha), with q = 1 + lam (1-alpha): j != * is discarded when
+//   |(lmax+lam) xt_j'yc - (lmax-lam) cst s* xt_j'xt_*| < rhs,
+//   cst = alpha lmax / q,  rhs = 2 n alpha lam lmax - (lmax-lam) sqrt(n q ||yc||^2 - n^2 alpha^2 lmax^2);
+// at alpha = 1 this is the lasso rule.  rmag = the magnitude of rhs's two terms.
+void bedpp_consts(int64_t n, double alpha, double lmax, double yn2, double lam, double *cst, double *rhs,
+                  double *rmag);
 cudaError_t launch_screen(const ScreenArgs &a, DevScalars *sc, cudaStream_t st);
 
 cudaError_t launch_compact(const uint8_t *mask, int64_t p, int32_t *idx, int64_t cap,

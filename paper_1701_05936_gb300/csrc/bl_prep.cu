@@ -4,6 +4,8 @@
 #include "bl_device.cuh"
 #include "bl_internal.h"
 
+#include <cmath>
+
 #include <cuda_bf16.h>
 
 namespace bl {
@@ -395,21 +397,34 @@ cudaError_t launch_xtxstar(int dtype, const void *X, int64_t n, int64_t p, int64
 
 // ---------------------------------------------------------------- screening
 // BEDPP (Sec. 2.2; the basic EDPP rule with reference point lambda_max, in
-// the 1/(2n) scaling with ||xt_j||^2 = n): j is discarded at lam when
-//   |(lmax+lam) xty_j - (lmax-lam) s* lmax xtxstar_j|
-//        < 2 n lam lmax - (lmax-lam) sqrt(n ||yc||^2 - n^2 lmax^2),
+// the 1/(2n) scaling with ||xt_j||^2 = n, applied for alpha < 1 to the lasso
+// the elastic net is at a fixed lam; the constants come from bedpp_consts):
+// j is discarded at lam when
+//   |(lmax+lam) xty_j - (lmax-lam) cst s* xtxstar_j| < rhs,
 // tightened here by a 1e-10 relative margin so that FP64 rounding of the
 // precomputed inputs can only keep more features.  x_* is never discarded.
-__device__ __forceinline__ bool bedpp_keep(const ScreenArgs &a, int64_t j, double lam)
+__device__ __forceinline__ bool bedpp_keep(const ScreenArgs &a, int64_t j, double lam, double cst, double rhs,
+                                           double rmag)
 {
     if (j == a.jstar) return true;
     const double t1 = (a.lmax + lam) * a.xty[j];
-    const double t2 = (a.lmax - lam) * a.sstar * a.lmax * a.xtxstar[j];
+    const double t2 = (a.lmax - lam) * cst * a.sstar * a.xtxstar[j];
     const double lhs = fabs(t1 - t2);
-    const double r1 = 2.0 * (double)a.n * lam * a.lmax;
-    const double r2 = (a.lmax - lam) * a.radius;
-    const double margin = 1e-10 * (fabs(t1) + fabs(t2) + fabs(r1) + fabs(r2));
-    return !(lhs < (r1 - r2) - margin);
+    const double margin = 1e-10 * (fabs(t1) + fabs(t2) + rmag);
+    return !(lhs < rhs - margin);
+}
+
+void bedpp_consts(int64_t n, double alpha, double lmax, double yn2, double lam, double *cst, double *rhs,
+                  double *rmag)
+{
+    const double nn = (double)n;
+    const double q = 1.0 + lam * (1.0 - alpha);
+    const double rad = nn * q * yn2 - nn * nn * alpha * alpha * lmax * lmax;
+    const double r1 = 2.0 * nn * alpha * lam * lmax;
+    const double r2 = (lmax - lam) * (rad > 0.0 ? std::sqrt(rad) : 0.0);
+    *cst = alpha * lmax / q;
+    *rhs = r1 - r2;
+    *rmag = std::fabs(r1) + std::fabs(r2);
 }
 
 __global__ void __launch_bounds__(256) k_screen(ScreenArgs a, DevScalars *sc)
@@ -418,14 +433,16 @@ __global__ void __launch_bounds__(256) k_screen(ScreenArgs a, DevScalars *sc)
     if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
     __syncthreads();
     unsigned int n_safe = 0, n_strong = 0, n_scan = 0;
-    const bool use_bedpp = (a.rule == 2) && (a.alpha >= 1.0) && (a.jstar >= 0);
+    const bool use_bedpp = (a.rule == 2) && (a.jstar >= 0);
     const double thr = a.alpha * (2.0 * a.lam - a.lam_prev);
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.p;
          j += (int64_t)gridDim.x * blockDim.x) {
         uint8_t sf = 0, sg = 0, sn = 0;
         if (a.keep[j]) {
-            const bool s_now = use_bedpp ? bedpp_keep(a, j, a.lam) : true;
-            const bool s_next = (use_bedpp && a.lam_next > 0.0) ? bedpp_keep(a, j, a.lam_next) : s_now;
+            const bool s_now = use_bedpp ? bedpp_keep(a, j, a.lam, a.cst_now, a.rhs_now, a.rmag_now) : true;
+            const bool s_next = (use_bedpp && a.lam_next > 0.0)
+                                    ? bedpp_keep(a, j, a.lam_next, a.cst_next, a.rhs_next, a.rmag_next)
+                                    : s_now;
             double b = 0.0;
             if (a.beta_prev) b = a.beta_f64 ? ((const double *)a.beta_prev)[j] : (double)((const float *)a.beta_prev)[j];
             sf = s_now;

@@ -117,7 +117,10 @@ def test_lambda_max_and_bedpp_init_match_oracle(ctx, which):
 
 
 # --------------------------------------------------------------- screening
-def test_screen_matches_oracle_and_is_safe(ctx):
+@pytest.mark.parametrize("alpha", [1.0, 0.6])
+def test_screen_matches_oracle_and_is_safe(ctx, alpha):
+    """BEDPP for the lasso and, at alpha < 1, for the lasso the elastic net is at
+    each lambda; the GPU safe set is the oracle's up to the GPU's safety margin."""
     prob = synth.gaussian_iid(n=150, p=3000, k=5, dtype="f64", replicate=7)
     X, y = to_dev(prob)
     p, n = prob.p, prob.n
@@ -125,29 +128,32 @@ def test_screen_matches_oracle_and_is_safe(ctx):
     keep = dev_zeros(p, torch.uint8)
     yc = dev_zeros(n, torch.float64)
     bl.bl_standardize(ctx, X, n, c, s, xn, keep)
-    lm, js, _ = bl.bl_lambda_max(ctx, X, n, c, s, keep, y, 1.0, yc, xty)
+    lm, js, _ = bl.bl_lambda_max(ctx, X, n, c, s, keep, y, alpha, yc, xty)
     yy = bl.bl_bedpp_init(ctx, X, n, c, s, keep, yc, js, xtxs)
-    res = oracle.fit_path(prob.dense_f64(), prob.y, ratio=0.1, nlambda=40, eps=1e-9)
+    res = oracle.fit_path(prob.dense_f64(), prob.y, alpha=alpha, ratio=0.1, nlambda=40, eps=1e-9)
     o = oracle_prep(prob)
     oxtxs, oyy = oracle.bedpp_init(o["Xt"], res["jstar"], o["yc"])
     safe, strong = dev_zeros(p, torch.uint8), dev_zeros(p, torch.uint8)
     rng = np.random.default_rng(0)
+    discarded = 0
     for k in range(1, 40, 3):
         lam, lam_prev = res["lambdas"][k], res["lambdas"][k - 1]
         zprev = (o["Xt"] @ (o["yc"] - o["Xt"].T @ res["beta"][k - 1]) / n).astype(np.float32)
         bprev = res["beta"][k - 1].astype(np.float32)
-        ns, ng = bl.bl_screen(ctx, n, p, xty, xtxs, keep, lm, js, yy, lam, lam_prev, 1.0,
+        ns, ng = bl.bl_screen(ctx, n, p, xty, xtxs, keep, lm, js, yy, lam, lam_prev, alpha,
                               torch.from_numpy(zprev).to(DEV), torch.from_numpy(bprev).to(DEV), safe, strong)
-        osafe = oracle.bedpp_safe(res["xty"], oxtxs, res["keep"], n, res["lmax"], res["jstar"], oyy, lam, 1.0)
+        osafe = oracle.bedpp_safe(res["xty"], oxtxs, res["keep"], n, res["lmax"], res["jstar"], oyy, lam, alpha)
         gsafe = safe.cpu().numpy()
         # the GPU's discard test carries a 1e-10 relative margin: it may keep more, never fewer
         assert np.all(gsafe >= osafe)
         assert np.sum(gsafe != osafe) <= max(1, p // 1000)
         assert not np.any((res["beta"][k] != 0) & (gsafe == 0))       # safety against the oracle path
-        ostrong = oracle.strong(zprev.astype(np.float64), gsafe, bprev.astype(np.float64), lam, lam_prev, 1.0)
+        ostrong = oracle.strong(zprev.astype(np.float64), gsafe, bprev.astype(np.float64), lam, lam_prev, alpha)
         assert np.array_equal(strong.cpu().numpy(), ostrong)
         assert ns == int(gsafe.sum()) and ng == int(ostrong.sum())
         assert np.all(strong.cpu().numpy() <= gsafe)                   # strong subset of safe
+        discarded += int(p - gsafe.sum())
+    assert discarded > 0
     del rng
 
 
