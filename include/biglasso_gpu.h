@@ -65,7 +65,12 @@ typedef enum {
                              the scalar updates in order with the within-block coupling
                              xt_i'xt_k/n (identical iterates in exact arithmetic); FP32
                              and FP64 designs with n <= 2048 (FP32) / 1024 (FP64), else
-                             BL_CD_RESIDUAL is used */
+                             BL_CD_RESIDUAL is used.  FP32 designs with n <= 1024 run
+                             on a cluster of three SMs: two stream the row halves and
+                             form the dots, the third runs the scalar updates, with
+                             the dots of a block taken before the two previous blocks'
+                             updates and those updates added through R (the same
+                             iterates in exact arithmetic) */
 } bl_cd_mode;
 
 typedef enum {
