@@ -66,6 +66,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """The largest per-rank value in the process group (the slowest rank's time
+    sets the whole job's); the value itself with one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: int, ms_max: float) -> float:
+    """Units all ranks processed, divided by the slowest rank's time (weak
+    scaling: every rank fits its own replicate)."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 def make_problem(rank: int, small: bool):
     from paper_1701_05936_gb300 import synth
     if small:
@@ -508,12 +526,8 @@ def run_ours(args):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     tim = ctx.timing()
-    ms_all = ms
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_all = float(t.item())
-    value = world * args.steps / (ms_all / 1e3)
+    ms_all = max_over_ranks(ms, dev)
+    value = whole_job_rate(world, args.steps, ms_all)
 
     # end to end through the public API from pinned host buffers
     Xh = torch.from_numpy(prob.X).pin_memory()
@@ -531,12 +545,8 @@ def run_ours(args):
     f1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    e2e_ms = f0.elapsed_time(f1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * e2e_steps / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1), dev)
+    e2e_value = whole_job_rate(world, e2e_steps, e2e_ms)
 
     # the plain form: the same path with residual-update CD, for comparison
     plain = None
