@@ -119,6 +119,10 @@ typedef struct {
                                 (bl_fit_path and bl_fit_many; ignored by
                                 bl_fit_path_batched) */
     int32_t reserved;        /* 0 */
+    int64_t timeout_ns;      /* wall-clock limit of one CD launch of bl_fit_path /
+                                bl_fit_many (the GPU clock); 0 = 20 s.  On expiry the
+                                kernel stops at the end of a sweep, the call returns
+                                BL_ERR_TIMEOUT and the ctx stays usable */
 } bl_options;
 
 /* Outputs of bl_fit_path.  Pointers marked device are caller-allocated device

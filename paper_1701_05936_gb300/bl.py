@@ -47,7 +47,7 @@ class bl_options(C.Structure):
     _fields_ = [("alpha", C.c_double), ("eps", C.c_double), ("lambda_min_ratio", C.c_double),
                 ("max_sweeps", C.c_int64), ("screen", C.c_int32), ("cd_mode", C.c_int32),
                 ("proposer", C.c_void_p), ("proposer_tau", C.c_double), ("xprec", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("reserved", C.c_int32), ("timeout_ns", C.c_int64)]
 
 
 class bl_path(C.Structure):
@@ -299,7 +299,7 @@ def bl_cd_active_noalloc(device, stream, X, n, center, scale, work_idx, lam, alp
 
 def bl_fit_path(ctx, X, n, y, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, lambdas=None,
                 screen=BL_SCREEN_SSR_BEDPP, max_sweeps=100_000, nnz_capacity=None, cd_mode=BL_CD_RESIDUAL,
-                proposer=None, proposer_tau=0.5, capture=0, xprec=BL_XPREC_NATIVE):
+                proposer=None, proposer_tau=0.5, capture=0, xprec=BL_XPREC_NATIVE, timeout_ns=0):
     """The whole path on the GPU.  X (p, ldx) and y (n, float64) on the ctx's
     device.  Returns a dict of device tensors (lambdas, col_ptr, row_idx, val,
     val_orig, intercept, loss) and host tensors (per-lambda counters).
@@ -338,7 +338,8 @@ def bl_fit_path(ctx, X, n, y, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, lambd
         path.prop_label = res["prop_label"].data_ptr()
         path.prop_cap = int(capture)
     opt = bl_options(float(alpha), float(eps), float(ratio), int(max_sweeps), int(screen), int(cd_mode),
-                     None if proposer is None else proposer.data_ptr(), float(proposer_tau), int(xprec))
+                     None if proposer is None else proposer.data_ptr(), float(proposer_tau), int(xprec), 0,
+                     int(timeout_ns))
     lam_arr = None
     if lambdas is not None:
         lam_arr = (C.c_double * K)(*[float(v) for v in lambdas])

@@ -1345,6 +1345,8 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
         LAUNCH(1, launch_to_bf16((const float *)X, n, p, ldx, ctx->xbf, ctx->num_sms, s));
         tend(ctx, pslot, (double)n * p * 4);
     }
+    if (opt->timeout_ns < 0) return fail(ctx, BL_ERR_ARG, "timeout_ns < 0");
+    const uint64_t tlim = opt->timeout_ns > 0 ? (uint64_t)opt->timeout_ns : CD_TIME_LIMIT_NS;  // per CD launch
     const double gamma_bf = prec ? zpass_bf16_gamma(n) : 0.0;
     const double gamma32 = gamma_for(BL_F32, n) + 8.0 * std::ldexp(1.0, -24);  // the recheck's one-sided test
     const int64_t wcap = max_w_for(dtype);
@@ -1473,7 +1475,7 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
                 if (gram_mode) {
                     LAUNCH(1, launch_gram(dtype, X, n, ldx, cvec, isvec, w.idx, wh, w.sc, ctx->gram, ctx->num_sms, s));
                     LAUNCH(1, launch_cd_gram(dtype, ctx->gram, n, p, isvec, w.idx, wh, w.gref, lam, alpha, w.beta, eps,
-                                             opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc, s));
+                                             opt->max_sweeps, tlim, w.sc, s));
                 } else if (cd_clu_ok(dtype, n, wh)) {  // chain on one SM, row halves on two more (bl_clu.cu)
                     if (!ctx->packed) {
                         CK(cudaMalloc(&ctx->packed, 2 * (size_t)MAX_WORKING * 4096));
@@ -1482,20 +1484,20 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
                     LAUNCH(1, launch_gram(dtype, X, n, ldx, cvec, isvec, w.idx, wh, w.sc, ctx->gram, ctx->num_sms, s));
                     LAUNCH(2, launch_cd_clu((const float *)X, n, p, ldx, (const float *)cvec, (const float *)isvec,
                                             w.idx, wh, (const float *)w.gref, (const float *)ctx->gram, lam, alpha,
-                                            (float *)w.beta, eps, opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc,
+                                            (float *)w.beta, eps, opt->max_sweeps, tlim, w.sc,
                                             ctx->packed, ctx->packed + (size_t)MAX_WORKING * 1024,
                                             (int64_t)MAX_WORKING * 512, ctx->num_sms, s));
                 } else if (cd_blk_fits(dtype, n, wh)) {
                     LAUNCH(1, launch_gram(dtype, X, n, ldx, cvec, isvec, w.idx, wh, w.sc, ctx->gram, ctx->num_sms, s));
                     LAUNCH(1, launch_cd_blk(dtype, X, n, p, ldx, cvec, isvec, w.idx, wh, w.gref, ctx->gram, lam, alpha,
-                                            w.beta, nullptr, eps, opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc, s));
+                                            w.beta, nullptr, eps, opt->max_sweeps, tlim, w.sc, s));
                 } else {  // working set too large for the block stages: coordinate-at-a-time form
                     LAUNCH(1, launch_cd(dtype, X, n, p, ldx, cvec, isvec, w.idx, wh, w.gref, lam, alpha, w.beta, nullptr,
-                                        eps, opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc, s));
+                                        eps, opt->max_sweeps, tlim, w.sc, s));
                 }
             } else {
                 LAUNCH(1, launch_cd(dtype, X, n, p, ldx, cvec, isvec, w.idx, -1, w.gref, lam, alpha, w.beta, nullptr,
-                                    eps, opt->max_sweeps, CD_TIME_LIMIT_NS, w.sc, s));
+                                    eps, opt->max_sweeps, tlim, w.sc, s));
             }
             tend(ctx, slot, 0.0);
             slot = tbegin(ctx, 6);
