@@ -123,6 +123,16 @@ typedef struct {
                                 bl_fit_many (the GPU clock); 0 = 20 s.  On expiry the
                                 kernel stops at the end of a sweep, the call returns
                                 BL_ERR_TIMEOUT and the ctx stays usable */
+    const double *warm_beta; /* device [p] FP64, nullable: resume a path.  The
+                                standardized-scale coefficients (bl_path.val) of
+                                the solution at warm_lambda; the path starts from
+                                them (residual and z recomputed) instead of from 0.
+                                Needs a user lambda sequence below warm_lambda and
+                                lambda_max, and at most BL_MAX_WORKING nonzeros
+                                (bl_fit_path only: BL_ERR_ARG in bl_fit_many,
+                                ignored by bl_fit_path_batched) */
+    double warm_lambda;      /* the lambda warm_beta solves; the strong rule's
+                                previous lambda at lambdas[0] (Sec. 2.2) */
 } bl_options;
 
 /* Outputs of bl_fit_path.  Pointers marked device are caller-allocated device

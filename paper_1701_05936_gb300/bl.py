@@ -47,7 +47,8 @@ class bl_options(C.Structure):
     _fields_ = [("alpha", C.c_double), ("eps", C.c_double), ("lambda_min_ratio", C.c_double),
                 ("max_sweeps", C.c_int64), ("screen", C.c_int32), ("cd_mode", C.c_int32),
                 ("proposer", C.c_void_p), ("proposer_tau", C.c_double), ("xprec", C.c_int32),
-                ("reserved", C.c_int32), ("timeout_ns", C.c_int64)]
+                ("reserved", C.c_int32), ("timeout_ns", C.c_int64), ("warm_beta", C.c_void_p),
+                ("warm_lambda", C.c_double)]
 
 
 class bl_path(C.Structure):
@@ -299,7 +300,8 @@ def bl_cd_active_noalloc(device, stream, X, n, center, scale, work_idx, lam, alp
 
 def bl_fit_path(ctx, X, n, y, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, lambdas=None,
                 screen=BL_SCREEN_SSR_BEDPP, max_sweeps=100_000, nnz_capacity=None, cd_mode=BL_CD_RESIDUAL,
-                proposer=None, proposer_tau=0.5, capture=0, xprec=BL_XPREC_NATIVE, timeout_ns=0):
+                proposer=None, proposer_tau=0.5, capture=0, xprec=BL_XPREC_NATIVE, timeout_ns=0, warm_beta=None,
+                warm_lambda=0.0):
     """The whole path on the GPU.  X (p, ldx) and y (n, float64) on the ctx's
     device.  Returns a dict of device tensors (lambdas, col_ptr, row_idx, val,
     val_orig, intercept, loss) and host tensors (per-lambda counters).
@@ -337,9 +339,12 @@ def bl_fit_path(ctx, X, n, y, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, lambd
         path.prop_idx = res["prop_idx"].data_ptr()
         path.prop_label = res["prop_label"].data_ptr()
         path.prop_cap = int(capture)
+    if warm_beta is not None and (warm_beta.dtype != torch.float64 or warm_beta.numel() != X.shape[0]
+                                  or not warm_beta.is_contiguous() or warm_beta.device != X.device):
+        raise BLError(BL_ERR_ARG, "warm_beta must be a contiguous float64 (p,) tensor on X's device")
     opt = bl_options(float(alpha), float(eps), float(ratio), int(max_sweeps), int(screen), int(cd_mode),
                      None if proposer is None else proposer.data_ptr(), float(proposer_tau), int(xprec), 0,
-                     int(timeout_ns))
+                     int(timeout_ns), None if warm_beta is None else warm_beta.data_ptr(), float(warm_lambda))
     lam_arr = None
     if lambdas is not None:
         lam_arr = (C.c_double * K)(*[float(v) for v in lambdas])

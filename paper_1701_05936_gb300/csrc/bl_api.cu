@@ -866,6 +866,7 @@ extern "C" int bl_fit_many(bl_ctx *ctx, bl_problem *probs, int nprob, const bl_o
 {
     if (!ctx) return BL_ERR_ARG;
     if (!probs || !opt || nprob < 1) return fail(ctx, BL_ERR_ARG, "NULL argument or nprob < 1");
+    if (opt->warm_beta) return fail(ctx, BL_ERR_ARG, "warm_beta resumes one path: use bl_fit_path");
     for (int i = 0; i < nprob; ++i)
         if (!probs[i].out || !probs[i].X || !probs[i].y || probs[i].nlambda < 1)
             return fail(ctx, BL_ERR_ARG, "every problem needs X, y, out and nlambda >= 1");
@@ -1244,6 +1245,9 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
     if (opt->cd_mode < 0 || opt->cd_mode > 2) return fail(ctx, BL_ERR_ARG, "unknown cd_mode");
     if (!lambdas_in && K > 1 && !(opt->lambda_min_ratio > 0.0 && opt->lambda_min_ratio < 1.0))
         return fail(ctx, BL_ERR_ARG, "lambda_min_ratio must be in (0, 1)");
+    const bool warm = opt->warm_beta != nullptr;
+    if (warm && (!lambdas_in || !(opt->warm_lambda > lambdas_in[0])))
+        return fail(ctx, BL_ERR_ARG, "a warm start needs a lambda sequence below warm_lambda");
     if (lambdas_in) {
         for (int k = 0; k < K; ++k) {
             if (!(lambdas_in[k] > 0.0)) return fail(ctx, BL_ERR_ARG, "lambdas must be positive");
@@ -1385,6 +1389,23 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
         CK(cudaMemsetAsync(&w.sc->prop_pos, 0, sizeof(unsigned long long), s));
     }
     out->prop_count = 0;
+    if (warm) {
+        // resume: b = warm_beta, r = yc - Xt b (FP64), z = Xt'r/n over the kept
+        // columns; the first lambda then screens against warm_lambda
+        if (!(L[0] < lmax)) return fail(ctx, BL_ERR_ARG, "a warm start needs lambdas below lambda_max");
+        LAUNCH(1, launch_warm_beta(opt->warm_beta, w.keep, p, w.beta, beta_f64, w.working, s));
+        LAUNCH(1, launch_compact(w.working, p, w.idx, wcap, w.sc, s));
+        LAUNCH(2, launch_residual(dtype, X, n, ldx, w.center, w.inv_scale, w.idx, -1, w.sc, w.beta, w.yc, w.partial,
+                                  w.r, w.r64, w.sc, s));
+        if ((st = reset_round(ctx))) return st;
+        CK(cudaMemsetAsync(w.safe, 0, (size_t)p, s));  // no KKT marks: z only
+        ZpassArgs zw{X, n, p, ldx, w.center, w.inv_scale, w.xnorm, w.c32, w.is32, w.xn32, w.r, opt->warm_lambda, alpha,
+                     gamma, gamma_reg, w.keep, w.safe, w.working, w.z};
+        LAUNCH(1, launch_zpass(dtype, zw, w.sc, zgrid, s));
+        if ((st = sync_sc(ctx))) return st;
+        if (ctx->sc_host->status & ST_WORKING_TOO_BIG)
+            return fail(ctx, BL_ERR_UNSUPPORTED, "warm_beta has more nonzeros than the CD kernel's limit");
+    }
     const float logit_tau = learned ? (float)std::log(opt->proposer_tau / (1.0 - opt->proposer_tau)) : 0.f;
     int hist_k = -1;  // lambda index whose z history is current
     for (int k = 0; k < K; ++k) {
@@ -1403,7 +1424,7 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
             if (out->cols_scanned) out->cols_scanned[k] = 0;
             continue;
         }
-        const double lam_prev = (k == 0) ? lmax : std::fmin(L[k - 1], lmax);
+        const double lam_prev = (k == 0) ? (warm ? std::fmin(opt->warm_lambda, lmax) : lmax) : std::fmin(L[k - 1], lmax);
         const double lam_next = (k + 1 < K) ? L[k + 1] : -1.0;
         if ((st = reset_counters(ctx))) return st;
         ScreenArgs sa{};

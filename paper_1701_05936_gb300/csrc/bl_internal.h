@@ -103,6 +103,10 @@ struct ScreenArgs {
 void bedpp_consts(int64_t n, double alpha, double lmax, double yn2, double lam, double *cst, double *rhs,
                   double *rmag);
 cudaError_t launch_screen(const ScreenArgs &a, DevScalars *sc, cudaStream_t st);
+// resume of a path: beta from the caller's FP64 standardized-scale coefficients
+// (kept columns only), working = its support
+cudaError_t launch_warm_beta(const double *wb, const uint8_t *keep, int64_t p, void *beta, bool beta_f64,
+                             uint8_t *working, cudaStream_t st);
 
 cudaError_t launch_compact(const uint8_t *mask, int64_t p, int32_t *idx, int64_t cap,
                            DevScalars *sc, cudaStream_t st);

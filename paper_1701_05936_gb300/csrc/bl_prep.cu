@@ -546,6 +546,33 @@ __global__ void __launch_bounds__(1024) k_compact(const uint8_t *__restrict__ ma
     }
 }
 
+// Resume of a path: b_j = warm_j on kept columns (0 elsewhere), stored in the
+// path's precision, and working_j = (b_j != 0) for the compaction that follows.
+__global__ void __launch_bounds__(256) k_warm_beta(const double *__restrict__ wb, const uint8_t *__restrict__ keep,
+                                                   int64_t p, void *beta, int beta_f64, uint8_t *__restrict__ working)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p; j += (int64_t)gridDim.x * blockDim.x) {
+        const double v = keep[j] ? wb[j] : 0.0;
+        if (beta_f64) {
+            ((double *)beta)[j] = v;
+            working[j] = v != 0.0;
+        } else {
+            const float f = (float)v;
+            ((float *)beta)[j] = f;
+            working[j] = f != 0.f;
+        }
+    }
+}
+
+cudaError_t launch_warm_beta(const double *wb, const uint8_t *keep, int64_t p, void *beta, bool beta_f64,
+                             uint8_t *working, cudaStream_t st)
+{
+    int64_t blocks = (p + 255) / 256;
+    if (blocks > 2048) blocks = 2048;
+    k_warm_beta<<<(int)blocks, 256, 0, st>>>(wb, keep, p, beta, beta_f64 ? 1 : 0, working);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_compact(const uint8_t *mask, int64_t p, int32_t *idx, int64_t cap, DevScalars *sc,
                            cudaStream_t st)
 {
