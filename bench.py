@@ -620,13 +620,16 @@ def run_ours(args):
         "plain_form": plain,
         "kernel_ms_per_step": breakdown, "status": res["status"],
     }
-    if rank == 0 and not args.no_precision and prob.dtype == "f32" and prob.n <= 1024:
+    # the single-GPU sections beside the main line: at N = 1 only (with more ranks
+    # they would hold every GPU while rank 0 alone runs them)
+    solo = rank == 0 and world == 1
+    if solo and not args.no_precision and prob.dtype == "f32" and prob.n <= 1024:
         line["precision_form"] = precision_form(ctx, X, y, prob, kw, res, tim["zpass"]["ms"] / args.steps)
-    if rank == 0 and not args.no_batched:
+    if solo and not args.no_batched:
         line["batched_zpass"], line["batched_path"] = batched(local)
-    if rank == 0 and not args.no_learned:
+    if solo and not args.no_learned:
         line["learned"] = learned(local)
-    if rank == 0 and not args.no_many:
+    if solo and not args.no_many:
         line["many"] = many(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob)
