@@ -13,9 +13,10 @@ Under torchrun each rank fits its own replicate (a different seed) -- the
 path has no data-path exchange, so scaling is weak and there is no
 collective besides the timing barrier and the max over ranks.
 
-``--impl reference`` times the FP64 oracle on the host cores instead: each
-step runs 10 consecutive lambdas of one warm-started oracle path (ten steps
-make one path); the value is paths/s extrapolated from lambdas done.
+``--impl reference`` times the FP64 oracle on the host cores instead (its
+OpenMP build on every usable core): each step runs 10 consecutive lambdas of
+one warm-started oracle path (ten steps make one path); the value is paths/s
+extrapolated from lambdas done.
 """
 from __future__ import annotations
 
@@ -169,28 +170,70 @@ def zpass_traffic():
     return None
 
 
-def cpu_baseline(prob):
-    """The FP64 oracle as it stands, one full 100-lambda path, single thread."""
+def host_cpu() -> dict:
+    """The host's CPU model and core counts (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu part")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except AttributeError:
+        usable = os.cpu_count()
+    return {"model": model, "nproc": os.cpu_count(), "usable": usable}
+
+
+def _time_oracle_path(prob, threads: int) -> tuple[float, int]:
     import oracle
-    X = prob.dense_f64()
-    t0 = time.perf_counter()
-    runner = oracle.PathRunner(X, prob.y, prob.alpha, prob.ratio, prob.nlambda, prob.eps)
-    while not runner.done:
-        runner.advance(10)
-    dt = time.perf_counter() - t0
-    return {"value": 1.0 / dt, "unit": "paths/s", "cores": 1, "kind": "oracle",
+    used = oracle.set_threads(threads)
+    try:
+        X = prob.dense_f64()
+        t0 = time.perf_counter()
+        runner = oracle.PathRunner(X, prob.y, prob.alpha, prob.ratio, prob.nlambda, prob.eps)
+        while not runner.done:
+            runner.advance(10)
+        return time.perf_counter() - t0, used
+    finally:
+        oracle.set_threads(1)
+
+
+def cpu_baseline(prob):
+    """The FP64 oracle as it stands, one full 100-lambda path: on all host cores
+    (its OpenMP build: the full sweep's gradient and the correlation loops in
+    parallel, bit-identical results) and on one core."""
+    cpu = host_cpu()
+    dt_all, used = _time_oracle_path(prob, cpu["usable"] or 1)
+    dt_one, _ = _time_oracle_path(prob, 1)
+    return {"value": 1.0 / dt_all, "unit": "paths/s", "cores": used, "kind": "oracle",
             "sample": f"one full 100-lambda path of the same {prob.n}x{prob.p} workload (replicate 0), "
-                      f"FP64 oracle, no screening, {dt:.1f} s"}
+                      f"FP64 oracle, no screening, {dt_all:.1f} s on {used} threads",
+            "cpu_model": cpu["model"], "nproc": cpu["nproc"],
+            "single_core": {"value": 1.0 / dt_one, "unit": "paths/s", "cores": 1,
+                            "sample": f"the same path on one thread, {dt_one:.1f} s"}}
 
 
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return 0
-    import oracle  # noqa: F401
+    import oracle as orc
     prob = make_problem(0, args.small)
     X = prob.dense_f64()
-    import oracle as orc
+    cpu = host_cpu()
+    used = orc.set_threads(cpu["usable"] or 1)
 
     def fresh():
         return orc.PathRunner(X, prob.y, prob.alpha, prob.ratio, prob.nlambda, prob.eps)
@@ -206,15 +249,17 @@ def run_reference(args):
             runner = fresh()
         lam_done += runner.advance(10)
     dt = time.perf_counter() - t0
+    orc.set_threads(1)
     value = (lam_done / prob.nlambda) / dt
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config(prob),
-        "cpu_baseline": {"value": value, "unit": "paths/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "paths/s", "cores": used, "kind": "oracle",
+                         "cpu_model": cpu["model"], "nproc": cpu["nproc"],
                          "sample": f"{args.steps} steps x 10 consecutive lambdas of a warm-started 100-lambda "
-                                   f"oracle path ({lam_done} lambdas)"},
+                                   f"oracle path ({lam_done} lambdas) on {used} threads"},
         "e2e": {"value": value, "unit": "paths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

@@ -509,10 +509,14 @@ int bl_fit_many(bl_ctx *ctx, bl_problem *probs, int nprob, const bl_options *opt
  * calls that overlap on the GPU -- on different streams or from different
  * host threads -- race and must be serialized by the caller.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress with
- * that device current); make that first call before any stream capture.
+ * that device current) and keeps it for the life of the process; make that
+ * first call before any stream capture, and do not call this entry point on a
+ * device after a cudaDeviceReset of it.  A CUDA error already pending on the
+ * calling thread is reported (BL_ERR_CUDA) before anything is enqueued.
  * err (nullable) receives a NUL-terminated message of at most err_len bytes
- * when the call fails.  Errors: as bl_cd_active, plus BL_ERR_UNSUPPORTED for
- * n_work > BL_NOALLOC_MAX_WORK. */
+ * when the call fails.  Errors: as bl_cd_active (BL_ERR_ARG, with beta and r
+ * untouched, when work_idx holds an index outside [0, p)), plus
+ * BL_ERR_UNSUPPORTED for n_work > BL_NOALLOC_MAX_WORK. */
 int bl_cd_active_noalloc(int device, void *stream, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx,
                          const double *center, const double *scale, const int32_t *work_idx, int64_t n_work,
                          double lam, double alpha, void *beta, void *r, double eps, int64_t max_sweeps,

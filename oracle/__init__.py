@@ -23,58 +23,104 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_OUT_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_lib = None        # the serial build (pins, parity tests)
+_lib_omp = None    # the OpenMP build (timed all-cores baseline), loaded by set_threads
+_threads = 1
 
 OK, ERR_ARG, ERR_OOM, ERR_NOT_CONVERGED = 0, -1, -3, -4
 
 _dp = C.POINTER(C.c_double)
 _i64p = C.POINTER(C.c_int64)
 _u8p = C.POINTER(C.c_uint8)
+_i8p = C.POINTER(C.c_int8)
+
+
+def _compile(out: str, extra: list, force: bool) -> str:
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", *extra,
+                               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 def build(force: bool = False) -> str:
     """Compile oracle.c into _build/liboracle.so (gcc, -O2, no FP contraction)."""
-    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
-        tmp = _OUT + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
-                               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _OUT)
-    return _OUT
+    return _compile(_OUT, [], force)
+
+
+def build_omp(force: bool = False) -> str:
+    """The same source with -fopenmp (_build/liboracle_omp.so): the all-cores
+    build whose results are bit-identical to the serial one's."""
+    return _compile(_OUT_OMP, ["-fopenmp"], force)
+
+
+def _declare(L):
+    i64 = C.c_int64
+    L.orc_set_threads.argtypes = [C.c_int]
+    L.orc_standardize.argtypes = [_dp, i64, i64, i64, _dp, _dp, _u8p]
+    L.orc_center.argtypes = [_dp, i64, _dp]
+    L.orc_center.restype = C.c_double
+    L.orc_standardized_matrix.argtypes = [_dp, i64, i64, i64, _dp, _dp, _u8p, _dp]
+    L.orc_xtv.argtypes = [_dp, i64, i64, _dp, _dp]
+    L.orc_z.argtypes = [_dp, i64, i64, _dp, _dp]
+    L.orc_lambda_max.argtypes = [_dp, _u8p, i64, i64, C.c_double, _dp, _i64p]
+    L.orc_lambda_grid.argtypes = [C.c_double, C.c_double, C.c_int, _dp]
+    L.orc_bedpp_init.argtypes = [_dp, i64, i64, i64, _dp, _dp]
+    L.orc_bedpp_init.restype = C.c_double
+    L.orc_bedpp_safe.argtypes = [_dp, _dp, _u8p, i64, i64, C.c_double, i64, C.c_double,
+                                 C.c_double, C.c_double, _u8p]
+    L.orc_strong.argtypes = [_dp, _u8p, _dp, i64, C.c_double, C.c_double, C.c_double, _u8p]
+    L.orc_cd.argtypes = [_dp, i64, _i64p, i64, C.c_double, C.c_double, C.c_double, i64,
+                         _dp, _dp, _i64p]
+    L.orc_objective.argtypes = [_dp, i64, i64, _dp, _dp, C.c_double, C.c_double]
+    L.orc_objective.restype = C.c_double
+    L.orc_fit_path.argtypes = [_dp, i64, i64, i64, _dp, C.c_double, _dp, C.c_int, C.c_int,
+                               C.c_double, i64, _dp, _dp, _dp, _dp, _i64p]
+    L.orc_standardize_i8.argtypes = [_i8p, i64, i64, i64, _dp, _dp, _u8p]
+    L.orc_xtv_i8.argtypes = [_i8p, i64, i64, i64, _dp, _dp, _u8p, _dp, _dp]
+    L.orc_fit_path_i8.argtypes = [_i8p, i64, i64, i64, _dp, C.c_double, _dp, C.c_int, C.c_int,
+                                  C.c_double, i64, _dp, _dp, _dp, _dp, _i64p]
+    L.orc_mlp_nparam.argtypes = []
+    L.orc_mlp_forward.argtypes = [_dp, _dp, i64, _dp]
+    L.orc_mlp_loss_grad.argtypes = [_dp, _dp, _u8p, i64, _dp]
+    L.orc_mlp_loss_grad.restype = C.c_double
+    return L
 
 
 def lib():
     global _lib
     with _lock:
+        if _threads > 1 and _lib_omp is not None:
+            return _lib_omp
         if _lib is None:
-            L = C.CDLL(build())
-            i64 = C.c_int64
-            L.orc_standardize.argtypes = [_dp, i64, i64, i64, _dp, _dp, _u8p]
-            L.orc_center.argtypes = [_dp, i64, _dp]
-            L.orc_center.restype = C.c_double
-            L.orc_standardized_matrix.argtypes = [_dp, i64, i64, i64, _dp, _dp, _u8p, _dp]
-            L.orc_xtv.argtypes = [_dp, i64, i64, _dp, _dp]
-            L.orc_z.argtypes = [_dp, i64, i64, _dp, _dp]
-            L.orc_lambda_max.argtypes = [_dp, _u8p, i64, i64, C.c_double, _dp, _i64p]
-            L.orc_lambda_grid.argtypes = [C.c_double, C.c_double, C.c_int, _dp]
-            L.orc_bedpp_init.argtypes = [_dp, i64, i64, i64, _dp, _dp]
-            L.orc_bedpp_init.restype = C.c_double
-            L.orc_bedpp_safe.argtypes = [_dp, _dp, _u8p, i64, i64, C.c_double, i64, C.c_double,
-                                         C.c_double, C.c_double, _u8p]
-            L.orc_strong.argtypes = [_dp, _u8p, _dp, i64, C.c_double, C.c_double, C.c_double, _u8p]
-            L.orc_cd.argtypes = [_dp, i64, _i64p, i64, C.c_double, C.c_double, C.c_double, i64,
-                                 _dp, _dp, _i64p]
-            L.orc_objective.argtypes = [_dp, i64, i64, _dp, _dp, C.c_double, C.c_double]
-            L.orc_objective.restype = C.c_double
-            L.orc_fit_path.argtypes = [_dp, i64, i64, i64, _dp, C.c_double, _dp, C.c_int, C.c_int,
-                                       C.c_double, i64, _dp, _dp, _dp, _dp, _i64p]
-            L.orc_mlp_nparam.argtypes = []
-            L.orc_mlp_forward.argtypes = [_dp, _dp, i64, _dp]
-            L.orc_mlp_loss_grad.argtypes = [_dp, _dp, _u8p, i64, _dp]
-            L.orc_mlp_loss_grad.restype = C.c_double
-            _lib = L
+            _lib = _declare(C.CDLL(build()))
     return _lib
+
+
+def set_threads(k: int) -> int:
+    """Run later oracle calls on k threads (the OpenMP build) or serially (k <= 1).
+    Returns the thread count in use; 1 where the OpenMP build is unavailable."""
+    global _lib_omp, _threads
+    if k <= 1:
+        _threads = 1
+        return 1
+    with _lock:
+        if _lib_omp is None:
+            try:
+                _lib_omp = _declare(C.CDLL(build_omp()))
+            except (OSError, subprocess.CalledProcessError):
+                _threads = 1
+                return 1
+        _threads = int(_lib_omp.orc_set_threads(int(k)))
+    return _threads
+
+
+def threads() -> int:
+    return _threads
 
 
 def _p(a, t=_dp):
@@ -233,6 +279,59 @@ def fit_path(X, y, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, lambdas=None,
     return dict(lambdas=lambdas, beta=beta, beta_orig=beta_orig, intercept=icpt, loss=loss,
                 sweeps=sweeps, status=st, lmax=lmax, jstar=jstar, c=c, s=s, keep=keep,
                 ybar=ybar, xty=xty)
+
+
+def _i8(a):
+    return np.ascontiguousarray(a, dtype=np.int8)
+
+
+def standardize_i8(X8, n):
+    """c, s, keep of the int8 columns X8[j, :n] (X8 shape (p, ldx)), Sec. 3.1."""
+    X8 = _i8(X8)
+    p, ldx = X8.shape
+    c, s = np.empty(p), np.empty(p)
+    keep = np.empty(p, dtype=np.uint8)
+    st = lib().orc_standardize_i8(_p(X8, _i8p), n, p, ldx, _p(c), _p(s), _p(keep, _u8p))
+    if st != OK:
+        raise MemoryError("oracle: standardize_i8 failed")
+    return c, s, keep
+
+
+def xtv_i8(X8, n, c, s, keep, v):
+    """xt_j' v for every int8 column, xt_ij = (x_ij - c_j)/s_j evaluated in FP64."""
+    X8 = _i8(X8)
+    p, ldx = X8.shape
+    out = np.empty(p)
+    lib().orc_xtv_i8(_p(X8, _i8p), n, p, ldx, _p(_f64(c)), _p(_f64(s)),
+                     _p(np.ascontiguousarray(keep, dtype=np.uint8), _u8p), _p(_f64(v)), _p(out))
+    return out
+
+
+def fit_path_i8(X8, n, y, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, n_solve=None, max_sweeps=100_000):
+    """The path of ``fit_path`` on a raw int8 design X8 (shape (p, ldx), column
+    j = X8[j, :n]) without forming the FP64 standardized copy.  Solves the first
+    ``n_solve`` lambdas of the K-point grid (all when None); returns the dict of
+    ``fit_path`` for those lambdas."""
+    X8 = _i8(X8)
+    p, ldx = X8.shape
+    y = _f64(y)
+    c, s, keep = standardize_i8(X8, n)
+    yc, ybar = center(y)
+    xty = xtv_i8(X8, n, c, s, keep, yc)
+    lmax, jstar = lambda_max(xty, keep, n, alpha)
+    grid = lambda_grid(lmax, ratio, nlambda)
+    lambdas = grid if n_solve is None else grid[:n_solve]
+    K = lambdas.size
+    beta = np.empty((K, p))
+    beta_orig = np.empty((K, p))
+    icpt, loss = np.empty(K), np.empty(K)
+    sweeps = np.empty(K, dtype=np.int64)
+    st = lib().orc_fit_path_i8(_p(X8, _i8p), n, p, ldx, _p(y), alpha, _p(lambdas), K, 1, eps, max_sweeps,
+                               _p(beta), _p(beta_orig), _p(icpt), _p(loss), _p(sweeps, _i64p))
+    if st == ERR_ARG:
+        raise ValueError("invalid arguments to the oracle path")
+    return dict(lambdas=lambdas, grid=grid, beta=beta, beta_orig=beta_orig, intercept=icpt, loss=loss,
+                sweeps=sweeps, status=st, lmax=lmax, jstar=jstar, c=c, s=s, keep=keep, ybar=ybar, xty=xty)
 
 
 def mlp_nparam():

@@ -61,11 +61,20 @@
  *
  * Parity pins for every function live in tests/test_oracle_pins.py
  * (closed forms, brute-force support enumeration, KKT conditions, safety).
+ *
+ * Built twice: serially (the oracle the pins and parity tests use) and with
+ * -fopenmp (the timed all-cores baseline).  The OpenMP build parallelizes only
+ * the gradient of the full sweep and the per-feature correlation loops -- the
+ * places Sec. 3.2 names for its OpenMP loop -- in a way that leaves every
+ * result bit-identical to the serial build's (see full_sweep).
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef int64_t i64;
 
@@ -73,6 +82,18 @@ typedef int64_t i64;
 #define ORC_ERR_ARG (-1)
 #define ORC_ERR_OOM (-3)
 #define ORC_ERR_NOT_CONVERGED (-4)
+
+/* Threads of the OpenMP build (1 in the serial build); returns the count in use. */
+int orc_set_threads(int k)
+{
+#ifdef _OPENMP
+    if (k > 0) omp_set_num_threads(k);
+    return omp_get_max_threads();
+#else
+    (void)k;
+    return 1;
+#endif
+}
 
 static const double *col(const double *X, i64 ldx, i64 j) { return X + (size_t)j * (size_t)ldx; }
 
@@ -138,6 +159,7 @@ int orc_standardized_matrix(const double *X, i64 n, i64 p, i64 ldx, const double
 /* out_j = xt_j' v  (plain dot products of the explicit standardized columns). */
 void orc_xtv(const double *Xt, i64 n, i64 p, const double *v, double *out)
 {
+#pragma omp parallel for schedule(static)
     for (i64 j = 0; j < p; ++j) {
         const double *t = Xt + (size_t)j * (size_t)n;
         double acc = 0.0;
@@ -236,29 +258,121 @@ void orc_strong(const double *zprev, const uint8_t *safe, const double *beta_pre
         strong[j] = (uint8_t)(safe[j] && (beta_prev[j] != 0.0 || fabs(zprev[j]) >= t));
 }
 
-/* One coordinate update; returns the change in b_j. */
-static double cd_update(const double *Xt, i64 n, i64 j, double thr, double den, double *beta,
-                        double *r, int *became_nonzero)
+/* The standardized design as the descent reads it: either the explicit FP64
+ * columns Xt (p x n, column j contiguous), or raw int8 columns (leading
+ * dimension ld) with xt_ij = (x_ij - c_j)/s_j evaluated where it is used.  The
+ * second form is for designs whose explicit FP64 copy would not fit in host
+ * memory (5000 x 500,000 genotypes: 20 GB); it does, element by element, the
+ * arithmetic orc_standardized_matrix stores, so both forms give bit-identical
+ * results on a design small enough for either. */
+typedef struct {
+    const double *Xt;
+    const int8_t *X8;
+    i64 n, ld;
+    const double *c, *s;
+} design;
+
+/* xt_j' r. */
+static double col_dot(const design *D, i64 j, const double *r)
 {
-    const double *t = Xt + (size_t)j * (size_t)n;
     double acc = 0.0;
-    for (i64 i = 0; i < n; ++i) acc += t[i] * r[i];
+    if (D->Xt) {
+        const double *t = D->Xt + (size_t)j * (size_t)D->n;
+        for (i64 i = 0; i < D->n; ++i) acc += t[i] * r[i];
+    } else {
+        const int8_t *x = D->X8 + (size_t)j * (size_t)D->ld;
+        const double cj = D->c[j], sj = D->s[j];
+        for (i64 i = 0; i < D->n; ++i) acc += (((double)x[i] - cj) / sj) * r[i];
+    }
+    return acc;
+}
+
+/* r <- r - d xt_j. */
+static void col_axpy(const design *D, i64 j, double d, double *r)
+{
+    if (D->Xt) {
+        const double *t = D->Xt + (size_t)j * (size_t)D->n;
+        for (i64 i = 0; i < D->n; ++i) r[i] -= d * t[i];
+    } else {
+        const int8_t *x = D->X8 + (size_t)j * (size_t)D->ld;
+        const double cj = D->c[j], sj = D->s[j];
+        for (i64 i = 0; i < D->n; ++i) r[i] -= d * (((double)x[i] - cj) / sj);
+    }
+}
+
+/* The update of coordinate j given acc = xt_j' r; returns the change in b_j. */
+static double cd_apply(const design *D, i64 j, double acc, double thr, double den, double *beta, double *r,
+                       int *became_nonzero)
+{
     double old = beta[j];
-    double zt = acc / (double)n + old;
+    double zt = acc / (double)D->n + old;
     double nb = soft(zt, thr) / den;
     double d = nb - old;
     if (d != 0.0) {
-        for (i64 i = 0; i < n; ++i) r[i] -= d * t[i];
+        col_axpy(D, j, d, r);
         beta[j] = nb;
         if (old == 0.0 && nb != 0.0) *became_nonzero = 1;
     }
     return d;
 }
 
-/* Coordinate descent at one lambda over the coordinates idx[0..m) (in that
- * order), starting from (beta, r) with r = yc - Xt beta.  beta is dense (p). */
-int orc_cd(const double *Xt, i64 n, const i64 *idx, i64 m, double lam, double alpha, double eps,
-           i64 max_sweeps, double *beta, double *r, i64 *sweeps_out)
+/* One coordinate update; returns the change in b_j. */
+static double cd_update(const design *D, i64 j, double thr, double den, double *beta, double *r,
+                        int *became_nonzero)
+{
+    return cd_apply(D, j, col_dot(D, j, r), thr, den, beta, r, became_nonzero);
+}
+
+#ifdef _OPENMP
+/* The full sweep (i) with the dot products of runs of zero coordinates taken in
+ * parallel (where the paper places its OpenMP loop, Sec. 3.2: the gradient over
+ * the features).  A coordinate whose update leaves b_j unchanged does not touch
+ * r, so the dots of a run of such coordinates all see the same r and can be
+ * formed at once; the run is walked in index order and cut after the first
+ * coordinate that changes, where the next run starts.  Coordinates with
+ * b_j != 0 are updated one by one.  Every update therefore sees exactly the r
+ * of the serial sweep and does the same arithmetic, so the results are
+ * bit-identical to the serial build's. */
+#define ORC_RUN 512
+static void full_sweep(const design *D, const i64 *idx, i64 m, double thr, double den, double *beta, double *r,
+                       double *maxd, int *newnz)
+{
+    double acc[ORC_RUN];
+    i64 t = 0;
+    while (t < m) {
+        if (beta[idx[t]] != 0.0) {
+            double d = fabs(cd_update(D, idx[t], thr, den, beta, r, newnz));
+            if (d > *maxd) *maxd = d;
+            ++t;
+            continue;
+        }
+        i64 e = t;
+        while (e < m && e - t < ORC_RUN && beta[idx[e]] == 0.0) ++e;
+#pragma omp parallel for schedule(static)
+        for (i64 u = t; u < e; ++u) acc[u - t] = col_dot(D, idx[u], r);
+        i64 u = t;
+        while (u < e) {
+            double d = fabs(cd_apply(D, idx[u], acc[u - t], thr, den, beta, r, newnz));
+            if (d > *maxd) *maxd = d;
+            ++u;
+            if (d != 0.0) break;
+        }
+        t = u;
+    }
+}
+#else
+static void full_sweep(const design *D, const i64 *idx, i64 m, double thr, double den, double *beta, double *r,
+                       double *maxd, int *newnz)
+{
+    for (i64 t = 0; t < m; ++t) {
+        double d = fabs(cd_update(D, idx[t], thr, den, beta, r, newnz));
+        if (d > *maxd) *maxd = d;
+    }
+}
+#endif
+
+static int cd_run(const design *D, const i64 *idx, i64 m, double lam, double alpha, double eps, i64 max_sweeps,
+                  double *beta, double *r, i64 *sweeps_out)
 {
     double thr = lam * alpha, den = 1.0 + lam * (1.0 - alpha);
     i64 sweeps = 0;
@@ -268,10 +382,7 @@ int orc_cd(const double *Xt, i64 n, const i64 *idx, i64 m, double lam, double al
     for (;;) {
         double maxd = 0.0;
         int newnz = 0;
-        for (i64 t = 0; t < m; ++t) {
-            double d = fabs(cd_update(Xt, n, idx[t], thr, den, beta, r, &newnz));
-            if (d > maxd) maxd = d;
-        }
+        full_sweep(D, idx, m, thr, den, beta, r, &maxd, &newnz);
         ++sweeps;
         if (maxd < eps && !newnz) break;
         if (sweeps >= max_sweeps) {
@@ -285,7 +396,7 @@ int orc_cd(const double *Xt, i64 n, const i64 *idx, i64 m, double lam, double al
             double md = 0.0;
             int dummy = 0;
             for (i64 a = 0; a < na; ++a) {
-                double d = fabs(cd_update(Xt, n, act[a], thr, den, beta, r, &dummy));
+                double d = fabs(cd_update(D, act[a], thr, den, beta, r, &dummy));
                 if (d > md) md = d;
             }
             ++sweeps;
@@ -302,10 +413,18 @@ int orc_cd(const double *Xt, i64 n, const i64 *idx, i64 m, double lam, double al
     return status;
 }
 
-/* Q(b; lam) with the residual recomputed from scratch. */
-double orc_objective(const double *Xt, i64 n, i64 p, const double *yc, const double *beta,
-                     double lam, double alpha)
+/* Coordinate descent at one lambda over the coordinates idx[0..m) (in that
+ * order), starting from (beta, r) with r = yc - Xt beta.  beta is dense (p). */
+int orc_cd(const double *Xt, i64 n, const i64 *idx, i64 m, double lam, double alpha, double eps,
+           i64 max_sweeps, double *beta, double *r, i64 *sweeps_out)
 {
+    design D = {Xt, NULL, n, n, NULL, NULL};
+    return cd_run(&D, idx, m, lam, alpha, eps, max_sweeps, beta, r, sweeps_out);
+}
+
+static double objective(const design *D, i64 p, const double *yc, const double *beta, double lam, double alpha)
+{
+    i64 n = D->n;
     double *r = (double *)malloc((size_t)n * sizeof(double));
     if (!r) return NAN;
     memcpy(r, yc, (size_t)n * sizeof(double));
@@ -313,8 +432,7 @@ double orc_objective(const double *Xt, i64 n, i64 p, const double *yc, const dou
     for (i64 j = 0; j < p; ++j) {
         double b = beta[j];
         if (b == 0.0) continue;
-        const double *t = Xt + (size_t)j * (size_t)n;
-        for (i64 i = 0; i < n; ++i) r[i] -= b * t[i];
+        col_axpy(D, j, b, r);
         l1 += fabs(b);
         l2 += b * b;
     }
@@ -322,6 +440,60 @@ double orc_objective(const double *Xt, i64 n, i64 p, const double *yc, const dou
     for (i64 i = 0; i < n; ++i) rss += r[i] * r[i];
     free(r);
     return rss / (2.0 * (double)n) + lam * alpha * l1 + 0.5 * lam * (1.0 - alpha) * l2;
+}
+
+/* Q(b; lam) with the residual recomputed from scratch. */
+double orc_objective(const double *Xt, i64 n, i64 p, const double *yc, const double *beta,
+                     double lam, double alpha)
+{
+    design D = {Xt, NULL, n, n, NULL, NULL};
+    return objective(&D, p, yc, beta, lam, alpha);
+}
+
+/* The path over lambdas[0..K) on a standardized design (see orc_fit_path). */
+static int fit_path(const design *D, i64 p, const uint8_t *keep, const double *c, const double *s, const double *yc,
+                    double ybar, double lmax, double alpha, const double *lambdas, int K, int grid_from_lmax,
+                    double eps, i64 max_sweeps, double *beta_out, double *beta_orig, double *intercept, double *loss,
+                    i64 *sweeps)
+{
+    i64 n = D->n;
+    double *beta = calloc((size_t)p, sizeof(double));
+    double *r = malloc((size_t)n * sizeof(double));
+    i64 *idx = malloc((size_t)p * sizeof(i64));
+    int status = ORC_OK;
+    if (!beta || !r || !idx) {
+        status = ORC_ERR_OOM;
+        goto done;
+    }
+    i64 m = 0;
+    for (i64 j = 0; j < p; ++j)
+        if (keep[j]) idx[m++] = j;
+    memcpy(r, yc, (size_t)n * sizeof(double));
+    for (int k = 0; k < K; ++k) {
+        double lam = lambdas[k];
+        i64 sw = 0;
+        int at_max = (grid_from_lmax && k == 0) || lam >= lmax;
+        if (!at_max) {
+            int st = cd_run(D, idx, m, lam, alpha, eps, max_sweeps, beta, r, &sw);
+            if (st != ORC_OK && status == ORC_OK) status = st;
+        }
+        double *bk = beta_out + (size_t)k * (size_t)p;
+        memcpy(bk, beta, (size_t)p * sizeof(double));
+        double icpt = ybar;
+        for (i64 j = 0; j < p; ++j) {
+            double bo = (beta[j] != 0.0) ? beta[j] / s[j] : 0.0;
+            if (beta_orig) beta_orig[(size_t)k * (size_t)p + (size_t)j] = bo;
+            icpt -= c[j] * bo;
+        }
+        if (intercept) intercept[k] = icpt;
+        if (loss) loss[k] = objective(D, p, yc, beta, lam, alpha);
+        if (sweeps) sweeps[k] = sw;
+    }
+done:
+    free(beta);
+    free(r);
+    free(idx);
+    return status;
 }
 
 /* Full path from raw FP64 data (column-major, leading dimension ldx).
@@ -344,11 +516,8 @@ int orc_fit_path(const double *X, i64 n, i64 p, i64 ldx, const double *y, double
     double *yc = malloc((size_t)n * sizeof(double));
     double *Xt = malloc((size_t)n * (size_t)p * sizeof(double));
     double *xty = malloc((size_t)p * sizeof(double));
-    double *beta = calloc((size_t)p, sizeof(double));
-    double *r = malloc((size_t)n * sizeof(double));
-    i64 *idx = malloc((size_t)p * sizeof(i64));
     int status = ORC_OK;
-    if (!c || !s || !keep || !yc || !Xt || !xty || !beta || !r || !idx) {
+    if (!c || !s || !keep || !yc || !Xt || !xty) {
         status = ORC_ERR_OOM;
         goto done;
     }
@@ -359,30 +528,9 @@ int orc_fit_path(const double *X, i64 n, i64 p, i64 ldx, const double *y, double
     double lmax;
     i64 jstar;
     orc_lambda_max(xty, keep, p, n, alpha, &lmax, &jstar);
-    i64 m = 0;
-    for (i64 j = 0; j < p; ++j)
-        if (keep[j]) idx[m++] = j;
-    memcpy(r, yc, (size_t)n * sizeof(double));
-    for (int k = 0; k < K; ++k) {
-        double lam = lambdas[k];
-        i64 sw = 0;
-        int at_max = (grid_from_lmax && k == 0) || lam >= lmax;
-        if (!at_max) {
-            int st = orc_cd(Xt, n, idx, m, lam, alpha, eps, max_sweeps, beta, r, &sw);
-            if (st != ORC_OK && status == ORC_OK) status = st;
-        }
-        double *bk = beta_out + (size_t)k * (size_t)p;
-        memcpy(bk, beta, (size_t)p * sizeof(double));
-        double icpt = ybar;
-        for (i64 j = 0; j < p; ++j) {
-            double bo = (beta[j] != 0.0) ? beta[j] / s[j] : 0.0;
-            if (beta_orig) beta_orig[(size_t)k * (size_t)p + (size_t)j] = bo;
-            icpt -= c[j] * bo;
-        }
-        if (intercept) intercept[k] = icpt;
-        if (loss) loss[k] = orc_objective(Xt, n, p, yc, beta, lam, alpha);
-        if (sweeps) sweeps[k] = sw;
-    }
+    design D = {Xt, NULL, n, n, NULL, NULL};
+    status = fit_path(&D, p, keep, c, s, yc, ybar, lmax, alpha, lambdas, K, grid_from_lmax, eps, max_sweeps,
+                      beta_out, beta_orig, intercept, loss, sweeps);
 done:
     free(c);
     free(s);
@@ -390,9 +538,84 @@ done:
     free(yc);
     free(Xt);
     free(xty);
-    free(beta);
-    free(r);
-    free(idx);
+    return status;
+}
+
+/* ------------------------------------------------------------------------
+ * Raw int8 designs (genotype codes) too large for the explicit FP64 copy of
+ * Xt: the same standardization, correlations and path, with xt_ij evaluated
+ * where it is used (the second form of `design` above).  X8 is column-major
+ * with leading dimension ldx; every value is promoted exactly to FP64. */
+
+/* Column mean, population sd and keep flag of each int8 column (Sec. 3.1). */
+int orc_standardize_i8(const int8_t *X8, i64 n, i64 p, i64 ldx, double *c, double *s, uint8_t *keep)
+{
+    if (n < 1 || p < 0 || ldx < n) return ORC_ERR_ARG;
+    int status = ORC_OK;
+#pragma omp parallel
+    {
+        double *x = malloc((size_t)n * sizeof(double));
+        if (!x) {
+#pragma omp atomic write
+            status = ORC_ERR_OOM;
+        }
+#pragma omp for schedule(static)
+        for (i64 j = 0; j < p; ++j) {
+            if (!x) continue;
+            const int8_t *x8 = X8 + (size_t)j * (size_t)ldx;
+            for (i64 i = 0; i < n; ++i) x[i] = (double)x8[i];
+            orc_standardize(x, n, 1, n, c + j, s + j, keep + j);
+        }
+        free(x);
+    }
+    return status;
+}
+
+/* out_j = xt_j' v for every column (0 for keep = 0 columns). */
+void orc_xtv_i8(const int8_t *X8, i64 n, i64 p, i64 ldx, const double *c, const double *s, const uint8_t *keep,
+                const double *v, double *out)
+{
+    design D = {NULL, X8, n, ldx, c, s};
+#pragma omp parallel for schedule(static)
+    for (i64 j = 0; j < p; ++j) out[j] = keep[j] ? col_dot(&D, j, v) : 0.0;
+}
+
+/* The path of orc_fit_path on a raw int8 design.  Also returns lambda_max and
+ * its column, so a caller can build the grid and solve a prefix of it. */
+int orc_fit_path_i8(const int8_t *X8, i64 n, i64 p, i64 ldx, const double *y, double alpha,
+                    const double *lambdas, int K, int grid_from_lmax, double eps, i64 max_sweeps,
+                    double *beta_out, double *beta_orig, double *intercept, double *loss, i64 *sweeps)
+{
+    if (n < 1 || p < 1 || ldx < n || K < 1 || !(alpha > 0.0 && alpha <= 1.0) || !(eps > 0.0))
+        return ORC_ERR_ARG;
+    for (int k = 1; k < K; ++k)
+        if (!(lambdas[k] < lambdas[k - 1])) return ORC_ERR_ARG;
+    double *c = malloc((size_t)p * sizeof(double));
+    double *s = malloc((size_t)p * sizeof(double));
+    uint8_t *keep = malloc((size_t)p);
+    double *yc = malloc((size_t)n * sizeof(double));
+    double *xty = malloc((size_t)p * sizeof(double));
+    int status = ORC_OK;
+    if (!c || !s || !keep || !yc || !xty) {
+        status = ORC_ERR_OOM;
+        goto done;
+    }
+    status = orc_standardize_i8(X8, n, p, ldx, c, s, keep);
+    if (status != ORC_OK) goto done;
+    double ybar = orc_center(y, n, yc);
+    orc_xtv_i8(X8, n, p, ldx, c, s, keep, yc, xty);
+    double lmax;
+    i64 jstar;
+    orc_lambda_max(xty, keep, p, n, alpha, &lmax, &jstar);
+    design D = {NULL, X8, n, ldx, c, s};
+    status = fit_path(&D, p, keep, c, s, yc, ybar, lmax, alpha, lambdas, K, grid_from_lmax, eps, max_sweeps,
+                      beta_out, beta_orig, intercept, loss, sweeps);
+done:
+    free(c);
+    free(s);
+    free(keep);
+    free(yc);
+    free(xty);
     return status;
 }
 

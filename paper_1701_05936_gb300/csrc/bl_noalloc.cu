@@ -20,6 +20,9 @@ constexpr int64_t NOALLOC_W = BL_NOALLOC_MAX_WORK;
 // gref, c_w and 1/s_w (8 bytes per working-set entry each) and the counters
 constexpr size_t NOALLOC_BYTES = 3 * (size_t)NOALLOC_W * 8 + 256;
 static_assert(sizeof(DevScalars) <= 256, "counters must fit their scratch slot");
+// the CD kernel's own shared-memory capacity (the smallest, FP64's) bounds the
+// working sets this entry point may accept
+static_assert(BL_NOALLOC_MAX_WORK <= MAX_WORKING_F64, "scratch capacity beyond the CD kernel's limit");
 
 }  // namespace
 
@@ -44,7 +47,8 @@ void put_err(char *buf, size_t len, const char *fmt, ...)
 }
 
 // Device address of the scratch on `device` (the current device), looked up
-// once per device.
+// once per device and kept for the life of the process (a cudaDeviceReset of
+// that device invalidates it; the header says so).
 cudaError_t scratch_address(int device, void **out)
 {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -119,8 +123,15 @@ extern "C" int bl_cd_active_noalloc(int device, void *stream, const void *X, int
                 (long long)n_work, (long long)NOALLOC_W);
         return BL_ERR_UNSUPPORTED;
     }
+    // an error a previous call left pending on this thread is the caller's, not
+    // this call's: report it before anything is enqueued
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        put_err(err, err_len, "a CUDA error was pending before this call: %s", cudaGetErrorString(e));
+        return BL_ERR_CUDA;
+    }
     int prev = 0;
-    cudaError_t e = cudaGetDevice(&prev);
+    e = cudaGetDevice(&prev);
     if (e == cudaSuccess && prev != device) e = cudaSetDevice(device);
     if (e != cudaSuccess) {
         put_err(err, err_len, "cudaSetDevice: %s", cudaGetErrorString(e));
@@ -168,6 +179,9 @@ extern "C" int bl_cd_active_noalloc(int device, void *stream, const void *X, int
     if (h.status & ST_BAD_INDEX) {
         put_err(err, err_len, "work_idx holds an index outside [0, p)");
         status = BL_ERR_ARG;
+    } else if (h.status & ST_WORKING_TOO_BIG) {
+        put_err(err, err_len, "working set too large for the coordinate-descent kernel");
+        status = BL_ERR_UNSUPPORTED;
     } else if (h.status & ST_TIMEOUT) {
         put_err(err, err_len, "CD reached its wall-clock limit");
         status = BL_ERR_TIMEOUT;

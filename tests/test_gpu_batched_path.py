@@ -47,7 +47,7 @@ def _check(bp, res, alpha, K, ratio=0.05, eps=1e-7, allow_exempt=0):
                                                       eps=eps)
             g = res[r * F + f]
             assert g["status"] in (bl.BL_OK,)
-            worst = max(worst, compare_paths(prob, g, ref, 1e-5, allow_exempt=allow_exempt))
+            worst = max(worst, compare_paths(prob, g, ref, 1e-5, allow_exempt=allow_exempt, label=f"r{r} f{f}")[0])
             np.testing.assert_allclose(g["ybar"], ref["ybar"], rtol=1e-12, atol=1e-12)
     return worst
 

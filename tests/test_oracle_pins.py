@@ -211,6 +211,71 @@ def test_lambda_max_is_the_entry_point():
         np.testing.assert_allclose(res2["beta"][1], bf_lo, atol=1e-12)
 
 
+# ------------------------------------------------------------- lambda grid ---
+def test_lambda_grid_closed_form():
+    """Sec. 4: lambda runs from lambda_max down to ratio * lambda_max on a log
+    scale.  Closed forms: K = 1 gives [lambda_max]; K = 2 gives [lambda_max,
+    ratio lambda_max]; with ratio = 2^-6 and K = 7 every step halves, so the grid
+    is lambda_max * 2^-k exactly up to pow's rounding; for any K the endpoints
+    are lambda_max and ratio lambda_max and successive ratios are constant."""
+    lmax = 3.7
+    assert oracle.lambda_grid(lmax, 0.05, 1).tolist() == [lmax]
+    np.testing.assert_array_equal(oracle.lambda_grid(lmax, 0.05, 2), [lmax, lmax * 0.05])
+    g7 = oracle.lambda_grid(lmax, 2.0 ** -6, 7)
+    np.testing.assert_allclose(g7, lmax * 2.0 ** -np.arange(7), rtol=4e-16, atol=0)
+    for K, ratio in ((100, 0.05), (100, 0.1), (37, 0.02)):
+        g = oracle.lambda_grid(lmax, ratio, K)
+        assert g[0] == lmax and g[-1] == pytest.approx(ratio * lmax, rel=1e-15)
+        q = g[1:] / g[:-1]
+        np.testing.assert_allclose(q, ratio ** (1.0 / (K - 1)), rtol=1e-14)
+        # k-th point from the definition, written as exp of a sum of logs in long double
+        k = np.arange(K, dtype=np.longdouble)
+        ref = np.longdouble(lmax) * np.exp(k / (K - 1) * np.log(np.longdouble(ratio)))
+        np.testing.assert_allclose(g, ref.astype(np.float64), rtol=1e-15)
+
+
+def test_path_runner_reproduces_fit_path():
+    """The reference arm's PathRunner steps the same path as fit_path, a few
+    lambdas at a time: identical coefficients at every lambda."""
+    prob = synth.gaussian_ar1(n=60, p=150, k=6, dtype="f64", replicate=31)
+    res = oracle.fit_path(prob.dense_f64(), prob.y, alpha=0.8, ratio=0.05, nlambda=30, eps=1e-9)
+    run = oracle.PathRunner(prob.dense_f64(), prob.y, alpha=0.8, ratio=0.05, nlambda=30, eps=1e-9)
+    np.testing.assert_array_equal(run.lambdas, res["lambdas"])
+    k = 0
+    for step in (1, 3, 5, 100):
+        ran = run.advance(step)
+        k += ran
+        np.testing.assert_array_equal(run.beta, res["beta"][k - 1])
+    assert run.done and k == 30
+
+
+def test_openmp_build_and_int8_form_are_bit_identical():
+    """The all-cores (OpenMP) build and the int8 form that evaluates xt_ij on the
+    fly give exactly the serial explicit oracle's path (same arithmetic, same
+    order), on a genotype design and on a correlated FP64 design."""
+    geno = synth.genotype(n=150, p=700, k=6, replicate=32)
+    ar1 = synth.gaussian_ar1(n=120, p=500, k=6, dtype="f64", replicate=33)
+    ref_g = oracle.fit_path(geno.dense_f64(), geno.y, ratio=0.05, nlambda=40)
+    ref_a = oracle.fit_path(ar1.dense_f64(), ar1.y, alpha=0.7, ratio=0.05, nlambda=40)
+    i8 = oracle.fit_path_i8(geno.X, geno.n, geno.y, ratio=0.05, nlambda=40)
+    part = oracle.fit_path_i8(geno.X, geno.n, geno.y, ratio=0.05, nlambda=40, n_solve=12)
+    for key in ("beta", "loss", "intercept", "sweeps"):
+        np.testing.assert_array_equal(i8[key], ref_g[key])
+        np.testing.assert_array_equal(part[key], ref_g[key][:12])
+    try:
+        if oracle.set_threads(4) < 2:
+            pytest.skip("no OpenMP build on this host")
+        omp_g = oracle.fit_path(geno.dense_f64(), geno.y, ratio=0.05, nlambda=40)
+        omp_a = oracle.fit_path(ar1.dense_f64(), ar1.y, alpha=0.7, ratio=0.05, nlambda=40)
+        omp_i8 = oracle.fit_path_i8(geno.X, geno.n, geno.y, ratio=0.05, nlambda=40)
+    finally:
+        oracle.set_threads(1)
+    for key in ("beta", "loss", "intercept", "sweeps"):
+        np.testing.assert_array_equal(omp_g[key], ref_g[key])
+        np.testing.assert_array_equal(omp_a[key], ref_a[key])
+        np.testing.assert_array_equal(omp_i8[key], ref_g[key])
+
+
 # ---------------------------------------------------------------- KKT ---
 @pytest.mark.parametrize("alpha", [1.0, 0.6])
 def test_kkt_conditions_at_every_lambda(alpha):
@@ -533,7 +598,7 @@ def test_mlp_closed_form_network():
 # ------------------------------------------------------- planted mistakes ---
 _MUTATIONS = {
     "dropped_ridge_term": ("den = 1.0 + lam * (1.0 - alpha);", "den = 1.0;"),
-    "wrong_sign_warm_start": ("double zt = acc / (double)n + old;", "double zt = acc / (double)n - old;"),
+    "wrong_sign_warm_start": ("double zt = acc / (double)D->n + old;", "double zt = acc / (double)D->n - old;"),
     "sample_sd_divisor": ("s[j] = varies ? sqrt(ss / (double)n) : 0.0;",
                           "s[j] = varies ? sqrt(ss / (double)(n - 1)) : 0.0;"),
     "bedpp_sign_flip": ("- (lmax - lam) * cstar * sstar * xtxstar[j]",
@@ -541,6 +606,9 @@ _MUTATIONS = {
     "en_bedpp_ridge_dropped": ("double q = 1.0 + lam * (1.0 - alpha);", "double q = 1.0;"),
     "mlp_relu_mask_dropped": ("d2[u] = (a2[u] > 0.0) ? dout * W3[u] : 0.0;", "d2[u] = dout * W3[u];"),
     "mlp_transposed_backprop": ("s2 += W2[u * MLP_H + h] * d2[u];", "s2 += W2[h * MLP_H + u] * d2[u];"),
+    "grid_k_over_K": ("double e = (K > 1) ? (double)k / (double)(K - 1) : 0.0;",
+                      "double e = (K > 1) ? (double)k / (double)K : 0.0;"),
+    "grid_unnormalized_power": ("lam[k] = lmax * pow(ratio, e);", "lam[k] = lmax * pow(ratio, (double)k);"),
 }
 
 
@@ -568,6 +636,8 @@ def test_planted_mistake_in_oracle_copy_is_caught(name, monkeypatch):
                 test_standardize_invariants_and_constant_columns()
             elif name.startswith("mlp_"):
                 test_mlp_gradient_matches_central_differences()
+            elif name.startswith("grid_"):
+                test_lambda_grid_closed_form()
             else:
                 test_brute_force_support_enumeration(0.5, 0.3, 6)
         except AssertionError:
