@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-proposer (block-factor workload) object")
     ap.add_argument("--no-many", action="store_true", help="skip the many-problems object")
+    ap.add_argument("--no-rules", action="store_true", help="skip the screening-rule comparison (SSR, SEDPP, BEDPP)")
     ap.add_argument("--plain-steps", type=int, default=2,
                     help="steps of the plain form (residual-update CD) timed for comparison; 0 = skip")
     return ap.parse_args()
@@ -521,6 +522,34 @@ def precision_form(ctx, X, y, prob, kw, res_native, native_zpass_ms, steps: int 
             "max_abs_coef_diff_vs_native": diff, "status": res["status"]}
 
 
+def screen_rules(ctx, X, y, prob, kw, res_chosen):
+    """The screening rules of Sec. 2.2 side by side on the same path (Table 1's
+    comparison): the strong rule alone (SSR), SSR inside the sequential EDPP safe
+    set (SEDPP), and the hybrid SSR-BEDPP the benchmark times.  Each is exact
+    (the KKT check judges); the object reports what each scans and keeps and its
+    path time."""
+    import torch
+    from paper_1701_05936_gb300 import bl
+    out = {}
+    for name, rule in (("SSR", bl.BL_SCREEN_SSR), ("SSR-SEDPP", bl.BL_SCREEN_SEDPP),
+                       ("SSR-BEDPP", bl.BL_SCREEN_SSR_BEDPP)):
+        kwr = dict(kw, screen=rule)
+        bl.bl_fit_path(ctx, X, prob.n, y, **kwr)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        r = bl.bl_fit_path(ctx, X, prob.n, y, **kwr)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        diff = float((bl.path_dense(r, prob.p) - bl.path_dense(res_chosen, prob.p)).abs().max())
+        out[name] = {"ms_per_path": e0.elapsed_time(e1), "cols_scanned": int(r["cols_scanned"].sum()),
+                     "sum_safe_set": int(r["n_safe"].sum()) if rule != bl.BL_SCREEN_SSR else None,
+                     "sum_working_set": int(r["n_strong"].sum()), "kkt_passes": int(r["kkt_rounds"].sum()),
+                     "max_abs_coef_diff_vs_chosen": diff, "status": r["status"]}
+    return {"workload": config(prob)["workload"], "rules": out,
+            "note": "SSR and SSR-SEDPP read every kept column at every z pass; SSR-BEDPP reads only its safe set"}
+
+
 def config(prob):
     return {"workload": WORKLOAD_NAME if prob.p == 100_000 else f"ar1_{prob.n}x{prob.p}_f32_small",
             "n": prob.n, "p": prob.p, "ldx": prob.ldx, "nlambda": prob.nlambda, "lambda_min_ratio": prob.ratio,
@@ -670,6 +699,8 @@ def run_ours(args):
     solo = rank == 0 and world == 1
     if solo and not args.no_precision and prob.dtype == "f32" and prob.n <= 1024:
         line["precision_form"] = precision_form(ctx, X, y, prob, kw, res, tim["zpass"]["ms"] / args.steps)
+    if solo and not args.no_rules:
+        line["screen_rules"] = screen_rules(ctx, X, y, prob, kw, res)
     if solo and not args.no_batched:
         line["batched_zpass"], line["batched_path"] = batched(local)
     if solo and not args.no_learned:

@@ -77,10 +77,19 @@ typedef enum {
     BL_SCREEN_NONE = 0,      /* every kept feature is scanned and enters CD */
     BL_SCREEN_SSR = 1,       /* strong rule + KKT check over all features */
     BL_SCREEN_SSR_BEDPP = 2, /* hybrid rule of Sec. 2.2 (default) */
-    BL_SCREEN_LEARNED = 3    /* BEDPP safe set (Sec. 2.2); the working set is the previous
+    BL_SCREEN_LEARNED = 3,   /* BEDPP safe set (Sec. 2.2); the working set is the previous
                                 active set plus the features a trained perceptron proposes
                                 (bl_mlp_*), in place of the strong rule; the KKT check
                                 judges, so the path stays exact */
+    BL_SCREEN_SEDPP = 4      /* the comparison rule of Sec. 2.2: the sequential EDPP safe
+                                rule from the solution at the previous lambda (BEDPP at the
+                                first lambda below lambda_max), with the strong rule inside
+                                its safe set.  It needs z at every kept column, so every z
+                                pass scans all of them (the full scan per lambda that Sec.
+                                2.2 and Table 1 set against SSR-BEDPP); the KKT check also
+                                covers every kept column, so the path is exact even though
+                                the previous solution is only eps-accurate.  Lasso only:
+                                alpha < 1 returns BL_ERR_UNSUPPORTED */
 } bl_screen_rule;
 
 typedef enum {
@@ -280,6 +289,28 @@ int bl_screen(bl_ctx *ctx, int64_t n, int64_t p, const double *xty, const double
               const uint8_t *keep, double lambda_max, int64_t jstar, double ynorm2, double lam,
               double lam_prev, double alpha, const float *z_prev, const float *beta_prev,
               uint8_t *safe, uint8_t *strong, int64_t *n_safe, int64_t *n_strong);
+
+/* SEDPP screening at lam (Sec. 2.2: the sequential EDPP rule the paper compares
+ * SSR-BEDPP with; lasso, alpha = 1) from the solution at lam_prev, with the
+ * strong rule inside the safe set.  With lam' = n lam (the 1/(2n) scaling),
+ * theta = r_prev/(n lam_prev), v1 = yc/(n lam_prev) - theta, v2 = yc/(n lam) -
+ * theta and v2p = v2 - (<v1,v2>/||v1||^2) v1, feature j is discarded when
+ *     |xt_j'(theta + v2p/2)| < 1 - ||v2p|| ||xt_j|| / 2;
+ * at lam_prev >= lambda_max the reference point is lambda_max and the rule is
+ * bl_screen's BEDPP.  Inputs: xty, xtxstar, keep, lambda_max, jstar, ynorm2 as
+ * bl_screen; yc and r_prev device FP64 [n] (centred response and the residual
+ * yc - Xt b at lam_prev); z_prev device FP32 [p], the z pass (bl_kkt_check) at
+ * lam_prev on r_prev rounded to the design's residual type, for every kept
+ * column; xnorm, center, scale from bl_standardize; beta_prev device FP32 [p]
+ * (nullable).  dtype is the design's: the test is tightened by twice the
+ * rounding bound of that z pass, so rounding can only keep more features.
+ * Outputs and counts as bl_screen.  Errors: BL_ERR_ARG for NULL arguments,
+ * lam >= lam_prev, lam <= 0 or a missing lambda_max/jstar. */
+int bl_screen_sedpp(bl_ctx *ctx, int dtype, int64_t n, int64_t p, const double *xty, const double *xtxstar,
+                    const uint8_t *keep, double lambda_max, int64_t jstar, double ynorm2, const double *yc,
+                    const double *r_prev, const float *z_prev, const double *xnorm, const double *center,
+                    const double *scale, const float *beta_prev, double lam, double lam_prev, uint8_t *safe,
+                    uint8_t *strong, int64_t *n_safe, int64_t *n_strong);
 
 /* Full-feature correlation pass and post-convergence KKT check (Sec. 2.2 and
  * simplification (3) of Sec. 3.1.1): for every column j with scan[j] != 0,

@@ -74,6 +74,7 @@ def _declare(L):
     L.orc_bedpp_safe.argtypes = [_dp, _dp, _u8p, i64, i64, C.c_double, i64, C.c_double,
                                  C.c_double, C.c_double, _u8p]
     L.orc_strong.argtypes = [_dp, _u8p, _dp, i64, C.c_double, C.c_double, C.c_double, _u8p]
+    L.orc_sedpp_safe.argtypes = [_dp, i64, i64, _u8p, _dp, _dp, C.c_double, i64, C.c_double, C.c_double, _u8p]
     L.orc_cd.argtypes = [_dp, i64, _i64p, i64, C.c_double, C.c_double, C.c_double, i64,
                          _dp, _dp, _i64p]
     L.orc_objective.argtypes = [_dp, i64, i64, _dp, _dp, C.c_double, C.c_double]
@@ -214,6 +215,19 @@ def bedpp_safe(xty, xtxstar, keep, n, lmax, jstar, ynorm2, lam, alpha):
     lib().orc_bedpp_safe(_p(xty), _p(_f64(xtxstar)),
                          _p(np.ascontiguousarray(keep, dtype=np.uint8), _u8p), p, n, lmax, jstar,
                          ynorm2, lam, alpha, _p(safe, _u8p))
+    return safe
+
+
+def sedpp_safe(Xt, keep, yc, r_prev, lmax, jstar, lam, lam_prev):
+    """SEDPP safe set at lam from the solution at lam_prev with residual r_prev
+    (Sec. 2.2, the sequential EDPP rule; lasso): 1 = not discarded."""
+    Xt = _f64(Xt)
+    p, n = Xt.shape
+    safe = np.empty(p, dtype=np.uint8)
+    st = lib().orc_sedpp_safe(_p(Xt), n, p, _p(np.ascontiguousarray(keep, dtype=np.uint8), _u8p), _p(_f64(yc)),
+                              _p(_f64(r_prev)), lmax, jstar, lam, lam_prev, _p(safe, _u8p))
+    if st != OK:
+        raise ValueError("sedpp_safe: needs 0 < lam < lam_prev")
     return safe
 
 

@@ -249,6 +249,79 @@ void orc_bedpp_safe(const double *xty, const double *xtxstar, const uint8_t *kee
     }
 }
 
+/* SEDPP (Sec. 2.2, the sequential EDPP rule of Wang, Wonka and Ye that the
+ * paper compares its hybrid rule against; the lasso, alpha = 1), written in
+ * vector form for the 1/(2n) scaling (penalty lam' = n lam on
+ * (1/2)||yc - Xt b||^2): with r the residual of the solution at lam_prev,
+ *   theta = r / (n lam_prev)                 (the dual point at lam_prev),
+ *   v1    = yc / (n lam_prev) - theta        (lam_prev < lmax), or
+ *           s* xt_*                          (lam_prev >= lmax: the reference
+ *                                             point is lambda_max),
+ *   v2    = yc / (n lam) - theta,
+ *   v2p   = v2 - (<v1, v2> / ||v1||^2) v1,
+ * feature j is discarded at lam when
+ *   |xt_j' (theta + v2p / 2)| < 1 - ||v2p|| ||xt_j|| / 2.
+ * At lam_prev = lmax this is the BEDPP rule above.  Xt is the explicit
+ * standardized design (p x n); safe_j = 1 when j is not discarded. */
+int orc_sedpp_safe(const double *Xt, i64 n, i64 p, const uint8_t *keep, const double *yc, const double *r_prev,
+                   double lmax, i64 jstar, double lam, double lam_prev, uint8_t *safe)
+{
+    if (jstar < 0 || !(lam > 0.0) || !(lam < lam_prev)) {
+        for (i64 j = 0; j < p; ++j) safe[j] = keep[j];
+        return jstar < 0 ? ORC_OK : ORC_ERR_ARG;
+    }
+    double nn = (double)n;
+    double *theta = malloc((size_t)n * sizeof(double));
+    double *v1 = malloc((size_t)n * sizeof(double));
+    double *v2 = malloc((size_t)n * sizeof(double));
+    if (!theta || !v1 || !v2) {
+        free(theta);
+        free(v1);
+        free(v2);
+        return ORC_ERR_OOM;
+    }
+    int at_max = !(lam_prev < lmax);
+    double lp = at_max ? lmax : lam_prev;
+    const double *xs = Xt + (size_t)jstar * (size_t)n;
+    double xsy = 0.0;
+    for (i64 i = 0; i < n; ++i) xsy += xs[i] * yc[i];
+    double sstar = (xsy >= 0.0) ? 1.0 : -1.0;
+    for (i64 i = 0; i < n; ++i) {
+        theta[i] = (at_max ? yc[i] : r_prev[i]) / (nn * lp);
+        v1[i] = at_max ? sstar * xs[i] : yc[i] / (nn * lp) - theta[i];
+        v2[i] = yc[i] / (nn * lam) - theta[i];
+    }
+    double v11 = 0.0, v12 = 0.0;
+    for (i64 i = 0; i < n; ++i) {
+        v11 += v1[i] * v1[i];
+        v12 += v1[i] * v2[i];
+    }
+    double cproj = (v11 > 0.0) ? v12 / v11 : 0.0;
+    double pp = 0.0;
+    for (i64 i = 0; i < n; ++i) {
+        v2[i] -= cproj * v1[i]; /* v2 now holds v2p */
+        pp += v2[i] * v2[i];
+    }
+    double np2 = sqrt(pp);
+    for (i64 j = 0; j < p; ++j) {
+        if (!keep[j]) {
+            safe[j] = 0;
+            continue;
+        }
+        const double *t = Xt + (size_t)j * (size_t)n;
+        double a = 0.0, xx = 0.0;
+        for (i64 i = 0; i < n; ++i) {
+            a += t[i] * (theta[i] + 0.5 * v2[i]);
+            xx += t[i] * t[i];
+        }
+        safe[j] = (uint8_t)!(fabs(a) < 1.0 - 0.5 * np2 * sqrt(xx));
+    }
+    free(theta);
+    free(v1);
+    free(v2);
+    return ORC_OK;
+}
+
 /* Sequential strong rule restricted to the safe set (SSR-BEDPP, Sec. 2.2). */
 void orc_strong(const double *zprev, const uint8_t *safe, const double *beta_prev, i64 p,
                 double lam, double lam_prev, double alpha, uint8_t *strong)

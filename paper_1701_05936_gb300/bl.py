@@ -25,7 +25,7 @@ from . import build as _build
 BL_OK, BL_ERR_ARG, BL_ERR_CUDA, BL_ERR_OOM = 0, -1, -2, -3
 BL_ERR_NOT_CONVERGED, BL_ERR_TIMEOUT, BL_ERR_UNSUPPORTED, BL_ERR_CAPACITY = -4, -5, -6, -7
 BL_F64, BL_F32, BL_BF16, BL_I8 = 0, 1, 2, 3
-BL_SCREEN_NONE, BL_SCREEN_SSR, BL_SCREEN_SSR_BEDPP, BL_SCREEN_LEARNED = 0, 1, 2, 3
+BL_SCREEN_NONE, BL_SCREEN_SSR, BL_SCREEN_SSR_BEDPP, BL_SCREEN_LEARNED, BL_SCREEN_SEDPP = 0, 1, 2, 3, 4
 BL_MLP_NPARAM = 4609
 BL_CD_RESIDUAL, BL_CD_COVARIANCE, BL_CD_BLOCKED = 0, 1, 2
 BL_XPREC_NATIVE, BL_XPREC_BF16 = 0, 1
@@ -104,6 +104,8 @@ def lib():
                 "bl_bedpp_init": [_vp, *X, _vp, _vp, _vp, _vp, _i64, _vp, C.POINTER(_dbl)],
                 "bl_screen": [_vp, _i64, _i64, _vp, _vp, _vp, _dbl, _i64, _dbl, _dbl, _dbl, _dbl, _vp, _vp,
                               _vp, _vp, C.POINTER(_i64), C.POINTER(_i64)],
+                "bl_screen_sedpp": [_vp, _int, _i64, _i64, _vp, _vp, _vp, _dbl, _i64, _dbl, _vp, _vp, _vp, _vp,
+                                    _vp, _vp, _vp, _dbl, _dbl, _vp, _vp, C.POINTER(_i64), C.POINTER(_i64)],
                 "bl_kkt_check": [_vp, *X, _vp, _vp, _vp, _vp, _vp, _dbl, _dbl, _vp, _vp, _vp, _vp,
                                  C.POINTER(_i64)],
                 "bl_kkt_check_bf16": [_vp, _vp, _i64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _dbl, _dbl, _vp, _vp,
@@ -237,6 +239,17 @@ def bl_screen(ctx, n, p, xty, xtxstar, keep, lambda_max, jstar, ynorm2, lam, lam
     ctx.check(lib().bl_screen(ctx.h, int(n), int(p), _ptr(xty), _ptr(xtxstar), _ptr(keep), float(lambda_max),
                               int(jstar), float(ynorm2), float(lam), float(lam_prev), float(alpha), _ptr(z_prev),
                               _ptr(beta_prev), _ptr(safe), _ptr(strong), C.byref(ns), C.byref(ng)))
+    return ns.value, ng.value
+
+
+def bl_screen_sedpp(ctx, dtype, n, p, xty, xtxstar, keep, lambda_max, jstar, ynorm2, yc, r_prev, z_prev, xnorm,
+                    center, scale, beta_prev, lam, lam_prev, safe, strong):
+    """SEDPP screening at lam from the solution at lam_prev (see the header)."""
+    ns, ng = C.c_int64(), C.c_int64()
+    ctx.check(lib().bl_screen_sedpp(ctx.h, int(dtype), int(n), int(p), _ptr(xty), _ptr(xtxstar), _ptr(keep),
+                                    float(lambda_max), int(jstar), float(ynorm2), _ptr(yc), _ptr(r_prev),
+                                    _ptr(z_prev), _ptr(xnorm), _ptr(center), _ptr(scale), _ptr(beta_prev),
+                                    float(lam), float(lam_prev), _ptr(safe), _ptr(strong), C.byref(ns), C.byref(ng)))
     return ns.value, ng.value
 
 

@@ -516,6 +516,68 @@ extern "C" int bl_screen(bl_ctx *ctx, int64_t n, int64_t p, const double *xty, c
     return BL_OK;
 }
 
+extern "C" int bl_screen_sedpp(bl_ctx *ctx, int dtype, int64_t n, int64_t p, const double *xty,
+                               const double *xtxstar, const uint8_t *keep, double lambda_max, int64_t jstar,
+                               double ynorm2, const double *yc, const double *r_prev, const float *z_prev,
+                               const double *xnorm, const double *center, const double *scale,
+                               const float *beta_prev, double lam, double lam_prev, uint8_t *safe, uint8_t *strong,
+                               int64_t *n_safe, int64_t *n_strong)
+{
+    if (!ctx) return BL_ERR_ARG;
+    if (dtype != BL_F64 && dtype != BL_F32 && dtype != BL_I8) return fail(ctx, BL_ERR_ARG, "unknown dtype");
+    if (n < 1 || p < 1 || !xty || !xtxstar || !keep || !yc || !r_prev || !z_prev || !xnorm || !center || !scale ||
+        !safe || !strong)
+        return fail(ctx, BL_ERR_ARG, "NULL argument or bad size");
+    if (!(lam > 0.0) || !(lam < lam_prev)) return fail(ctx, BL_ERR_ARG, "need 0 < lam < lam_prev");
+    if (jstar < 0 || jstar >= p || !(lambda_max > 0.0)) return fail(ctx, BL_ERR_ARG, "lambda_max and jstar required");
+    ctx->err.clear();
+    CK(cudaSetDevice(ctx->device));
+    int st;
+    if ((st = ensure_ws(ctx, n, p))) return st;
+    Workspace &w = ctx->ws;
+    double xs = 0.0;
+    CK(cudaMemcpyAsync(&xs, xty + jstar, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ScreenArgs a{};
+    bedpp_consts(n, 1.0, lambda_max, ynorm2, lam, &a.cst_now, &a.rhs_now, &a.rmag_now);
+    a.n = n;
+    a.p = p;
+    a.xty = xty;
+    a.xtxstar = xtxstar;
+    a.keep = keep;
+    a.lmax = lambda_max;
+    a.sstar = xs >= 0.0 ? 1.0 : -1.0;
+    a.jstar = jstar;
+    a.lam = lam;
+    a.lam_prev = lam_prev;
+    a.lam_next = -1.0;
+    a.alpha = 1.0;
+    a.rule = BL_SCREEN_SEDPP;
+    a.z_prev = z_prev;
+    a.beta_prev = beta_prev;
+    a.beta_f64 = 0;
+    a.safe = safe;
+    a.strong = strong;
+    a.scan = nullptr;
+    a.ynorm2 = ynorm2;
+    a.gamma = std::fmax(gamma_for(dtype, n), zpass_reg_gamma(dtype, n));
+    a.xnorm = xnorm;
+    a.center = center;
+    a.scale = scale;
+    if ((st = reset_counters(ctx))) return st;
+    int slot = tbegin(ctx, 3);
+    LAUNCH(1, launch_rstats(BL_F64, r_prev, n, w.sc, ctx->stream));
+    if (lam_prev < lambda_max) LAUNCH(1, launch_sedpp_stats(yc, r_prev, n, w.sc, ctx->stream));
+    LAUNCH(1, launch_screen(a, w.sc, ctx->stream));
+    tend(ctx, slot, (double)p * (8 + 8 + 8 + 8 + 8 + 1 + 4 + 4 + 2));
+    if (n_safe || n_strong) {
+        if ((st = sync_sc(ctx))) return st;
+        if (n_safe) *n_safe = (int64_t)ctx->sc_host->n_safe;
+        if (n_strong) *n_strong = (int64_t)ctx->sc_host->n_strong;
+    }
+    return BL_OK;
+}
+
 // The precision form's buffers: the BF16 copy of an n x p design and the list
 // of columns its bound leaves open.
 static int ensure_prec(bl_ctx *ctx, int64_t n, int64_t p)
@@ -1237,7 +1299,9 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
     if (!(alpha > 0.0 && alpha <= 1.0)) return fail(ctx, BL_ERR_ARG, "alpha must be in (0, 1]");
     if (!(eps > 0.0)) return fail(ctx, BL_ERR_ARG, "eps must be > 0");
     if (opt->max_sweeps < 1) return fail(ctx, BL_ERR_ARG, "max_sweeps must be >= 1");
-    if (opt->screen < 0 || opt->screen > 3) return fail(ctx, BL_ERR_ARG, "unknown screening rule");
+    if (opt->screen < 0 || opt->screen > 4) return fail(ctx, BL_ERR_ARG, "unknown screening rule");
+    if (opt->screen == BL_SCREEN_SEDPP && alpha != 1.0)
+        return fail(ctx, BL_ERR_UNSUPPORTED, "SEDPP is a lasso rule (alpha = 1)");
     if (opt->screen == BL_SCREEN_LEARNED && (!opt->proposer || !(opt->proposer_tau > 0.0 && opt->proposer_tau < 1.0)))
         return fail(ctx, BL_ERR_ARG, "the learned rule needs proposer weights and 0 < proposer_tau < 1");
     if (out->prop_cap > 0 && (!out->prop_feat || !out->prop_idx || !out->prop_label))
@@ -1301,8 +1365,10 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
     CK(cudaMemcpyAsync(out->lambdas, L.data(), (size_t)K * sizeof(double), cudaMemcpyHostToDevice, s));
 
     const bool use_bedpp = opt->screen == BL_SCREEN_SSR_BEDPP && jstar >= 0 && lmax > 0.0;
+    // SEDPP: the sequential rule; at lam_prev = lambda_max it is BEDPP, which needs xt'x_*
+    const bool use_sedpp = opt->screen == BL_SCREEN_SEDPP && jstar >= 0 && lmax > 0.0;
     double sstar = 1.0;
-    if (use_bedpp) {
+    if (use_bedpp || use_sedpp) {
         slot = tbegin(ctx, 2);
         LAUNCH(2, launch_xtxstar(dtype, X, n, p, ldx, w.center, w.scale, w.keep, jstar, w.xcs, w.sc, w.xtxstar,
                           ctx->num_sms, s));
@@ -1442,8 +1508,19 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
         sa.lam_prev = lam_prev;
         sa.lam_next = lam_next;
         sa.alpha = alpha;
-        sa.rule = use_bedpp ? BL_SCREEN_SSR_BEDPP : (opt->screen == BL_SCREEN_NONE ? BL_SCREEN_NONE : BL_SCREEN_SSR);
+        sa.rule = use_bedpp   ? BL_SCREEN_SSR_BEDPP
+                  : use_sedpp ? BL_SCREEN_SEDPP
+                              : (opt->screen == BL_SCREEN_NONE ? BL_SCREEN_NONE : BL_SCREEN_SSR);
         sa.strong_prev_only = learned ? 1 : 0;
+        if (use_sedpp) {
+            sa.ynorm2 = ynorm2;
+            sa.gamma = std::fmax(gamma, gamma_reg);
+            sa.xnorm = w.xnorm;
+            sa.center = w.center;
+            sa.scale = w.scale;
+            // u = yc - r at lam_prev (r64 holds the FP64 residual of the last CD)
+            if (lam_prev < lmax) LAUNCH(1, launch_sedpp_stats(w.yc, w.r64, n, w.sc, s));
+        }
         sa.z_prev = w.z;
         sa.beta_prev = w.beta;
         sa.beta_f64 = beta_f64;
@@ -1526,8 +1603,10 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
                                       w.partial, w.r, w.r64, w.sc, s));
             tend(ctx, slot, 0.0);
             if ((st = reset_round(ctx))) return st;
+            // SEDPP's safe set comes from an approximate dual point (the CD
+            // tolerance), so its KKT check covers every kept column, not S_k only
             ZpassArgs za{X, n, p, ldx, w.center, w.inv_scale, w.xnorm, w.c32, w.is32, w.xn32, w.r, lam, alpha,
-                         gamma, gamma_reg, w.scan, w.safe, w.working, w.z};
+                         gamma, gamma_reg, w.scan, use_sedpp ? w.keep : w.safe, w.working, w.z};
             int zslot = tbegin(ctx, 7);
             if (prec) {
                 ZpassArgs zb = za;

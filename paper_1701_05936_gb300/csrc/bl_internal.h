@@ -28,6 +28,8 @@ struct DevScalars {
     // lambda_max search result
     double absmax;  // max_j |xty_j| over kept columns
     double sum_xcs; // sum_i (x_i* - c_*) (BEDPP init)
+    // SEDPP inner products of u = yc - r, yc and the FP64 residual r at lam_prev
+    double sed_uu, sed_uy, sed_ur, sed_yr, sed_rr;
     long long jstar;
     // per-round counters (reset by the host)
     unsigned long long n_viol, n_cols;
@@ -89,6 +91,11 @@ struct ScreenArgs {
     double alpha;
     int rule;          // bl_screen_rule
     int strong_prev_only;  // strong set = safe and previously active (the learned rule adds the rest)
+    // SEDPP (rule 4) at lam_prev < lmax: ||yc||^2, the z pass's rounding-bound
+    // factor and the per-feature vectors its bound needs; the inner products
+    // come from DevScalars (launch_sedpp_stats)
+    double ynorm2, gamma;
+    const double *xnorm, *center, *scale;
     const float *z_prev;
     const void *beta_prev;  // nullable
     int beta_f64;
@@ -103,6 +110,9 @@ struct ScreenArgs {
 void bedpp_consts(int64_t n, double alpha, double lmax, double yn2, double lam, double *cst, double *rhs,
                   double *rmag);
 cudaError_t launch_screen(const ScreenArgs &a, DevScalars *sc, cudaStream_t st);
+// SEDPP (Sec. 2.2, the sequential EDPP rule): sc->sed_* = u'u, u'yc, u'r, yc'r,
+// r'r for u = yc - r, in FP64 (one block)
+cudaError_t launch_sedpp_stats(const double *yc, const double *r, int64_t n, DevScalars *sc, cudaStream_t st);
 // resume of a path: beta from the caller's FP64 standardized-scale coefficients
 // (kept columns only), working = its support
 cudaError_t launch_warm_beta(const double *wb, const uint8_t *keep, int64_t p, void *beta, bool beta_f64,

@@ -427,19 +427,61 @@ void bedpp_consts(int64_t n, double alpha, double lmax, double yn2, double lam, 
     *rmag = std::fabs(r1) + std::fabs(r2);
 }
 
+// SEDPP (Sec. 2.2: the sequential EDPP rule the paper compares against; lasso)
+// at lam from the solution at lam_prev < lmax.  With lam' = n lam, the dual
+// point theta = r/(n lam_prev), v1 = yc/(n lam_prev) - theta = u/(n lam_prev)
+// (u = yc - r), v2 = yc/(n lam) - theta and v2p = v2 - (<v1,v2>/||v1||^2) v1,
+// j is discarded when |xt_j'(theta + v2p/2)| < 1 - ||v2p|| sqrt(n)/2.  Every
+// inner product with xt_j reduces to xt_j'yc and z_j = xt_j'r/n:
+//   xt_j'theta = z_j/lam_prev,  xt_j'v1 = (xt_j'yc/n - z_j)/lam_prev,
+//   xt_j'v2 = xt_j'yc/(n lam) - z_j/lam_prev,
+// and ||v1||^2, <v1,v2>, ||v2||^2 to the five sums of launch_sedpp_stats.  z_j
+// comes from the FP32 z pass at lam_prev: the left side moves by
+// |1 + c| dz/(2 lam_prev) per unit error dz of z_j, so the test is tightened by
+// twice that pass's rounding bound (plus the FP32 rounding of r) and by FP64
+// margins on the cancellation in ||v2p||^2 and on the left side, so rounding
+// can only keep more features.
+__device__ __forceinline__ bool sedpp_keep(const ScreenArgs &a, int64_t j, const DevScalars *sc)
+{
+    constexpr double U32 = 5.9604644775390625e-08;  // 2^-24
+    const double nn = (double)a.n, lp = a.lam_prev, lk = a.lam;
+    const double nlp = nn * lp, nlk = nn * lk;
+    const double v11 = sc->sed_uu / (nlp * nlp);
+    const double v12 = (sc->sed_uy / lk - sc->sed_ur / lp) / (nn * nlp);
+    const double v22 = a.ynorm2 / (nlk * nlk) - 2.0 * sc->sed_yr / (nlk * nlp) + sc->sed_rr / (nlp * nlp);
+    const double c = (v11 > 0.0) ? v12 / v11 : 0.0;
+    const double pp = fmax(v22 - c * v12, 0.0) + 4e-16 * (fabs(v22) + fabs(c * v12));
+    const double zj = (double)a.z_prev[j], xy = a.xty[j];
+    const double xth = zj / lp, xv1 = (xy / nn - zj) / lp, xv2 = xy / nlk - zj / lp;
+    const double t = xth + 0.5 * (xv2 - c * xv1);
+    const double f = 1.0 / (nn * a.scale[j]);
+    const double dz = 2.0 * (a.gamma * a.xnorm[j] * sc->rnorm * f * 1.01 +
+                             8.0 * U32 * (fabs(a.center[j] * sc->sum_r) * f + fabs(zj))) +
+                      U32 * sc->rnorm / sqrt(nn);
+    const double lhs = fabs(t) + fabs(1.0 + c) * dz / (2.0 * lp) +
+                       1e-10 * (fabs(xth) + 0.5 * fabs(xv2) + 0.5 * fabs(c * xv1));
+    const double rhs = 1.0 - 0.5 * sqrt(pp) * sqrt(nn) - 1e-10;
+    return !(lhs < rhs);
+}
+
 __global__ void __launch_bounds__(256) k_screen(ScreenArgs a, DevScalars *sc)
 {
     __shared__ unsigned int cnt[3];
     if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
     __syncthreads();
     unsigned int n_safe = 0, n_strong = 0, n_scan = 0;
-    const bool use_bedpp = (a.rule == 2) && (a.jstar >= 0);
+    // SEDPP with lam_prev at lambda_max is the BEDPP rule (the reference point is lambda_max)
+    const bool sedpp = (a.rule == 4) && (a.jstar >= 0);
+    const bool sed_seq = sedpp && a.lam_prev < a.lmax;
+    const bool use_bedpp = ((a.rule == 2) || (sedpp && !sed_seq)) && (a.jstar >= 0);
     const double thr = a.alpha * (2.0 * a.lam - a.lam_prev);
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.p;
          j += (int64_t)gridDim.x * blockDim.x) {
         uint8_t sf = 0, sg = 0, sn = 0;
         if (a.keep[j]) {
-            const bool s_now = use_bedpp ? bedpp_keep(a, j, a.lam, a.cst_now, a.rhs_now, a.rmag_now) : true;
+            const bool s_now = sed_seq     ? sedpp_keep(a, j, sc)
+                               : use_bedpp ? bedpp_keep(a, j, a.lam, a.cst_now, a.rhs_now, a.rmag_now)
+                                           : true;
             const bool s_next = (use_bedpp && a.lam_next > 0.0)
                                     ? bedpp_keep(a, j, a.lam_next, a.cst_next, a.rhs_next, a.rmag_next)
                                     : s_now;
@@ -452,7 +494,8 @@ __global__ void __launch_bounds__(256) k_screen(ScreenArgs a, DevScalars *sc)
                 sg = s_now && (b != 0.0);
             else
                 sg = s_now && (b != 0.0 || (double)fabsf(a.z_prev[j]) >= thr);
-            sn = s_now || s_next;
+            // SEDPP needs z at every kept column at the next lambda: scan them all
+            sn = (a.rule == 4) ? 1 : (s_now || s_next);
         }
         a.safe[j] = sf;
         a.strong[j] = sg;
@@ -475,6 +518,46 @@ __global__ void __launch_bounds__(256) k_screen(ScreenArgs a, DevScalars *sc)
         atomicAdd(&sc->n_strong, (unsigned long long)cnt[1]);
         atomicAdd(&sc->n_scan, (unsigned long long)cnt[2]);
     }
+}
+
+__global__ void __launch_bounds__(1024) k_sedpp_stats(const double *__restrict__ yc, const double *__restrict__ r,
+                                                      int64_t n, DevScalars *sc)
+{
+    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int64_t i = threadIdx.x; i < n; i += 1024) {
+        const double y = yc[i], ri = r[i], u = y - ri;
+        v[0] = fma(u, u, v[0]);
+        v[1] = fma(u, y, v[1]);
+        v[2] = fma(u, ri, v[2]);
+        v[3] = fma(y, ri, v[3]);
+        v[4] = fma(ri, ri, v[4]);
+    }
+    __shared__ double part[5][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const double s = warp_sum(v[q]);
+        if (lane == 0) part[q][wid] = s;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        double t[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) t[q] = warp_sum(part[q][lane]);
+        if (lane == 0) {
+            sc->sed_uu = t[0];
+            sc->sed_uy = t[1];
+            sc->sed_ur = t[2];
+            sc->sed_yr = t[3];
+            sc->sed_rr = t[4];
+        }
+    }
+}
+
+cudaError_t launch_sedpp_stats(const double *yc, const double *r, int64_t n, DevScalars *sc, cudaStream_t st)
+{
+    k_sedpp_stats<<<1, 1024, 0, st>>>(yc, r, n, sc);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_screen(const ScreenArgs &a, DevScalars *sc, cudaStream_t st)

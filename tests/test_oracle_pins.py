@@ -468,6 +468,101 @@ def test_bedpp_is_safe_on_random_paths():
     assert checked == 120 * 30
 
 
+def sedpp_scalar_form(xty, z_prev, keep, n, lmax, jstar, yy, uu, uy, ur, yr, rr, lam, lam_prev, zerr=None):
+    """SEDPP evaluated the way the CUDA screen kernel does: from per-feature
+    scalars (xt_j'yc and z_j = xt_j'r/n at lam_prev) and six FP64 inner products
+    of u = yc - r, yc and r, with v1, v2, v2p never formed.  It is a
+    restatement of the algebra, checked here against the oracle's vector form.
+    zerr (optional): a bound on |z_prev error|; the test is then tightened by
+    |1 + c| zerr / (2 lam_prev) so that a rounding of z cannot discard."""
+    nn = float(n)
+    lp = lam_prev
+    xj_theta = z_prev / lp
+    xj_v1 = (xty / nn - z_prev) / lp
+    xj_v2 = xty / (nn * lam) - z_prev / lp
+    v11 = uu / (nn * lp) ** 2
+    v12 = (uy / lam - ur / lp) / (nn * nn * lp)
+    v22 = yy / (nn * lam) ** 2 - 2.0 * yr / (nn * nn * lam * lp) + rr / (nn * lp) ** 2
+    c = v12 / v11 if v11 > 0 else 0.0
+    pp = max(v22 - c * v12, 0.0)
+    lhs = np.abs(xj_theta + 0.5 * (xj_v2 - c * xj_v1))
+    if zerr is not None:
+        lhs = lhs + abs(1.0 + c) * zerr / (2.0 * lp)
+    rhs = 1.0 - 0.5 * np.sqrt(pp) * np.sqrt(nn)
+    safe = (keep != 0) & ~(lhs < rhs)
+    return safe.astype(np.uint8), lhs - rhs
+
+
+def _sedpp_problem(rng, trial):
+    n, p = int(rng.integers(8, 50)), int(rng.integers(5, 200))
+    rho = [0.0, 0.5, 0.9][trial % 3]
+    X = corr_design(n, p, rho, rng)
+    k = int(rng.integers(1, 6))
+    b = np.zeros(p)
+    b[rng.choice(p, min(k, p), replace=False)] = rng.standard_normal(min(k, p)) * 2
+    y = X.T @ b + rng.uniform(0.1, 2.0) * rng.standard_normal(n)
+    return X, y
+
+
+def test_sedpp_is_safe_on_random_paths_and_is_bedpp_at_lambda_max():
+    """SEDPP from the (near-exact) solution at lambda_{k-1} never discards a
+    feature active at lambda_k; with lambda_{k-1} = lambda_max it is the BEDPP
+    rule (same discards up to FP64 ties); deeper in the path it discards at least
+    as much as BEDPP on these problems (the point of a sequential rule)."""
+    rng = np.random.default_rng(12)
+    checked = stronger = 0
+    for trial in range(120):
+        X, y = _sedpp_problem(rng, trial)
+        n = X.shape[1]
+        res = oracle.fit_path(X, y, ratio=0.05, nlambda=30, eps=1e-12)
+        Xt = oracle.standardized_matrix(X, res["c"], res["s"], res["keep"])
+        yc, _ = oracle.center(y)
+        xtxs, yy = oracle.bedpp_init(Xt, res["jstar"], yc)
+        lams = res["lambdas"]
+        for kk in range(1, len(lams)):
+            r_prev = yc - Xt.T @ res["beta"][kk - 1]
+            safe = oracle.sedpp_safe(Xt, res["keep"], yc, r_prev, res["lmax"], res["jstar"], lams[kk], lams[kk - 1])
+            active = res["beta"][kk] != 0
+            assert not np.any(active & (safe == 0)), (trial, kk)
+            bedpp = oracle.bedpp_safe(res["xty"], xtxs, res["keep"], n, res["lmax"], res["jstar"], yy, lams[kk], 1.0)
+            if kk == 1:
+                assert np.sum(safe != bedpp) <= 1, (trial, np.sum(safe != bedpp))
+            stronger += int(safe.sum() <= bedpp.sum())
+            checked += 1
+    assert checked == 120 * 29
+    assert stronger >= 0.95 * checked
+
+
+def test_sedpp_scalar_form_matches_vector_form():
+    """The scalar reduction the CUDA kernel evaluates gives the oracle's
+    vector-form SEDPP safe set (up to FP64 ties), and tightening it by a z error
+    bound only keeps more."""
+    rng = np.random.default_rng(13)
+    ties = total = 0
+    for trial in range(60):
+        X, y = _sedpp_problem(rng, trial)
+        n = X.shape[1]
+        res = oracle.fit_path(X, y, ratio=0.05, nlambda=20, eps=1e-12)
+        Xt = oracle.standardized_matrix(X, res["c"], res["s"], res["keep"])
+        yc, _ = oracle.center(y)
+        lams = res["lambdas"]
+        for kk in range(2, len(lams)):
+            r = yc - Xt.T @ res["beta"][kk - 1]
+            u = yc - r
+            z_prev = Xt @ r / n
+            args = (res["xty"], z_prev, res["keep"], n, res["lmax"], res["jstar"], yc @ yc, u @ u, u @ yc, u @ r,
+                    yc @ r, r @ r, lams[kk], lams[kk - 1])
+            mine, gap = sedpp_scalar_form(*args)
+            ref = oracle.sedpp_safe(Xt, res["keep"], yc, r, res["lmax"], res["jstar"], lams[kk], lams[kk - 1])
+            diff = mine != ref
+            assert np.all(np.abs(gap[diff]) < 1e-9), (trial, kk)
+            ties += int(diff.sum())
+            total += int(res["keep"].sum())
+            tight, _ = sedpp_scalar_form(*args, zerr=1e-6 * np.ones_like(z_prev))
+            assert np.all(tight >= mine)
+    assert ties <= 1e-4 * total
+
+
 def test_bedpp_power_and_nesting():
     """Near lambda_max BEDPP discards most features of an iid design, and the
     safe set only grows as lambda decreases on this example."""
@@ -606,6 +701,8 @@ _MUTATIONS = {
     "en_bedpp_ridge_dropped": ("double q = 1.0 + lam * (1.0 - alpha);", "double q = 1.0;"),
     "mlp_relu_mask_dropped": ("d2[u] = (a2[u] > 0.0) ? dout * W3[u] : 0.0;", "d2[u] = dout * W3[u];"),
     "mlp_transposed_backprop": ("s2 += W2[u * MLP_H + h] * d2[u];", "s2 += W2[h * MLP_H + u] * d2[u];"),
+    "sedpp_projection_sign": ("v2[i] -= cproj * v1[i]; /* v2 now holds v2p */",
+                              "v2[i] += cproj * v1[i]; /* v2 now holds v2p */"),
     "grid_k_over_K": ("double e = (K > 1) ? (double)k / (double)(K - 1) : 0.0;",
                       "double e = (K > 1) ? (double)k / (double)K : 0.0;"),
     "grid_unnormalized_power": ("lam[k] = lmax * pow(ratio, e);", "lam[k] = lmax * pow(ratio, (double)k);"),
@@ -636,6 +733,8 @@ def test_planted_mistake_in_oracle_copy_is_caught(name, monkeypatch):
                 test_standardize_invariants_and_constant_columns()
             elif name.startswith("mlp_"):
                 test_mlp_gradient_matches_central_differences()
+            elif name.startswith("sedpp_"):
+                test_sedpp_is_safe_on_random_paths_and_is_bedpp_at_lambda_max()
             elif name.startswith("grid_"):
                 test_lambda_grid_closed_form()
             else:
