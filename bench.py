@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-proposer (block-factor workload) object")
     ap.add_argument("--no-many", action="store_true", help="skip the many-problems object")
+    ap.add_argument("--no-genotype", action="store_true",
+                    help="skip the full-size genotype (int8, 5000 x 500,000) path object")
     ap.add_argument("--no-rules", action="store_true", help="skip the screening-rule comparison (SSR, SEDPP, BEDPP)")
     ap.add_argument("--plain-steps", type=int, default=2,
                     help="steps of the plain form (residual-update CD) timed for comparison; 0 = skip")
@@ -550,6 +552,67 @@ def screen_rules(ctx, X, y, prob, kw, res_chosen):
             "note": "SSR and SSR-SEDPP read every kept column at every z pass; SSR-BEDPP reads only its safe set"}
 
 
+def genotype_path(local: int, steps: int = 2, oracle_lambdas: int = 8):
+    """The genotype-coded path at full size: 5000 x 500,000 int8 codes {0,1,2}
+    (MAF ~ U[0.05, 0.5], 50 causal effects, h2 = 0.3), 100 lambdas to 0.1
+    lambda_max, SSR-BEDPP.  p * ldx = 2.56e9 elements, beyond 2^31, so element
+    offsets into the design are 64-bit.  The z pass reads the codes at 1 byte per element.
+    Reports paths/s, the z pass's achieved GB/s against the HBM peak, CD's cost
+    per update, and the largest coefficient difference from the FP64 oracle
+    over the first `oracle_lambdas` lambdas (the oracle's int8 form on all host
+    cores; a full oracle path at this size takes hours)."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1701_05936_gb300 import bl, synth
+    dev = torch.device("cuda", local)
+    prob = synth.workload(3)
+    X = torch.from_numpy(prob.X).to(dev)
+    y = torch.from_numpy(prob.y).to(dev)
+    ctx = bl.Context(local)
+    kw = dict(alpha=prob.alpha, ratio=prob.ratio, nlambda=prob.nlambda, eps=prob.eps, cd_mode=bl.BL_CD_BLOCKED)
+    res = bl.bl_fit_path(ctx, X, prob.n, y, **kw)
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(steps):
+        res = bl.bl_fit_path(ctx, X, prob.n, y, **kw)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    t = ctx.timing()
+    ctx.set_timing(False)
+    zp, cd = t["zpass"], t["cd"]
+    peaks, which = measured_peaks()
+    gbs = zp["bytes"] / (zp["ms"] / 1e3) / 1e9 if zp["ms"] > 0 else None
+    B = bl.path_dense(res, prob.p)[:oracle_lambdas].cpu().numpy()
+    ctx.close()
+    del X
+    cpu = host_cpu()
+    used = oracle.set_threads(cpu["usable"] or 1)
+    t0 = time.perf_counter()
+    o = oracle.fit_path_i8(prob.X, prob.n, prob.y, alpha=prob.alpha, ratio=prob.ratio, nlambda=prob.nlambda,
+                           eps=prob.eps, n_solve=oracle_lambdas)
+    ot = time.perf_counter() - t0
+    oracle.set_threads(1)
+    diff = float(np.abs(B - o["beta"]).max())
+    same = bool(np.array_equal(B != 0, o["beta"] != 0))
+    return {"workload": f"genotype int8 {prob.n}x{prob.p} (ldx {prob.ldx}; p*ldx = {prob.p * prob.ldx:.3g} > 2^31), "
+                        f"MAF U[0.05,0.5], 50 causal, h2 0.3, {prob.nlambda} lambdas to {prob.ratio} lambda_max, "
+                        "SSR-BEDPP",
+            "value": 1e3 / ms, "unit": "paths/s", "ms_per_path": ms, "steps": steps,
+            "zpass": {"ms_per_path": zp["ms"] / steps, "launches_per_path": zp["launches"] / steps,
+                      "achieved_gbs": gbs, "peak": peaks["hbm_gbs"], "frac": (gbs / peaks["hbm_gbs"]) if gbs else None,
+                      "peak_source": f"{which} hbm_gbs", "bytes_per_element": 1},
+            "cd": {"ms_per_path": cd["ms"] / steps, "ns_per_update": 1e6 * cd["ms"] / max(1, t["cd_updates"]),
+                   "form": "residual-update CD, one CTA (int8 design, n = 5000)"},
+            "active_at_lambda_min": int(res["n_active"][-1]),
+            "oracle": {"lambdas_compared": oracle_lambdas, "max_abs_coef_diff": diff, "same_active_sets": same,
+                       "threads": used, "seconds": ot},
+            "status": res["status"]}
+
+
 def config(prob):
     return {"workload": WORKLOAD_NAME if prob.p == 100_000 else f"ar1_{prob.n}x{prob.p}_f32_small",
             "n": prob.n, "p": prob.p, "ldx": prob.ldx, "nlambda": prob.nlambda, "lambda_min_ratio": prob.ratio,
@@ -662,7 +725,7 @@ def run_ours(args):
     cd = tim["cd"]
     nlam = prob.nlambda - 1  # lambda_max itself needs no descent
     pair = mode == bl.BL_CD_BLOCKED and prob.dtype == "f32" and prob.n <= 1024
-    cd_info = {"bound": "latency (sequential coordinates; chain and dots on a 3-SM cluster)" if pair
+    cd_info = {"bound": "latency (sequential coordinates; chain and dots on a 5-SM cluster)" if pair
                else "latency (one CTA, sequential coordinates)",
                "updates_per_step": tim["cd_updates"] / args.steps,
                "ns_per_update": 1e6 * cd["ms"] / max(1, tim["cd_updates"]),
@@ -687,8 +750,9 @@ def run_ours(args):
         "value_excl_init": {"value": value_excl_init, "unit": "paths/s",
                             "excludes": "standardization, lambda_max and BEDPP init (one-time per design)"},
         "gpu_launches": int(tim["kernel_launches"]), "clocks": clk, "cd": cd_info,
-        "chosen_form": {bl.BL_CD_BLOCKED: "residual-update CD in blocks of 16 coordinates"
-                        + (", chain and row halves on a 3-SM cluster (k_cd_clu)" if pair else " (k_cd_blk)"),
+        "chosen_form": {bl.BL_CD_BLOCKED: ("residual-update CD in blocks of 32 coordinates, the chain and four "
+                                           "row parts on a 5-SM cluster (k_cd_clu)") if pair
+                        else "residual-update CD in blocks of 16 coordinates (k_cd_blk)",
                         bl.BL_CD_COVARIANCE: "covariance-form CD",
                         bl.BL_CD_RESIDUAL: "residual-update CD"}[mode],
         "plain_form": plain,
@@ -705,6 +769,8 @@ def run_ours(args):
         line["batched_zpass"], line["batched_path"] = batched(local)
     if solo and not args.no_learned:
         line["learned"] = learned(local)
+    if solo and not args.no_genotype:
+        line["genotype_path"] = genotype_path(local)
     if solo and not args.no_many:
         line["many"] = many(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

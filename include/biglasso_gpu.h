@@ -362,6 +362,18 @@ int bl_cd_active(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, in
                  int64_t n_work, double lam, double alpha, void *beta, void *r, double eps,
                  int64_t max_sweeps, int64_t *sweeps);
 
+/* The residual recomputed from scratch in FP64 (the record step of the path,
+ * Sec. 3.1.1's r = yc - Xt b): r64[i] = yc[i] - sum_t b_{j_t} (x_{i j_t} - c_{j_t}) /
+ * s_{j_t} over j_t = idx[t], t < n_idx, accumulated in FP64 in a fixed order,
+ * and r[i] = r64[i] rounded to the design's residual type (FP32; FP64 for
+ * BL_F64).  idx: device int32 [n_idx] of kept columns (s_j > 0); beta: device
+ * dense [p] in the design's residual type (only entries at idx are read); yc,
+ * r64: device FP64 [n]; r: device [n].  r64 nullable.  Asynchronous.  Errors:
+ * BL_ERR_ARG for bad shapes or NULL arguments. */
+int bl_residual(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx, const double *center,
+                const double *scale, const int32_t *idx, int64_t n_idx, const void *beta, const double *yc,
+                double *r64, void *r);
+
 /* ---------------------------------------------------------------- the path -- */
 
 /* The whole solution path over a decreasing lambda sequence with SSR-BEDPP

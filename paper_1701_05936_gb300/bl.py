@@ -114,6 +114,7 @@ def lib():
                                  C.POINTER(_i64)],
                 "bl_fit_path": [_vp, *X, _vp, C.POINTER(bl_options), C.POINTER(_dbl), _int,
                                 C.POINTER(bl_path)],
+                "bl_residual": [_vp, *X, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp],
                 "bl_cd_active_noalloc": [_int, _vp, *X[:1], _int, _i64, _i64, _i64, _vp, _vp, _vp, _i64, _dbl,
                                          _dbl, _vp, _vp, _dbl, _i64, C.POINTER(_i64), C.c_char_p, C.c_size_t],
                 "bl_xtr_batched": [_vp, *X, _vp, _i64, _i64, _vp, _vp, _i64, C.POINTER(_dbl), _i64, _vp, _vp,
@@ -280,6 +281,12 @@ def bl_cd_active(ctx, X, n, center, scale, work_idx, lam, alpha, beta, r, eps, m
                             int(max_sweeps), C.byref(sw))
     ctx.check(st, allow=(BL_ERR_NOT_CONVERGED,))
     return sw.value, st
+
+
+def bl_residual(ctx, X, n, center, scale, idx, beta, yc, r64, r):
+    """r64 = yc - Xt b over the columns idx (FP64), r = r64 in the residual type."""
+    ctx.check(lib().bl_residual(ctx.h, *design_args(X, n), _ptr(center), _ptr(scale), _ptr(idx),
+                                int(idx.numel()), _ptr(beta), _ptr(yc), _ptr(r64), _ptr(r)))
 
 
 def bl_xtr_batched(ctx, X, n, R, center, scale, n_fit, fit_of, Z):

@@ -578,6 +578,26 @@ extern "C" int bl_screen_sedpp(bl_ctx *ctx, int dtype, int64_t n, int64_t p, con
     return BL_OK;
 }
 
+extern "C" int bl_residual(bl_ctx *ctx, const void *X, int dtype, int64_t n, int64_t p, int64_t ldx,
+                           const double *center, const double *scale, const int32_t *idx, int64_t n_idx,
+                           const void *beta, const double *yc, double *r64, void *r)
+{
+    int st = check_design(ctx, X, dtype, n, p, ldx);
+    if (st) return st;
+    if (!center || !scale || !yc || !r || n_idx < 0 || (n_idx > 0 && (!idx || !beta)))
+        return fail(ctx, BL_ERR_ARG, "NULL argument or n_idx < 0");
+    ctx->err.clear();
+    CK(cudaSetDevice(ctx->device));
+    if ((st = ensure_ws(ctx, n, p))) return st;
+    Workspace &w = ctx->ws;
+    int slot = tbegin(ctx, 6);
+    LAUNCH(1, launch_derive(center, scale, p, w.inv_scale, w.c32, w.is32, ctx->stream));
+    LAUNCH(2, launch_residual(dtype, X, n, ldx, center, w.inv_scale, idx, n_idx, w.sc, beta, yc, w.partial, r, r64,
+                              w.sc, ctx->stream));
+    tend(ctx, slot, (double)n * (double)n_idx * (double)elem_size(dtype));
+    return BL_OK;
+}
+
 // The precision form's buffers: the BF16 copy of an n x p design and the list
 // of columns its bound leaves open.
 static int ensure_prec(bl_ctx *ctx, int64_t n, int64_t p)
@@ -1574,7 +1594,7 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
                     LAUNCH(1, launch_gram(dtype, X, n, ldx, cvec, isvec, w.idx, wh, w.sc, ctx->gram, ctx->num_sms, s));
                     LAUNCH(1, launch_cd_gram(dtype, ctx->gram, n, p, isvec, w.idx, wh, w.gref, lam, alpha, w.beta, eps,
                                              opt->max_sweeps, tlim, w.sc, s));
-                } else if (cd_clu_ok(dtype, n, wh)) {  // chain on one SM, row halves on two more (bl_clu.cu)
+                } else if (cd_clu_ok(dtype, n, wh)) {  // chain on one SM, row parts on four more (bl_clu.cu)
                     if (!ctx->packed) {
                         CK(cudaMalloc(&ctx->packed, 2 * (size_t)MAX_WORKING * 4096));
                         ctx->packed_bytes = 2 * (size_t)MAX_WORKING * 4096;
@@ -1583,8 +1603,7 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
                     LAUNCH(2, launch_cd_clu((const float *)X, n, p, ldx, (const float *)cvec, (const float *)isvec,
                                             w.idx, wh, (const float *)w.gref, (const float *)ctx->gram, lam, alpha,
                                             (float *)w.beta, eps, opt->max_sweeps, tlim, w.sc,
-                                            ctx->packed, ctx->packed + (size_t)MAX_WORKING * 1024,
-                                            (int64_t)MAX_WORKING * 512, ctx->num_sms, s));
+                                            ctx->packed, (int64_t)(ctx->packed_bytes / 4), ctx->num_sms, s));
                 } else if (cd_blk_fits(dtype, n, wh)) {
                     LAUNCH(1, launch_gram(dtype, X, n, ldx, cvec, isvec, w.idx, wh, w.sc, ctx->gram, ctx->num_sms, s));
                     LAUNCH(1, launch_cd_blk(dtype, X, n, p, ldx, cvec, isvec, w.idx, wh, w.gref, ctx->gram, lam, alpha,

@@ -1,29 +1,33 @@
-// bl_clu.cu -- blocked residual-form coordinate descent on a cluster of three SMs.
+// bl_clu.cu -- blocked residual-form coordinate descent on an SM cluster.
 //
 // The same cyclic CD with residual updates and active-set cycling (Sec. 1,
-// Sec. 3.1.1) as the one-CTA blocked form (k_cd_blk): blocks of B = 16
-// consecutive coordinates of the sweep; for a block, zt_k = (g_ref,k - xd_k'dr)
-// /(n s_k) + b_k from the dots, then the scalar chain b_k' = S(zt_k, lam alpha)
+// Sec. 3.1.1) as the one-CTA blocked form (k_cd_blk): blocks of B consecutive
+// coordinates of the sweep; for a block, zt_k = (g_ref,k - xd_k'dr)/(n s_k) +
+// b_k from the dots, then the scalar chain b_k' = S(zt_k, lam alpha)
 // /(1 + lam(1-alpha)), d_k = b_k' - b_k, zt_i -= d_k R_ik for the later i, then
 // dr += sum_k d_k xd_k / s_k.  Here the chain of one block overlaps the dots of
-// the next two:
+// the next two.  The cluster has ND data CTAs and one chain CTA, all of
+// 1024/ND threads, and B = 8 ND: ND = 4 (a 5-SM cluster, B = 32, 256 threads)
+// is the form the path uses; the fixed cost of a block (two exchanges, the
+// barriers, the loop tops) is then spread over 32 coordinates.
 //
-//   CTAs 0 and 1 (data, 512 threads, one row each; n <= 1024): CTA h owns rows
-//     [512 h, 512 h + 512).  It streams each block's centred columns from a
-//     packed copy of the working set (1-D TMA bulk copies of its half, two
-//     stages), forms the partial dots with dr, reduces them to 16
-//     sums and stores them into CTA 2's shared memory.  The dots of block b use
+//   CTAs 0..ND-1 (data, one row per thread; n <= 1024): CTA h owns rows
+//     [h 1024/ND, (h+1) 1024/ND).  It streams each block's centred columns from
+//     a packed copy of the working set (1-D TMA bulk copies of its rows, two
+//     stages), forms the partial dots with dr, reduces them to B sums and
+//     stores them into the chain CTA's shared memory.  The dots of block b use
 //     dr after block b-3's update; blocks b-2 and b-1 are applied once their
 //     steps come back, from the columns kept in registers (three blocks).
-//   CTA 2 (chain): adds the two halves and the update the dots did not see,
+//   CTA ND (chain): adds the ND partial sums and the update the dots did not see,
 //     zt_k -= sum_{m in b-1} d_m R_km + sum_{m in b-2} d_m R_km
 //     (R_km = xt_k'xt_m / n, which is exactly the change in xt_k'r/n that
 //     coordinate m's residual update causes), runs the chain of block b and
-//     stores d_k / s_k into both data CTAs' shared memory.  Warp 0 does only
-//     that: warp 1 prepares the next block's operands and its b-2 term, lanes
-//     16-31 of warp 0 accumulate its b-1 term inside the chain, and the
-//     helper warps (none on warp 0's scheduler) gather R two blocks ahead and,
-//     at each active-set change, repack the active columns.
+//     stores d_k / s_k into every data CTA's shared memory.  Warp 0 does only
+//     that: warp 1 prepares the next block's operands and its b-2 term, the
+//     lanes of warp 0 accumulate its b-1 term inside the chain (every lane
+//     computes every step), and the helper warps (none on warp 0's scheduler)
+//     gather R two blocks ahead and, at each active-set change, repack the
+//     active columns.
 //
 // Both exchanges are st.async stores into the peer's shared memory, each
 // completing transaction bytes on the receiver's own mbarrier, which the
@@ -43,12 +47,19 @@ namespace bl {
 
 namespace {
 
-constexpr int CB = 16;              // coordinates per block
-constexpr int CT = 512, CW = 16;    // threads, warps per CTA
-constexpr int NDATA = 2;            // data CTAs (cluster ranks 0 and 1); the chain CTA is rank NDATA
-constexpr int HROWS = 512;          // rows per data CTA
-constexpr uint32_t HCOL = HROWS * 4;  // bytes of one packed half column
-constexpr int LA = 3;               // look-ahead: the dots of block b see updates up to block b-LA
+// The shape of one cluster: ND data CTAs and a chain CTA of CT threads (one
+// row per data thread, 1024 rows in all), blocks of CB coordinates.
+template <int ND> struct Clu {
+    static constexpr int NDATA = ND;           // data CTAs (cluster ranks 0..ND-1); the chain CTA is rank ND
+    static constexpr int CT = 1024 / ND;       // threads per CTA
+    static constexpr int CW = CT / 32;         // warps per CTA
+    static constexpr int HROWS = CT;           // rows per data CTA
+    static constexpr uint32_t HCOL = HROWS * 4;  // bytes of one packed column part
+    static constexpr int CB = 8 * ND;          // coordinates per block
+    static_assert(CB == 16 || CB == 32, "the chain warp holds one block's coordinates");
+};
+constexpr int CLU_ND = 4;  // the form the path uses: 4 data CTAs of 256 rows, blocks of 32
+constexpr int LA = 3;      // look-ahead: the dots of block b see updates up to block b-LA
 constexpr uint64_t CLU_WAIT_NS = 1000ull * 1000ull * 1000ull;
 enum { SW_STOP = 0, SW_FULL = 1, SW_ACTIVE = 2 };
 
@@ -106,13 +117,14 @@ __device__ __forceinline__ bool wait_cl(uint32_t bar, uint32_t parity, uint64_t 
 __device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
 
 // the static shared state of all roles (each CTA uses its role's part)
-struct CluShared {
+template <int ND> struct CluShared {
+    static constexpr int CB = Clu<ND>::CB, CW = Clu<ND>::CW;
     // data CTAs
     float red[CW][CB];
     __align__(16) float dks[LA][CB];        // d_k / s_k of a block, stored by the chain CTA
     __align__(8) uint64_t stF[2], dsF[LA], desc;
     // chain CTA
-    float part[LA][NDATA][CB];              // block dots, one half from each data CTA
+    float part[LA][ND][CB];                 // block dots, one partial sum from each data CTA
     __align__(16) float QT[3][CB * CB];     // R(k, i) within block b: QT[s][k*CB + i], s = b % 3
     __align__(16) float QX1[3][CB * CB];    // R(k, m) against block b-1: QX1[s][m*CB + k]
     __align__(16) float QX2[3][CB * CB];    // R(k, m) against block b-2: QX2[s][m*CB + k]
@@ -130,9 +142,9 @@ struct CluShared {
 };
 
 struct CluArgs {
-    const float *Xw;   // packed centred working-set columns: half h of column t at Xw[h*hstride + t*512]
+    const float *Xw;   // packed centred working-set columns: part h of column t at Xw[h*hstride + t*HROWS]
     float *Xa;         // the same layout for the packed active columns
-    int64_t hstride;   // floats between the two halves
+    int64_t hstride;   // floats between two parts
     int64_t n, w, p, ld;
     const int32_t *idx;
     const float *isvec, *gref, *Rm;
@@ -144,14 +156,49 @@ struct CluArgs {
 };
 
 // ------------------------------------------------------------- data role
-__device__ void clu_data(const CluArgs &a, CluShared &S, unsigned char *dyn, int h)
+// Butterfly reduce-scatter of CB per-lane values over the warp: lane l ends
+// with the warp sum of column l / (32 / CB) (lanes 2c and 2c+1 for CB = 16,
+// lane c for CB = 32).
+template <int CB> __device__ __forceinline__ float reduce_scatter(float (&v)[CB], int lane)
 {
+    float v16[16], v8[8], v4[4], v2[2];
+    if constexpr (CB == 32) {
+        const bool hi = lane & 16;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            v16[j] = (hi ? v[16 + j] : v[j]) + __shfl_xor_sync(0xffffffffu, hi ? v[j] : v[16 + j], 16);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v16[j] = v[j];
+    }
+    constexpr int o16 = (CB == 32) ? 8 : 16;  // the offset that halves 16 values
+    const bool h16 = lane & o16, h8 = lane & (o16 >> 1), h4 = lane & (o16 >> 2), h2 = lane & (o16 >> 3);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        v8[j] = (h16 ? v16[8 + j] : v16[j]) + __shfl_xor_sync(0xffffffffu, h16 ? v16[j] : v16[8 + j], o16);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        v4[j] = (h8 ? v8[4 + j] : v8[j]) + __shfl_xor_sync(0xffffffffu, h8 ? v8[j] : v8[4 + j], o16 >> 1);
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+        v2[j] = (h4 ? v4[2 + j] : v4[j]) + __shfl_xor_sync(0xffffffffu, h4 ? v4[j] : v4[2 + j], o16 >> 2);
+    float v1 = (h2 ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, h2 ? v2[0] : v2[1], o16 >> 3);
+    if constexpr (CB == 16) v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
+    return v1;
+}
+
+template <int ND> __device__ void clu_data(const CluArgs &a, CluShared<ND> &S, unsigned char *dyn, int h)
+{
+    using C = Clu<ND>;
+    constexpr int CB = C::CB, CW = C::CW, HROWS = C::HROWS;
+    constexpr uint32_t HCOL = C::HCOL;
+    constexpr int LPS = 32 / CB;  // lanes per column after the reduce-scatter
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     unsigned char *stages = dyn;  // 2 x CB x HCOL
-    float dr = 0.f;               // row 512 h + tid (0 past n: the packed rows there are 0)
-    const uint32_t peer_part = peer(smem_u32(&S.part[0][h][0]), NDATA), peer_pF = peer(smem_u32(&S.pF[0]), NDATA);
-    const uint32_t peer_kind = peer(smem_u32(&S.dkind), NDATA), peer_len = peer(smem_u32(&S.dlen), NDATA);
-    const uint32_t peer_same = peer(smem_u32(&S.dsame), NDATA);
+    float dr = 0.f;               // row HROWS h + tid (0 past n: the packed rows there are 0)
+    const uint32_t peer_part = peer(smem_u32(&S.part[0][h][0]), ND), peer_pF = peer(smem_u32(&S.pF[0]), ND);
+    const uint32_t peer_kind = peer(smem_u32(&S.dkind), ND), peer_len = peer(smem_u32(&S.dlen), ND);
+    const uint32_t peer_same = peer(smem_u32(&S.dsame), ND);
     uint32_t g = 0;  // blocks consumed so far in this launch (the chain CTA counts the same)
     // stage copies in issue order: the i-th goes to stage i & 1 and is waited for as the i-th wait
     uint32_t n_iss = 0, n_wait = 0;
@@ -161,16 +208,16 @@ __device__ void clu_data(const CluArgs &a, CluShared &S, unsigned char *dyn, int
     const float *src = a.Xw + h * a.hstride;
     int kind = SW_FULL;
     int64_t len = 0;
-    // A block's copy: one 2 KB copy per column, issued by lanes 0-3 of warps
-    // 1-4 (a copy instruction holds its thread until the copy is accepted, at
-    // about 90 bytes per cycle: spread over four warps, and off warp 0, which
-    // reduces and sends the dots).  Every thread counts it.
+    // A block's copy: one HCOL-byte copy per column, issued by lanes 0..CB/4-1
+    // of warps 1-4 (a copy instruction holds its thread until the copy is
+    // accepted, at about 90 bytes per cycle: spread over four warps, and off
+    // warp 0, which reduces and sends the dots).  Every thread counts it.
     auto issue = [&](int64_t blk) {
-        if (wid >= 1 && wid <= 4 && lane < 4) {
+        if (wid >= 1 && wid <= 4 && lane < CB / 4) {
             const int64_t t0 = blk * CB;
             const int cnt = (int)((len - t0 < CB) ? len - t0 : CB);
             const int sl = (int)(n_iss & 1u);
-            const int c = (wid - 1) * 4 + lane;
+            const int c = (wid - 1) * (CB / 4) + lane;
             if (c == 0) mbar_expect_tx(smem_u32(&S.stF[sl]), (uint32_t)cnt * HCOL);  // the phase's one arrival
             if (c < cnt)
                 bulk_g2s(smem_u32(stages + ((size_t)sl * CB + c) * HCOL), src + (t0 + c) * HROWS, HCOL,
@@ -196,28 +243,15 @@ __device__ void clu_data(const CluArgs &a, CluShared &S, unsigned char *dyn, int
             X[k] = (k < cnt) ? stg[k * HROWS + tid] : 0.f;
             part[k] = X[k] * dr;
         }
-        // butterfly reduce-scatter: lanes 2c, 2c+1 end with column c's warp sum
-        float v8[8], v4[4], v2[2];
-        const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4, h2 = lane & 2;
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            v8[j] = (h16 ? part[8 + j] : part[j]) + __shfl_xor_sync(0xffffffffu, h16 ? part[j] : part[8 + j], 16);
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            v4[j] = (h8 ? v8[4 + j] : v8[j]) + __shfl_xor_sync(0xffffffffu, h8 ? v8[j] : v8[4 + j], 8);
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-            v2[j] = (h4 ? v4[2 + j] : v4[j]) + __shfl_xor_sync(0xffffffffu, h4 ? v4[j] : v4[2 + j], 4);
-        float v1 = (h2 ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, h2 ? v2[0] : v2[1], 2);
-        v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
-        if ((lane & 1) == 0) S.red[wid][lane >> 1] = v1;
+        const float v1 = reduce_scatter<CB>(part, lane);
+        if ((lane & (LPS - 1)) == 0) S.red[wid][lane / LPS] = v1;
         __syncthreads();  // stage consumed by every warp; red complete
         if (wid == 0 && lane < CB) {
             float s = 0.f;
 #pragma unroll
             for (int q = 0; q < CW; ++q) s += S.red[q][lane];
             const uint32_t ps = g % LA;
-            st_async_f32(peer_part + (ps * NDATA * CB + (uint32_t)lane) * 4, s, peer_pF + ps * 8);
+            st_async_f32(peer_part + (ps * ND * CB + (uint32_t)lane) * 4, s, peer_pF + ps * 8);
         }
     };
     // apply block gg's steps (stored by the chain CTA into slot gg % LA) to dr
@@ -320,8 +354,10 @@ __device__ void clu_data(const CluArgs &a, CluShared &S, unsigned char *dyn, int
 }
 
 // ------------------------------------------------------------ chain role
-__device__ void clu_chain(const CluArgs &a, CluShared &S, unsigned char *dyn)
+template <int ND> __device__ void clu_chain(const CluArgs &a, CluShared<ND> &S, unsigned char *dyn)
 {
+    using C = Clu<ND>;
+    constexpr int CB = C::CB, CT = C::CT, CW = C::CW, HROWS = C::HROWS;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t w = a.w, ld = a.ld;
     uint16_t *act_s = reinterpret_cast<uint16_t *>(dyn);  // w
@@ -342,10 +378,16 @@ __device__ void clu_chain(const CluArgs &a, CluShared &S, unsigned char *dyn)
     const float inv_n = (float)(1.0 / (double)a.n);
     const float epsA = (float)a.eps;
     constexpr float RES_FLOOR = 4.76837158203125e-07f;  // 8 units in the last place
-    // lanes 0-15 send to data CTA 0, lanes 16-31 to data CTA 1
-    const uint32_t peer_dks = peer(smem_u32(&S.dks[0][0]), (uint32_t)(lane >> 4));
-    const uint32_t peer_dsF = peer(smem_u32(&S.dsF[0]), (uint32_t)(lane >> 4));
-    const uint32_t peer_desc0 = peer(smem_u32(&S.desc), 0), peer_desc1 = peer(smem_u32(&S.desc), 1);
+    // the steps of a block go to every data CTA: SPL sends per lane, lane l
+    // sending value l % CB to data CTAs (l / CB) * SPL .. (l / CB) * SPL + SPL - 1
+    constexpr int SPL = ND * CB / 32;
+    uint32_t peer_dks[SPL], peer_dsF[SPL];
+#pragma unroll
+    for (int q = 0; q < SPL; ++q) {
+        const uint32_t r = (uint32_t)((lane / CB) * SPL + q);
+        peer_dks[q] = peer(smem_u32(&S.dks[0][0]), r);
+        peer_dsF[q] = peer(smem_u32(&S.dsF[0]), r);
+    }
     const uint64_t t_start = globaltimer_ns();
     uint32_t g = 0;
     int64_t sweeps = 0;
@@ -431,7 +473,7 @@ __device__ void clu_chain(const CluArgs &a, CluShared &S, unsigned char *dyn)
             repack = false;
             for (int64_t t = wid; t < len; t += CW) {
 #pragma unroll
-                for (int hh = 0; hh < NDATA; ++hh) {
+                for (int hh = 0; hh < ND; ++hh) {
                     const float4 *sv =
                         reinterpret_cast<const float4 *>(a.Xw + hh * a.hstride + (int64_t)act_s[t] * HROWS);
                     float4 *dv = reinterpret_cast<float4 *>(a.Xa + hh * a.hstride + t * HROWS);
@@ -448,8 +490,8 @@ __device__ void clu_chain(const CluArgs &a, CluShared &S, unsigned char *dyn)
             S.dkind = ok ? kind : SW_STOP;
             S.dlen = (int)len;
             S.dsame = same;
-            arrive_peer(peer_desc0);
-            arrive_peer(peer_desc1);
+#pragma unroll
+            for (int r = 0; r < ND; ++r) arrive_peer(peer(smem_u32(&S.desc), (uint32_t)r));
         }
         if (!ok || kind == SW_STOP) break;
         const int64_t nblk = (len + CB - 1) / CB;
@@ -468,10 +510,11 @@ __device__ void clu_chain(const CluArgs &a, CluShared &S, unsigned char *dyn)
         }
         if (wid == 1 && nblk > 0) prep(0, q0);
         // block 0's partials: armed now, each later block's right after the wait before it
-        if (tid == 0 && nblk > 0) mbar_expect_tx(smem_u32(&S.pF[q0]), NDATA * CB * 4);
+        if (tid == 0 && nblk > 0) mbar_expect_tx(smem_u32(&S.pF[q0]), ND * CB * 4);
         q0_ok = kind == SW_ACTIVE;
         bool moved = false, newnz = false;  // lanes of warp 0
-        float x1acc = 0.f;  // lanes 16-31 of warp 0: the next block's correction for this block's steps
+        float x1acc = 0.f;  // lane CB + i (CB = 16) or i (CB = 32) of warp 0: coordinate i of the next
+                            // block's correction for this block's steps
         __syncthreads();
         for (int64_t blk = 0; blk < nblk; ++blk, ++g) {
             const int q1 = (q0 == 2) ? 0 : q0 + 1, q2 = (q1 == 2) ? 0 : q1 + 1;
@@ -484,7 +527,7 @@ __device__ void clu_chain(const CluArgs &a, CluShared &S, unsigned char *dyn)
                 // lanes 16-31 during the last chain) and b-2 (from warp 1), which
                 // the dots did not see
                 const int o = (int)(blk & 1);
-                const float x1 = __shfl_down_sync(0xffffffffu, x1acc, CB);
+                const float x1 = (CB == 32) ? x1acc : __shfl_down_sync(0xffffffffu, x1acc, CB & 31);
                 const bool mine = lane < cnt;  // lanes >= CB have cnt <= CB <= lane
                 int my_pos = 0;
                 float my_b = 0.f, my_is = 0.f, my_g = 0.f, xc = 0.f;
@@ -498,11 +541,13 @@ __device__ void clu_chain(const CluArgs &a, CluShared &S, unsigned char *dyn)
                 // block g's partials from both data CTAs; then arm the next block's
                 // slot (its previous phase, block g+1-LA, completed long ago)
                 if (!wait_cl(smem_u32(&S.pF[ps]), par, CLU_WAIT_NS)) S.fail = 1;
-                if (lane == 0 && blk + 1 < nblk) mbar_expect_tx(smem_u32(&S.pF[q1]), NDATA * CB * 4);
+                if (lane == 0 && blk + 1 < nblk) mbar_expect_tx(smem_u32(&S.pF[q1]), ND * CB * 4);
                 if (lane < CB) {
                     float zt = 0.f;
                     if (mine) {
-                        const float dot = S.part[ps][0][lane] + S.part[ps][1][lane];
+                        float dot = S.part[ps][0][lane];
+#pragma unroll
+                        for (int r = 1; r < ND; ++r) dot += S.part[ps][r][lane];
                         zt = fmaf(my_g - dot, my_is * inv_n, my_b) - xc;
                     }
                     S.zts[lane] = zt;
@@ -517,8 +562,8 @@ __device__ void clu_chain(const CluArgs &a, CluShared &S, unsigned char *dyn)
                     zt[4 * q] = z4.x, zt[4 * q + 1] = z4.y, zt[4 * q + 2] = z4.z, zt[4 * q + 3] = z4.w;
                     bb[4 * q] = b4.x, bb[4 * q + 1] = b4.y, bb[4 * q + 2] = b4.z, bb[4 * q + 3] = b4.w;
                 }
-                // the chain; every lane computes every step, and lane 16 + i adds
-                // d_k R(i of block b+1, k) for the next block
+                // the chain; every lane computes every step, and lane CB + i (CB =
+                // 16) or i (CB = 32) adds d_k R(i of block b+1, k) for the next block
                 const float *qx1n = S.QX1[q1] + (lane & (CB - 1));
                 x1acc = 0.f;
                 float my_s = 0.f;
@@ -548,7 +593,9 @@ __device__ void clu_chain(const CluArgs &a, CluShared &S, unsigned char *dyn)
                     S.dph[blk & 1][lane] = dv;
                 }
                 dsv = __shfl_sync(0xffffffffu, dsv, lane & (CB - 1));
-                st_async_f32(peer_dks + (ps * CB + (uint32_t)(lane & (CB - 1))) * 4, dsv, peer_dsF + ps * 8);
+#pragma unroll
+                for (int q = 0; q < SPL; ++q)
+                    st_async_f32(peer_dks[q] + (ps * CB + (uint32_t)(lane & (CB - 1))) * 4, dsv, peer_dsF[q] + ps * 8);
                 updates += (unsigned long long)cnt;
             }
             __syncthreads();  // R entries two blocks ahead and the next block's operands are in place
@@ -632,11 +679,9 @@ __device__ void clu_chain(const CluArgs &a, CluShared &S, unsigned char *dyn)
     }
 }
 
-}  // namespace
-
-__global__ void __launch_bounds__(CT, 1) k_cd_clu(CluArgs a)
+template <int ND> __global__ void __launch_bounds__(Clu<ND>::CT, 1) k_cd_clu(CluArgs a)
 {
-    __shared__ CluShared S;
+    __shared__ CluShared<ND> S;
     extern __shared__ __align__(16) unsigned char dyn[];
     const uint32_t rank = cluster_rank();
     if (threadIdx.x == 0) {
@@ -651,19 +696,19 @@ __global__ void __launch_bounds__(CT, 1) k_cd_clu(CluArgs a)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     cluster_sync();  // every CTA's barriers exist before any remote arrival
-    if (rank < NDATA)
-        clu_data(a, S, dyn, (int)rank);
+    if (rank < (uint32_t)ND)
+        clu_data<ND>(a, S, dyn, (int)rank);
     else
-        clu_chain(a, S, dyn);
+        clu_chain<ND>(a, S, dyn);
     cluster_sync();  // no CTA leaves while another may still touch its memory
 }
 
-// Packed centred working set, in two row halves: Xw[h*hstride + t*512 + i] =
-// X[idx[t]][512 h + i] - c[idx[t]] (the FP32 subtraction the one-CTA form does
-// per use) for 512 h + i < n, 0 up to row 1024.
-__global__ void __launch_bounds__(256) k_pack_halves(const float *__restrict__ X, int64_t ldx, int64_t n,
-                                                     const float *__restrict__ cvec, const int32_t *__restrict__ idx,
-                                                     int64_t w, int64_t hstride, float *Xw)
+// Packed centred working set in ND row parts of HROWS rows: Xw[h*hstride +
+// t*HROWS + i] = X[idx[t]][HROWS h + i] - c[idx[t]] (the FP32 subtraction the
+// one-CTA form does per use) for HROWS h + i < n, 0 up to row 1024.
+__global__ void __launch_bounds__(256) k_pack_parts(const float *__restrict__ X, int64_t ldx, int64_t n,
+                                                    const float *__restrict__ cvec, const int32_t *__restrict__ idx,
+                                                    int64_t w, int64_t hrows, int64_t hstride, float *Xw)
 {
     for (int64_t t = blockIdx.x; t < w; t += gridDim.x) {
         const int32_t j = idx[t];
@@ -671,8 +716,8 @@ __global__ void __launch_bounds__(256) k_pack_halves(const float *__restrict__ X
         const float c = cvec[j];
         const int q = threadIdx.x;  // 256 x 4 = 1024 rows
         const int64_t i = (int64_t)q * 4;
-        const int hh = (int)(i / HROWS);
-        float4 *dst = reinterpret_cast<float4 *>(Xw + hh * hstride + t * HROWS + (i - hh * HROWS));
+        const int64_t hh = i / hrows;  // hrows is a multiple of 4: the four rows share a part
+        float4 *dst = reinterpret_cast<float4 *>(Xw + hh * hstride + t * hrows + (i - hh * hrows));
         float4 v;
         v.x = (i < n) ? col[i] - c : 0.f;
         v.y = (i + 1 < n) ? col[i + 1] - c : 0.f;
@@ -682,46 +727,57 @@ __global__ void __launch_bounds__(256) k_pack_halves(const float *__restrict__ X
     }
 }
 
-size_t cd_clu_smem(int64_t w)
+template <int ND> size_t clu_smem(int64_t w)
 {
-    const size_t data = 2 * (size_t)CB * HCOL;
+    const size_t data = 2 * (size_t)Clu<ND>::CB * Clu<ND>::HCOL;
     const size_t chain = (((size_t)w * 2 + 15) & ~(size_t)15) + (size_t)w * 16;
     return std::max(data, chain);
 }
 
-bool cd_clu_ok(int dtype, int64_t n, int64_t w)
+template <int ND> bool clu_ok(int64_t n, int64_t w)
 {
-    return dtype == BL_F32 && n >= 1 && n <= NDATA * HROWS && w >= 1 && w <= MAX_WORKING &&
-           cd_clu_smem(w) + sizeof(CluShared) <= 227 * 1024 - 1024;
+    return n >= 1 && n <= 1024 && w >= 1 && w <= MAX_WORKING &&
+           clu_smem<ND>(w) + sizeof(CluShared<ND>) <= 227 * 1024 - 1024;
 }
+
+}  // namespace
+
+size_t cd_clu_smem(int64_t w) { return clu_smem<CLU_ND>(w); }
+
+bool cd_clu_ok(int dtype, int64_t n, int64_t w) { return dtype == BL_F32 && clu_ok<CLU_ND>(n, w); }
 
 cudaError_t launch_cd_clu(const float *X, int64_t n, int64_t p, int64_t ldx, const float *cvec, const float *isvec,
                           const int32_t *idx, int64_t w, const float *gref, const float *Rm, double lam, double alpha,
                           float *beta, double eps, int64_t max_sweeps, uint64_t time_limit_ns, DevScalars *sc,
-                          float *Xw, float *Xa, int64_t hstride, int num_sms, cudaStream_t st)
+                          float *packed, int64_t packed_floats, int num_sms, cudaStream_t st)
 {
-    if (!cd_clu_ok(BL_F32, n, w) || hstride < w * HROWS || (hstride & 3)) return cudaErrorInvalidValue;
-    k_pack_halves<<<(int)std::min<int64_t>(w, (int64_t)num_sms * 8), 256, 0, st>>>(X, ldx, n, cvec, idx, w, hstride,
-                                                                                     Xw);
+    constexpr int ND = CLU_ND;
+    using C = Clu<ND>;
+    // packed: the working set's columns in its first half, the active ones in its second
+    const int64_t hstride = (packed_floats / 2) / ND;
+    if (!cd_clu_ok(BL_F32, n, w) || hstride < w * C::HROWS || (hstride & 3)) return cudaErrorInvalidValue;
+    float *Xw = packed, *Xa = packed + hstride * ND;
+    k_pack_parts<<<(int)std::min<int64_t>(w, (int64_t)num_sms * 8), 256, 0, st>>>(X, ldx, n, cvec, idx, w, C::HROWS,
+                                                                                    hstride, Xw);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem = cd_clu_smem(w);
-    if ((e = allow_smem(k_cd_clu, smem)) != cudaSuccess) return e;
+    const size_t smem = clu_smem<ND>(w);
+    if ((e = allow_smem(k_cd_clu<ND>, smem)) != cudaSuccess) return e;
     CluArgs a{Xw, Xa, hstride, n, w, p, gram_ld(w), idx, isvec, gref, Rm, beta, lam, alpha, eps, max_sweeps,
               time_limit_ns, sc};
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(NDATA + 1, 1, 1);
-    cfg.blockDim = dim3(CT, 1, 1);
+    cfg.gridDim = dim3(ND + 1, 1, 1);
+    cfg.blockDim = dim3(C::CT, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = NDATA + 1;
+    attr[0].val.clusterDim.x = ND + 1;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_cd_clu, a);
+    return cudaLaunchKernelEx(&cfg, k_cd_clu<ND>, a);
 }
 
 }  // namespace bl

@@ -156,14 +156,16 @@ cudaError_t launch_cd_gram(int dtype, const void *Rm, int64_t n, int64_t p, cons
                            int64_t w, const void *gref, double lam, double alpha, void *beta, double eps,
                            int64_t max_sweeps, uint64_t time_limit_ns, DevScalars *sc, cudaStream_t st);
 
-// ---- blocked CD on three SMs (two data CTAs of 512 rows, one chain CTA;
-// FP32, n <= 1024); Xw, Xa hold two row halves hstride floats apart
+// ---- blocked CD on an SM cluster (four data CTAs of 256 rows, one chain CTA,
+// blocks of 32 coordinates; FP32, n <= 1024).  packed: packed_floats of
+// scratch for the centred working-set columns (first half) and the active
+// ones (second half), at least 2 * MAX_WORKING * 1024 floats.
 size_t cd_clu_smem(int64_t w);
 bool cd_clu_ok(int dtype, int64_t n, int64_t w);
 cudaError_t launch_cd_clu(const float *X, int64_t n, int64_t p, int64_t ldx, const float *cvec, const float *isvec,
                           const int32_t *idx, int64_t w, const float *gref, const float *Rm, double lam, double alpha,
                           float *beta, double eps, int64_t max_sweeps, uint64_t time_limit_ns, DevScalars *sc,
-                          float *Xw, float *Xa, int64_t hstride, int num_sms, cudaStream_t st);
+                          float *packed, int64_t packed_floats, int num_sms, cudaStream_t st);
 
 // ---- learned working-set proposer
 constexpr int MLP_IN = 5, MLP_HIDDEN = 64;

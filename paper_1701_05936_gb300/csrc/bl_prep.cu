@@ -470,9 +470,11 @@ __global__ void __launch_bounds__(256) k_screen(ScreenArgs a, DevScalars *sc)
     if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
     __syncthreads();
     unsigned int n_safe = 0, n_strong = 0, n_scan = 0;
-    // SEDPP with lam_prev at lambda_max is the BEDPP rule (the reference point is lambda_max)
+    // SEDPP with lam_prev at lambda_max is the BEDPP rule (the reference point is
+    // lambda_max); so is a previous solution that is exactly 0 (u = 0: its
+    // lam_prev lies at or above lambda_max up to rounding)
     const bool sedpp = (a.rule == 4) && (a.jstar >= 0);
-    const bool sed_seq = sedpp && a.lam_prev < a.lmax;
+    const bool sed_seq = sedpp && a.lam_prev < a.lmax && sc->sed_uu > 0.0;
     const bool use_bedpp = ((a.rule == 2) || (sedpp && !sed_seq)) && (a.jstar >= 0);
     const double thr = a.alpha * (2.0 * a.lam - a.lam_prev);
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.p;

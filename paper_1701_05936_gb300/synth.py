@@ -21,7 +21,8 @@ Sec. 4.2 simulated data and Table 2's real-data shapes):
 * ``gaussian_ar1``  -- x_1 ~ N(0,I), x_j = rho x_{j-1} + sqrt(1-rho^2) e_j;
   k nonzero beta ~ U[lo,hi] with random sign; noise sd set so that the sample
   variance of X beta over sigma^2 equals the SNR.    (1000 x 100,000, FP32)
-* ``genotype``      -- x_ij ~ Binomial(2, MAF_j), MAF_j ~ U[0.05, 0.5], int8;
+* ``genotype``      -- x_ij ~ Binomial(2, MAF_j), MAF_j ~ U[0.05, 0.5], int8
+  (drawn by inversion of one uniform per cell, in parallel chunks);
   k causal effects N(0, 0.3^2); sigma^2 = Var(g)(1-h2)/h2.  (5000 x 500,000)
 * ``block_factor``  -- blocks of 100 columns sharing a factor (correlation 0.6
   within a block), 40 nonzero beta ~ +-U[0.3,1], SNR 3: the learned proposer's
@@ -32,6 +33,8 @@ Sec. 4.2 simulated data and Table 2's real-data shapes):
 """
 from __future__ import annotations
 
+import concurrent.futures as cf
+import os
 from dataclasses import dataclass, field
 from typing import Optional
 
@@ -137,10 +140,23 @@ def genotype(n=5000, p=500_000, k=50, effect_sd=0.3, h2=0.3, workload=3,
     g = rng_for(workload, replicate)
     X, ldx = _alloc_x(n, p, "i8", pad_value)
     maf = g.uniform(0.05, 0.5, size=p)
+    # x_ij = [u >= (1 - m)^2] + [u >= 1 - m^2] with u ~ U[0,1) is Binomial(2, m)
+    # (P(0) = (1-m)^2, P(2) = m^2).  Columns are drawn in chunks, chunk c from
+    # its own stream (the key's Philox jumped c + 1 times), on worker threads:
+    # the values depend only on the key, not on the thread schedule.
+    key = np.array([SEED_BASE, workload * 1000 + replicate], dtype=np.uint64)
     chunk = max(1, (1 << 24) // max(n, 1))
-    for j0 in range(0, p, chunk):
+
+    def fill(c: int, j0: int) -> None:
         j1 = min(p, j0 + chunk)
-        X[j0:j1, :n] = g.binomial(2, maf[j0:j1, None], size=(j1 - j0, n)).astype(np.int8)
+        gc = np.random.Generator(np.random.Philox(key=key).jumped(c + 1))
+        u = gc.random((j1 - j0, n), dtype=np.float32)
+        m = maf[j0:j1, None]
+        X[j0:j1, :n] = (u >= (1.0 - m) ** 2).astype(np.int8) + (u >= 1.0 - m * m).astype(np.int8)
+
+    starts = list(range(0, p, chunk))
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1, len(starts))) as ex:
+        list(ex.map(fill, range(len(starts)), starts))
     beta = np.zeros(p)
     k = min(k, p)
     idx = g.choice(p, size=k, replace=False)
