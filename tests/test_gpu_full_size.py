@@ -1,8 +1,9 @@
 """Full-size workloads against the FP64 oracle.
 
 * Genotype codes, 5000 x 500,000 int8 (p * ldx = 2.56e9 elements > 2^31:
-  element offsets into the design are 64-bit).  The oracle's int8 form (xt_ij evaluated on the fly, all
-  host cores, bit-identical to the serial explicit oracle) solves the first
+  element offsets into the design are 64-bit).  The oracle's int8 form (xt_ij
+  evaluated on the fly, all host cores, bit-identical to the serial explicit
+  oracle) solves the first
   lambdas of the same grid; those must match at the path's bar.  Deeper in the
   path, where a full oracle path would take hours, the GPU's solution is
   certified by the KKT conditions of Sec. 2.2 evaluated in FP64 over all
@@ -102,7 +103,9 @@ def test_block_factor_p100k_matches_oracle(rule, all_cores):
         per_lam = np.abs(B - o["beta"]).max(axis=1)
         print(f"block factor p=100k {rule}: per-lambda max|dbeta| worst {per_lam.max():.3e} at k={per_lam.argmax()}, "
               f"active at lambda_min {int((o['beta'][-1] != 0).sum())}")
-        compare_paths(prob, g, o, 1e-5, label=f"block factor {rule}")
+        # an entering-at-this-lambda tie (|b| < 1e-5 on both sides) is the one
+        # permitted active-set difference; the count is printed
+        compare_paths(prob, g, o, 1e-5, allow_exempt=2, label=f"block factor {rule}")
     finally:
         ctx.close()
 
