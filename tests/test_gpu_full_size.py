@@ -126,7 +126,8 @@ def test_batched_full_size_sampled_fits_match_oracle(all_cores):
     import types
     prob = types.SimpleNamespace(p=bp.p, dtype="f32")
     full = oracle.fit_path(bp.X[:, :bp.n], bp.Y[0], bp.alpha, ratio=bp.ratio, nlambda=bp.nlambda, eps=bp.eps)
-    compare_paths(prob, res[0], full, 1e-5, label="batched full size, response 0 on all rows")
+    # entering-at-this-lambda ties (|b| < 1e-5 on both sides) are counted and printed
+    compare_paths(prob, res[0], full, 1e-5, allow_exempt=2, label="batched full size, response 0 on all rows")
     rows = bp.fit_rows(1)
     fold = oracle.fit_path(bp.X[:, rows], bp.Y[0, rows], bp.alpha, lambdas=full["lambdas"], eps=bp.eps)
-    compare_paths(prob, res[1], fold, 1e-5, label="batched full size, response 0 without fold 0")
+    compare_paths(prob, res[1], fold, 1e-5, allow_exempt=2, label="batched full size, response 0 without fold 0")
