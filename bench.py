@@ -725,7 +725,7 @@ def run_ours(args):
     cd = tim["cd"]
     nlam = prob.nlambda - 1  # lambda_max itself needs no descent
     pair = mode == bl.BL_CD_BLOCKED and prob.dtype == "f32" and prob.n <= 1024
-    cd_info = {"bound": "latency (sequential coordinates; chain and dots on a 5-SM cluster)" if pair
+    cd_info = {"bound": "latency (sequential coordinates; chain and dots on a 3-SM cluster)" if pair
                else "latency (one CTA, sequential coordinates)",
                "updates_per_step": tim["cd_updates"] / args.steps,
                "ns_per_update": 1e6 * cd["ms"] / max(1, tim["cd_updates"]),
@@ -750,8 +750,8 @@ def run_ours(args):
         "value_excl_init": {"value": value_excl_init, "unit": "paths/s",
                             "excludes": "standardization, lambda_max and BEDPP init (one-time per design)"},
         "gpu_launches": int(tim["kernel_launches"]), "clocks": clk, "cd": cd_info,
-        "chosen_form": {bl.BL_CD_BLOCKED: ("residual-update CD in blocks of 32 coordinates, the chain and four "
-                                           "row parts on a 5-SM cluster (k_cd_clu)") if pair
+        "chosen_form": {bl.BL_CD_BLOCKED: ("residual-update CD in blocks of 16 coordinates, the chain and two "
+                                           "row halves on a 3-SM cluster (k_cd_clu)") if pair
                         else "residual-update CD in blocks of 16 coordinates (k_cd_blk)",
                         bl.BL_CD_COVARIANCE: "covariance-form CD",
                         bl.BL_CD_RESIDUAL: "residual-update CD"}[mode],

@@ -1594,7 +1594,7 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
                     LAUNCH(1, launch_gram(dtype, X, n, ldx, cvec, isvec, w.idx, wh, w.sc, ctx->gram, ctx->num_sms, s));
                     LAUNCH(1, launch_cd_gram(dtype, ctx->gram, n, p, isvec, w.idx, wh, w.gref, lam, alpha, w.beta, eps,
                                              opt->max_sweeps, tlim, w.sc, s));
-                } else if (cd_clu_ok(dtype, n, wh)) {  // chain on one SM, row parts on four more (bl_clu.cu)
+                } else if (cd_clu_ok(dtype, n, wh)) {  // chain on one SM, row halves on two more (bl_clu.cu)
                     if (!ctx->packed) {
                         CK(cudaMalloc(&ctx->packed, 2 * (size_t)MAX_WORKING * 4096));
                         ctx->packed_bytes = 2 * (size_t)MAX_WORKING * 4096;

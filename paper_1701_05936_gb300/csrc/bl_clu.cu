@@ -7,9 +7,8 @@
 // /(1 + lam(1-alpha)), d_k = b_k' - b_k, zt_i -= d_k R_ik for the later i, then
 // dr += sum_k d_k xd_k / s_k.  Here the chain of one block overlaps the dots of
 // the next two.  The cluster has ND data CTAs and one chain CTA, all of
-// 1024/ND threads, and B = 8 ND: ND = 4 (a 5-SM cluster, B = 32, 256 threads)
-// is the form the path uses; the fixed cost of a block (two exchanges, the
-// barriers, the loop tops) is then spread over 32 coordinates.
+// 1024/ND threads, and B = 8 ND; the path uses ND = 2 (a 3-SM cluster, B = 16,
+// 512 threads, see CLU_ND).
 //
 //   CTAs 0..ND-1 (data, one row per thread; n <= 1024): CTA h owns rows
 //     [h 1024/ND, (h+1) 1024/ND).  It streams each block's centred columns from
@@ -58,7 +57,12 @@ template <int ND> struct Clu {
     static constexpr int CB = 8 * ND;          // coordinates per block
     static_assert(CB == 16 || CB == 32, "the chain warp holds one block's coordinates");
 };
-constexpr int CLU_ND = 4;  // the form the path uses: 4 data CTAs of 256 rows, blocks of 32
+// The form the path uses: 2 data CTAs of 512 rows, blocks of 16 (62.5 ns per
+// update on the 1000 x 100,000 path).  ND = 4 (4 data CTAs of 256 rows, blocks
+// of 32) measured 101.6 ns: every chain lane evaluates every step, so the
+// chain warp issues CB^2/2 updates per block (4x at CB = 32), and the helper
+// warps gather 3 CB^2 entries of R per block over half as many threads.
+constexpr int CLU_ND = 2;
 constexpr int LA = 3;      // look-ahead: the dots of block b see updates up to block b-LA
 constexpr uint64_t CLU_WAIT_NS = 1000ull * 1000ull * 1000ull;
 enum { SW_STOP = 0, SW_FULL = 1, SW_ACTIVE = 2 };

@@ -156,8 +156,8 @@ cudaError_t launch_cd_gram(int dtype, const void *Rm, int64_t n, int64_t p, cons
                            int64_t w, const void *gref, double lam, double alpha, void *beta, double eps,
                            int64_t max_sweeps, uint64_t time_limit_ns, DevScalars *sc, cudaStream_t st);
 
-// ---- blocked CD on an SM cluster (four data CTAs of 256 rows, one chain CTA,
-// blocks of 32 coordinates; FP32, n <= 1024).  packed: packed_floats of
+// ---- blocked CD on an SM cluster (two data CTAs of 512 rows, one chain CTA,
+// blocks of 16 coordinates; FP32, n <= 1024).  packed: packed_floats of
 // scratch for the centred working-set columns (first half) and the active
 // ones (second half), at least 2 * MAX_WORKING * 1024 floats.
 size_t cd_clu_smem(int64_t w);

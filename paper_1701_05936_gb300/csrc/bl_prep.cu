@@ -474,7 +474,9 @@ __global__ void __launch_bounds__(256) k_screen(ScreenArgs a, DevScalars *sc)
     // lambda_max); so is a previous solution that is exactly 0 (u = 0: its
     // lam_prev lies at or above lambda_max up to rounding)
     const bool sedpp = (a.rule == 4) && (a.jstar >= 0);
-    const bool sed_seq = sedpp && a.lam_prev < a.lmax && sc->sed_uu > 0.0;
+    // (within 1e-12 relative of lambda_max, or ||u||^2 at rounding level of
+    // ||yc||^2, the reference point lambda_max is taken: BEDPP is safe at any lam)
+    const bool sed_seq = sedpp && a.lam_prev < a.lmax * (1.0 - 1e-12) && sc->sed_uu > 1e-24 * a.ynorm2;
     const bool use_bedpp = ((a.rule == 2) || (sedpp && !sed_seq)) && (a.jstar >= 0);
     const double thr = a.alpha * (2.0 * a.lam - a.lam_prev);
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.p;

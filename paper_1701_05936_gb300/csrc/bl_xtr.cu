@@ -46,10 +46,12 @@ constexpr int XT_MAXS = 6;                 // pipeline stages at most
 constexpr int XT_THREADS = 192;
 constexpr uint32_t XT_A_BYTES = XT_BM * XT_BK * 4;   // one 128 x 32 FP32 tile
 constexpr uint64_t XT_WAIT_NS = 2000ull * 1000ull * 1000ull;
+constexpr int XT_FIT_CACHE = 16;           // fits whose epilogue vectors a tile caches in shared memory
+constexpr size_t XT_STATIC_SMEM = 2 * 256 * 4 + 2 * XT_FIT_CACHE * XT_BM * 4 + 512;  // static arrays, barriers
 
 struct XtrArgs {
     int64_t n, p, ldz;
-    int nrhs, np, stages, ntiles, kchunks;
+    int nrhs, np, stages, ntiles, kchunks, nfit;
     uint32_t idesc, tmem_cols, stage_bytes;
     const int32_t *fit_of;
     const float *cfit, *insfit;  // nfit x p: c_fj and 1/(n_f s_fj) (0 for a dropped column)
@@ -105,6 +107,7 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
     __shared__ uint32_t tmem_slot;
     __shared__ int fit_s[256];
     __shared__ float sumr_s[256];
+    __shared__ float fc_s[XT_FIT_CACHE][XT_BM], fi_s[XT_FIT_CACHE][XT_BM];  // per-fit c and 1/(n s) of the tile
     __shared__ int err_s;
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -200,40 +203,61 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
         }
     } else {  // epilogue
         const int q = warp & 3;
+        const int et = threadIdx.x - 64;  // this thread's feature slot in the tile, 0..127
+        const bool cached = a.nfit <= XT_FIT_CACHE;
         int tl = 0;
         for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++tl) {
             const int acc = tl % XT_ACC, use = tl / XT_ACC;
+            const int64_t j = (int64_t)tile * XT_BM + 32 * q + lane;
+            const bool live = j < a.p;
+            // this feature's c_fj and 1/(n_f s_fj) for every fit, fetched once per
+            // tile (while the tile still accumulates) into slots only this thread uses
+            if (cached && live)
+                for (int f = 0; f < a.nfit; ++f) {
+                    fc_s[f][et] = __ldg(a.cfit + (int64_t)f * a.p + j);
+                    fi_s[f][et] = __ldg(a.insfit + (int64_t)f * a.p + j);
+                }
             if (!mbar_wait_bounded(smem_u32(&tfull[acc]), use & 1, XT_WAIT_NS)) {
                 if (lane == 0) atomicOr(&err_s, 4);
                 break;
             }
             tc_fence_after();
             {
-                const int64_t j = (int64_t)tile * XT_BM + 32 * q + lane;
-                const bool live = j < a.p;
+                // four 16-column TMEM loads in flight per wait
 #pragma unroll 1
-                for (int c0 = 0; c0 < a.np; c0 += 16) {
-                    uint32_t v[16];
-                    const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * a.np + c0);
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                        "[%16];"
-                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                          "=r"(v[15])
-                        : "r"(ta));
+                for (int c0 = 0; c0 < a.np; c0 += 64) {
+                    uint32_t v[4][16];
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        if (c0 + 16 * g < a.np) {
+                            const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * a.np + c0 + 16 * g);
+                            asm volatile(
+                                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                                "%15}, [%16];"
+                                : "=r"(v[g][0]), "=r"(v[g][1]), "=r"(v[g][2]), "=r"(v[g][3]), "=r"(v[g][4]), "=r"(v[g][5]),
+                                  "=r"(v[g][6]), "=r"(v[g][7]), "=r"(v[g][8]), "=r"(v[g][9]), "=r"(v[g][10]),
+                                  "=r"(v[g][11]), "=r"(v[g][12]), "=r"(v[g][13]), "=r"(v[g][14]), "=r"(v[g][15])
+                                : "r"(ta));
+                        }
+                    }
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                     if (live) {
 #pragma unroll
-                        for (int t = 0; t < 16; ++t) {
-                            const int b = c0 + t;
-                            if (b < a.nrhs) {
-                                const int f = fit_s[b];
-                                const float c = __ldg(a.cfit + (int64_t)f * a.p + j);
-                                const float is = __ldg(a.insfit + (int64_t)f * a.p + j);
-                                a.Z[(int64_t)b * a.ldz + j] = (__uint_as_float(v[t]) - c * sumr_s[b]) * is;
+                        for (int g = 0; g < 4; ++g)
+#pragma unroll
+                            for (int t = 0; t < 16; ++t) {
+                                const int b = c0 + 16 * g + t;
+                                if (b < a.nrhs) {
+                                    const int f = fit_s[b];
+                                    if ((unsigned)f >= (unsigned)a.nfit) {  // a fit index out of range: no value
+                                        a.Z[(int64_t)b * a.ldz + j] = __int_as_float(0x7fc00000);
+                                        continue;
+                                    }
+                                    const float c = cached ? fc_s[f][et] : __ldg(a.cfit + (int64_t)f * a.p + j);
+                                    const float is = cached ? fi_s[f][et] : __ldg(a.insfit + (int64_t)f * a.p + j);
+                                    a.Z[(int64_t)b * a.ldz + j] = (__uint_as_float(v[g][t]) - c * sumr_s[b]) * is;
+                                }
                             }
-                        }
                     }
                 }
             }
@@ -331,7 +355,7 @@ int xtr_stages(int nrhs, size_t *smem)
 {
     const int np = (nrhs + 15) / 16 * 16;
     const size_t stage = (size_t)XT_A_BYTES + (size_t)np * XT_BK * 4;
-    int s = (int)((227 * 1024 - 2048) / stage);
+    int s = (int)((227 * 1024 - 1024 - XT_STATIC_SMEM) / stage);
     if (s > XT_MAXS) s = XT_MAXS;
     if (smem) *smem = 1024 + (size_t)s * stage;
     return s >= 2 ? s : 0;
@@ -362,6 +386,7 @@ cudaError_t launch_xtr(const float *X, int64_t n, int64_t p, int64_t ldx, const 
     a.stages = S;
     a.ntiles = (int)((p + XT_BM - 1) / XT_BM);
     a.kchunks = (int)((n + XT_BK - 1) / XT_BK);
+    a.nfit = nfit;
     // instruction descriptor: FP32 accumulate, TF32 A and B, both K-major, N = np, M = 128
     a.idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(np >> 3) << 17) | ((uint32_t)(XT_BM >> 4) << 24);
     uint32_t cols = 32;
