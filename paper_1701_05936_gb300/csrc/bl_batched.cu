@@ -440,19 +440,48 @@ __global__ void __launch_bounds__(256)
              const int64_t *__restrict__ w, int64_t cap, const float *__restrict__ beta, const double *__restrict__ yc,
              const int *__restrict__ active, double *r64, float *r32, int64_t ldr)
 {
+    // the working set's nonzero terms, 256 at a time: column, c_fj and b_j / s_fj,
+    // each formed once per block (FP64 division is slow on this part)
+    __shared__ int32_t j_s[256];
+    __shared__ double c_s[256], k_s[256];
     const int b = blockIdx.y, f = b % F;
     if (!active[b]) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i < n && in_fit(fold, i, f);
     double acc = live ? yc[(int64_t)b * n + i] : 0.0;
     const int64_t wb = w[b];
-    for (int64_t t = 0; t < wb; ++t) {
-        const int32_t j = idx[(int64_t)b * cap + t];
-        const float bj = beta[(int64_t)b * p + j];
-        if (bj == 0.f) continue;  // the same for every thread of the block
-        const int64_t o = (int64_t)f * p + j;
-        const double coef = (double)bj / sca[o];
-        if (live) acc = fma(-((double)X[(int64_t)j * ldx + i] - cen[o]), coef, acc);
+    for (int64_t t0 = 0; t0 < wb; t0 += 256) {
+        __syncthreads();  // the previous chunk is consumed
+        // ascending order of t within the chunk: a block-wide ordered compaction
+        const int64_t t = t0 + threadIdx.x;
+        int32_t j = 0;
+        float bj = 0.f;
+        if (t < wb) {
+            j = idx[(int64_t)b * cap + t];
+            bj = beta[(int64_t)b * p + j];
+        }
+        const bool nz = (t < wb) && bj != 0.f;
+        const unsigned int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const unsigned int bal = __ballot_sync(0xffffffffu, nz);
+        __shared__ unsigned int wcnt[8];
+        if (lane == 0) wcnt[wid] = __popc(bal);
+        __syncthreads();
+        unsigned int base = 0, total = 0;
+        for (unsigned int q = 0; q < 8; ++q) {
+            if (q < wid) base += wcnt[q];
+            total += wcnt[q];
+        }
+        if (nz) {
+            const unsigned int pos = base + __popc(bal & ((1u << lane) - 1u));
+            const int64_t o = (int64_t)f * p + j;
+            j_s[pos] = j;
+            c_s[pos] = cen[o];
+            k_s[pos] = (double)bj / sca[o];
+        }
+        __syncthreads();
+        if (live)
+            for (unsigned int e = 0; e < total; ++e)
+                acc = fma(-((double)X[(int64_t)j_s[e] * ldx + i] - c_s[e]), k_s[e], acc);
     }
     if (i < n) r64[(int64_t)b * n + i] = live ? acc : 0.0;
     if (i < ldr) r32[(int64_t)b * ldr + i] = live ? (float)acc : 0.f;

@@ -96,6 +96,125 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// ------------------------------------------------------- int8 designs
+// The z pass for int8 designs (genotype codes).  Three changes from k_zpass:
+// * r is staged transposed, rT[k * nchp + q] = r_{16 q + k}: the lanes of a warp
+//   read 16 consecutive words for each k instead of words 16 apart (a 16-way
+//   bank conflict);
+// * a byte v becomes the float v exactly without an integer-to-float
+//   conversion: v + 128 (the byte xor 0x80) is placed by a byte permute in the
+//   low mantissa byte of 1.5 * 2^23, whose unit in the last place is 1, and
+//   1.5 * 2^23 + 128 is subtracted;
+// * each warp takes two columns at once (j and j + the warp count), so that
+//   every load of r serves two dot products.
+// The accumulation order within a column (chunks per lane, then the warp
+// tree) is k_zpass's, so zpass_depth's bound holds as it is.
+__device__ __forceinline__ void unpack_i8_exact(const int4 &v, float *o)
+{
+    const int w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t u = (uint32_t)w[k] ^ 0x80808080u;
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            o[4 * k + b] = __int_as_float((int)__byte_perm(u, 0x4B400000u, 0x7650u + (uint32_t)b)) - 12583040.0f;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+    k_zpass_i8(const int8_t *__restrict__ X, int64_t n, int64_t p, int64_t ldx, const double *__restrict__ center,
+               const double *__restrict__ inv_scale, const double *__restrict__ xnorm, const float *__restrict__ r,
+               const DevScalars *__restrict__ sc_in, double lam, double alpha, double gamma,
+               const uint8_t *__restrict__ scan, const uint8_t *__restrict__ safe, uint8_t *__restrict__ working,
+               float *__restrict__ z, DevScalars *sc)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *rT = reinterpret_cast<float *>(smem);
+    const int64_t nch = (n + 15) / 16;
+    const int64_t nfull = n / 16;
+    const int64_t nchp = nch;  // one row of rT per k
+    for (int64_t i = threadIdx.x; i < nch * 16; i += blockDim.x) rT[(i & 15) * nchp + (i >> 4)] = (i < n) ? r[i] : 0.f;
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const double sum_r = sc_in->sum_r;
+    const double rnorm = sc_in->rnorm;
+    const double thr = lam * alpha;
+    const double inv_n = 1.0 / (double)n;
+    unsigned int viol = 0, cols = 0;
+    for (int64_t j0 = gw; j0 < p; j0 += 2 * nw) {
+        const int64_t j1 = j0 + nw;
+        const bool s0 = scan[j0] != 0, s1 = (j1 < p) && scan[j1] != 0;
+        if (!s0 && !s1) continue;
+        const int4 *c0 = reinterpret_cast<const int4 *>(X + j0 * ldx);
+        const int4 *c1 = reinterpret_cast<const int4 *>(X + (s1 ? j1 : j0) * ldx);
+        float a0 = 0.f, a1 = 0.f;
+        for (int64_t q0 = lane; q0 < nfull; q0 += 64) {
+            const int64_t qb = q0 + 32;
+            const bool hb = qb < nfull;
+            const int4 z4 = make_int4(0, 0, 0, 0);
+            const int4 v0 = s0 ? ld_stream(c0 + q0) : z4, w0 = s1 ? ld_stream(c1 + q0) : z4;
+            const int4 v1 = (s0 && hb) ? ld_stream(c0 + qb) : z4, w1 = (s1 && hb) ? ld_stream(c1 + qb) : z4;
+            float e[16], g[16];
+            unpack_i8_exact(v0, e);
+            unpack_i8_exact(w0, g);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const float rk = rT[k * nchp + q0];
+                a0 = fmaf(e[k], rk, a0);
+                a1 = fmaf(g[k], rk, a1);
+            }
+            if (hb) {
+                unpack_i8_exact(v1, e);
+                unpack_i8_exact(w1, g);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const float rk = rT[k * nchp + qb];
+                    a0 = fmaf(e[k], rk, a0);
+                    a1 = fmaf(g[k], rk, a1);
+                }
+            }
+        }
+        if (lane == 0)
+            for (int64_t i = nfull * 16; i < n; ++i) {
+                const float rk = rT[(i & 15) * nchp + (i >> 4)];
+                a0 = fmaf((float)X[j0 * ldx + i], rk, a0);
+                if (s1) a1 = fmaf((float)X[j1 * ldx + i], rk, a1);
+            }
+        a0 = warp_sum(a0);
+        a1 = warp_sum(a1);
+        if (lane == 0) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t j = h ? j1 : j0;
+                if (!(h ? s1 : s0)) continue;
+                ++cols;
+                const double f = inv_n * inv_scale[j];
+                const double zj = ((double)(h ? a1 : a0) - center[j] * sum_r) * f;
+                z[j] = (float)zj;
+                if (safe[j] && !working[j]) {
+                    // |fl(x'r) - x'r| <= gamma_m ||x_j|| ||r|| (Higham, Sec. 3.1, with
+                    // Cauchy-Schwarz), m = accumulation depth (zpass_depth)
+                    const double tau = gamma * xnorm[j] * rnorm * f * (1.0 + 1e-6) +
+                                       4e-16 * (fabs(center[j] * sum_r) * f + fabs(zj));
+                    if (fabs(zj) > thr - tau) {
+                        working[j] = 1;
+                        ++viol;
+                    }
+                }
+            }
+        }
+    }
+    viol = warp_sum(viol);
+    cols = warp_sum(cols);
+    if (lane == 0) {
+        if (viol) atomicAdd(&sc->n_viol, (unsigned long long)viol);
+        if (cols) atomicAdd(&sc->n_cols, (unsigned long long)cols);
+    }
+}
+
 // ------------------------------------------------ register-resident variant
 // For n <= 32 RPL VEC: lane l keeps the residual chunks l, l+32, ... in
 // registers for the whole launch (no shared-memory traffic), each warp owns a
@@ -325,7 +444,7 @@ int zpass_grid(int dtype, int64_t n, int num_sms)
     switch (dtype) {
     case 0: e = occ(k_zpass<double, zpass_unroll<double>()>); break;
     case 1: e = occ(k_zpass<float, zpass_unroll<float>()>); break;
-    case 3: e = occ(k_zpass<int8_t, zpass_unroll<int8_t>()>); break;
+    case 3: e = occ(k_zpass_i8); break;
     default: break;
     }
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
@@ -357,7 +476,17 @@ cudaError_t launch_zpass(int dtype, const ZpassArgs &a, DevScalars *sc, int grid
     switch (dtype) {
     case 0: return zpass_t<double>(a, sc, grid, st);
     case 1: return zpass_t<float>(a, sc, grid, st);
-    case 3: return zpass_t<int8_t>(a, sc, grid, st);
+    case 3: {
+        const size_t smem = zpass_smem(3, a.n);
+        if (smem > 48 * 1024) {
+            cudaError_t e = allow_smem(k_zpass_i8, smem);
+            if (e != cudaSuccess) return e;
+        }
+        k_zpass_i8<<<grid, 256, smem, st>>>((const int8_t *)a.X, a.n, a.p, a.ldx, a.center, a.inv_scale, a.xnorm,
+                                            (const float *)a.r, sc, a.lam, a.alpha, a.gamma, a.scan, a.safe,
+                                            a.working, a.z, sc);
+        return cudaGetLastError();
+    }
     default: return cudaErrorInvalidValue;
     }
 }
