@@ -103,6 +103,16 @@ int cuda_fail(bl_ctx *ctx, cudaError_t e, const char *what)
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// Times the batched z pass's tensor-core kernel alone (kind 10), from inside
+// launch_xtr: the events bracket that kernel, after the small kernels that
+// prepare its per-fit vectors.
+struct XtrTimer {
+    bl_ctx *ctx;
+    double bytes;
+    int slot;
+};
+void xtr_timer(void *user, int after);
+
 int ensure_ws(bl_ctx *ctx, int64_t n, int64_t p)
 {
     Workspace &w = ctx->ws;
@@ -210,6 +220,15 @@ void tend(bl_ctx *ctx, int slot, double bytes)
     if (slot < 0) return;
     ctx->launches[slot].bytes = bytes;
     cudaEventRecord(ctx->launches[slot].b, ctx->stream);
+}
+
+void xtr_timer(void *user, int after)
+{
+    XtrTimer *t = (XtrTimer *)user;
+    if (!after)
+        t->slot = tbegin(t->ctx, 10);
+    else
+        tend(t->ctx, t->slot, t->bytes);
 }
 
 // Fold finished launches into the totals (the stream must be idle).
@@ -769,10 +788,9 @@ extern "C" int bl_xtr_batched(bl_ctx *ctx, const void *X, int dtype, int64_t n, 
     double *nfd = (double *)(b + 2 * fitb + 256 * 4);
     CK(cudaMemcpyAsync(nfd, n_fit, (size_t)nfit * 8, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemsetAsync(&ctx->ws.sc->status, 0, sizeof(int), ctx->stream));
-    int slot = tbegin(ctx, 10);
+    XtrTimer xt{ctx, (double)n * (double)p * 4.0, -1};
     LAUNCH(3, launch_xtr((const float *)X, n, p, ldx, R, ldr, (int)nrhs, center, scale, ldc, nfd, (int)nfit, fit_of,
-                         cfit, insfit, sumr, nullptr, Z, ldz, ctx->ws.sc, ctx->num_sms, ctx->stream));
-    tend(ctx, slot, (double)n * (double)p * 4.0);
+                         cfit, insfit, sumr, nullptr, Z, ldz, ctx->ws.sc, ctx->num_sms, ctx->stream, xtr_timer, &xt));
     if ((st = sync_sc(ctx))) return st;
     if (ctx->sc_host->status & ST_TIMEOUT) return fail(ctx, BL_ERR_TIMEOUT, "batched z pass: a pipeline wait ran out");
     return BL_OK;
@@ -1182,10 +1200,9 @@ extern "C" int bl_fit_path_batched(bl_ctx *ctx, const void *X, int dtype, int64_
     std::vector<int> sth((size_t)B);
     bool not_converged = false;
     auto zpass = [&]() -> int {
-        int zs = tbegin(ctx, 10);
+        XtrTimer xt{ctx, (double)n * p * 4.0, -1};
         LAUNCH(3, launch_xtr(Xf, n, p, ldx, r32, ldr, B, cen, sca, p, nfit_d, F, fit_of, cfit, insfit, sumr, rnorm, Z, p,
-                             ctx->ws.sc, ctx->num_sms, s));
-        tend(ctx, zs, (double)n * p * 4.0);
+                             ctx->ws.sc, ctx->num_sms, s, xtr_timer, &xt));
         return BL_OK;
     };
     CK(cudaMemsetAsync(&ctx->ws.sc->status, 0, sizeof(int), s));

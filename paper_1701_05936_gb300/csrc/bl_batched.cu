@@ -308,10 +308,18 @@ __global__ void __launch_bounds__(256, 1)
             buf[q] = (ch < nch) ? __ldg(colv + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     };
+    // columns of the next D coordinates in flight in registers (a ring)
+    constexpr int D = (RPT <= 2) ? 4 : ((RPT <= 4) ? 2 : 1);
     auto sweep = [&](bool full, int64_t len, bool &moved, bool &newnz) {
-        float4 buf[RPT];
-        if (len > 0) load_col(buf, idx_s[full ? 0 : act_s[0]]);
-        for (int64_t t = 0; t < len; ++t) {
+        float4 buf[D][RPT];
+#pragma unroll
+        for (int s = 0; s < D; ++s)
+            if (s < len) load_col(buf[s], idx_s[full ? s : (int)act_s[s]]);
+        for (int64_t base = 0; base < len; base += D) {
+#pragma unroll
+        for (int s = 0; s < D; ++s) {
+            const int64_t t = base + s;
+            if (t >= len) break;
             const int tt = full ? (int)t : (int)act_s[t];
             const float cj = c_s[tt], isj = is_s[tt], gj = g_s[tt];
             const float old = (tt == prev_tt) ? prev_nb : beta_s[tt];
@@ -319,14 +327,14 @@ __global__ void __launch_bounds__(256, 1)
             float acc = 0.f;
 #pragma unroll
             for (int q = 0; q < RPT; ++q) {
-                const float e[VEC] = {buf[q].x, buf[q].y, buf[q].z, buf[q].w};
+                const float e[VEC] = {buf[s][q].x, buf[s][q].y, buf[s][q].z, buf[s][q].w};
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) {
                     xd[q][v] = ((vmask >> (q * VEC + v)) & 1u) ? e[v] - cj : 0.f;
                     acc = fmaf(xd[q][v], dr[q][v], acc);
                 }
             }
-            if (t + 1 < len) load_col(buf, idx_s[full ? (int)(t + 1) : (int)act_s[t + 1]]);
+            if (t + D < len) load_col(buf[s], idx_s[full ? (int)(t + D) : (int)act_s[t + D]]);
             float dot = warp_sum(acc);
             if (lane == 0) red[parity][wid] = dot;
             __syncthreads();
@@ -349,6 +357,7 @@ __global__ void __launch_bounds__(256, 1)
             moved |= (fabsf(d) >= tol);
             newnz |= (old == 0.f && fabsf(nb) >= tol);
             ++updates;
+        }
         }
     };
     auto out_of_time = [&]() -> bool {

@@ -227,10 +227,15 @@ cudaError_t launch_brecord(int k, int64_t n, int64_t p, int B, int F, const int8
                            const float *beta, const double *r64, const double *ybar, const double *lam_b, double alpha,
                            BatchPathOut *outs, int64_t *nnz_total, cudaStream_t st);
 int xtr_stages(int nrhs, size_t *smem);
+// The batched z pass: the per-right-hand-side sums and per-fit vectors, then the
+// tensor-core kernel.  around_main (nullable) is called with `user` and 0 just
+// before the tensor-core kernel is enqueued and with 1 just after, so that a
+// caller can time that kernel alone.
 cudaError_t launch_xtr(const float *X, int64_t n, int64_t p, int64_t ldx, const float *R, int64_t ldr, int nrhs,
                        const double *center, const double *scale, int64_t ldc, const double *n_fit_dev, int nfit,
                        const int32_t *fit_of, float *cfit, float *insfit, float *sumr, double *rnorm, float *Z,
-                       int64_t ldz, DevScalars *sc, int num_sms, cudaStream_t st);
+                       int64_t ldz, DevScalars *sc, int num_sms, cudaStream_t st,
+                       void (*around_main)(void *user, int after) = nullptr, void *user = nullptr);
 // Residual-form CD in blocks of consecutive coordinates in one CTA (needs R
 // from launch_gram); cd_blk_ok tells whether this build covers the shape.
 bool cd_blk_ok(int dtype, int64_t n);

@@ -364,7 +364,8 @@ int xtr_stages(int nrhs, size_t *smem)
 cudaError_t launch_xtr(const float *X, int64_t n, int64_t p, int64_t ldx, const float *R, int64_t ldr, int nrhs,
                        const double *center, const double *scale, int64_t ldc, const double *n_fit_dev, int nfit,
                        const int32_t *fit_of, float *cfit, float *insfit, float *sumr, double *rnorm, float *Z,
-                       int64_t ldz, DevScalars *sc, int num_sms, cudaStream_t st)
+                       int64_t ldz, DevScalars *sc, int num_sms, cudaStream_t st,
+                       void (*around_main)(void *user, int after), void *user)
 {
     size_t smem = 0;
     const int S = xtr_stages(nrhs, &smem);
@@ -402,8 +403,11 @@ cudaError_t launch_xtr(const float *X, int64_t n, int64_t p, int64_t ldx, const 
     cudaError_t e = allow_smem(k_xtr_tf32, smem);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<int64_t>(a.ntiles, num_sms);
+    if (around_main) around_main(user, 0);
     k_xtr_tf32<<<grid, XT_THREADS, smem, st>>>(mx, mr, a);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (around_main) around_main(user, 1);
+    return e;
 }
 
 }  // namespace bl
