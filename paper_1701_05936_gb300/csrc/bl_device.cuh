@@ -77,13 +77,19 @@ template <typename A> __device__ __forceinline__ void unpack(const uint4 &v, A *
         o[2 * q + 1] = (A)__uint_as_float(w[q] & 0xffff0000u);
     }
 }
+// int8: each byte v becomes the float v exactly without an integer-to-float
+// conversion: v + 128 (the byte xor 0x80) is placed by a byte permute in the
+// low mantissa byte of 1.5 * 2^23 (whose unit in the last place is 1), and
+// 1.5 * 2^23 + 128 is subtracted.  The same values as (A)(int8_t)byte.
 template <typename A> __device__ __forceinline__ void unpack(const int4 &v, A *o)
 {
     const int w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
+        const uint32_t u = (uint32_t)w[k] ^ 0x80808080u;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) o[4 * k + b] = (A)(int8_t)((w[k] >> (8 * b)) & 0xff);
+        for (int b = 0; b < 4; ++b)
+            o[4 * k + b] = (A)(__int_as_float((int)__byte_perm(u, 0x4B400000u, 0x7650u + (uint32_t)b)) - 12583040.0f);
     }
 }
 

@@ -101,26 +101,12 @@ __global__ void __launch_bounds__(256)
 // * r is staged transposed, rT[k * nchp + q] = r_{16 q + k}: the lanes of a warp
 //   read 16 consecutive words for each k instead of words 16 apart (a 16-way
 //   bank conflict);
-// * a byte v becomes the float v exactly without an integer-to-float
-//   conversion: v + 128 (the byte xor 0x80) is placed by a byte permute in the
-//   low mantissa byte of 1.5 * 2^23, whose unit in the last place is 1, and
-//   1.5 * 2^23 + 128 is subtracted;
+// * each byte becomes its float exactly by a byte permute (unpack, without an
+//   integer-to-float conversion);
 // * each warp takes two columns at once (j and j + the warp count), so that
 //   every load of r serves two dot products.
 // The accumulation order within a column (chunks per lane, then the warp
 // tree) is k_zpass's, so zpass_depth's bound holds as it is.
-__device__ __forceinline__ void unpack_i8_exact(const int4 &v, float *o)
-{
-    const int w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const uint32_t u = (uint32_t)w[k] ^ 0x80808080u;
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-            o[4 * k + b] = __int_as_float((int)__byte_perm(u, 0x4B400000u, 0x7650u + (uint32_t)b)) - 12583040.0f;
-    }
-}
-
 __global__ void __launch_bounds__(256)
     k_zpass_i8(const int8_t *__restrict__ X, int64_t n, int64_t p, int64_t ldx, const double *__restrict__ center,
                const double *__restrict__ inv_scale, const double *__restrict__ xnorm, const float *__restrict__ r,
@@ -158,8 +144,8 @@ __global__ void __launch_bounds__(256)
             const int4 v0 = s0 ? ld_stream(c0 + q0) : z4, w0 = s1 ? ld_stream(c1 + q0) : z4;
             const int4 v1 = (s0 && hb) ? ld_stream(c0 + qb) : z4, w1 = (s1 && hb) ? ld_stream(c1 + qb) : z4;
             float e[16], g[16];
-            unpack_i8_exact(v0, e);
-            unpack_i8_exact(w0, g);
+            unpack(v0, e);
+            unpack(w0, g);
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
                 const float rk = rT[k * nchp + q0];
@@ -167,8 +153,8 @@ __global__ void __launch_bounds__(256)
                 a1 = fmaf(g[k], rk, a1);
             }
             if (hb) {
-                unpack_i8_exact(v1, e);
-                unpack_i8_exact(w1, g);
+                unpack(v1, e);
+                unpack(w1, g);
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     const float rk = rT[k * nchp + qb];

@@ -264,6 +264,56 @@ def block_factor(n=1000, p=1_000_000, block=100, k=40, lo=0.3, hi=1.0, snr=3.0, 
                    {"block": block, "k": k, "snr": snr, "sigma": sigma})
 
 
+def _fill_normal_f32(X: np.ndarray, n: int, key: np.ndarray) -> None:
+    """X[j, :n] ~ N(0,1) in FP32, drawn in chunks of columns, chunk c from the
+    key's Philox stream jumped c + 1 times, on worker threads (the values depend
+    on the key only)."""
+    p = X.shape[0]
+    chunk = max(1, (1 << 22) // max(n, 1))
+
+    def fill(c: int, j0: int) -> None:
+        j1 = min(p, j0 + chunk)
+        gc = np.random.Generator(np.random.Philox(key=key).jumped(c + 1))
+        X[j0:j1, :n] = gc.standard_normal((j1 - j0, n), dtype=np.float32)
+
+    starts = list(range(0, p, chunk))
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1, len(starts))) as ex:
+        list(ex.map(fill, range(len(starts)), starts))
+
+
+def many_problems(nprob: int = 256, n_range=(100, 2000), p_range=(1000, 50_000), k: int = 10, snr: float = 3.0,
+                  workload: int = 7, replicate: int = 0, which=None) -> list:
+    """Independent lasso problems of mixed sizes (the many-problems workload):
+    n ~ U{n_range}, p ~ U{p_range} (inclusive), X iid N(0,1) in FP32, k nonzero
+    beta = +-1 at random indices, noise for sample Var(X beta)/sigma^2 = snr,
+    100 lambdas to 0.05 lambda_max, alpha 1.  Problem i is keyed by
+    (20170120, workload * 1000 + replicate * 1000 * 1000 + i).  which (optional):
+    the indices of the problems to draw (the sizes of all nprob are drawn, so a
+    sample is the same problems as in the full set)."""
+    g = rng_for(workload, replicate)
+    sizes = [(int(g.integers(n_range[0], n_range[1] + 1)), int(g.integers(p_range[0], p_range[1] + 1)))
+             for _ in range(nprob)]
+    out = []
+    for i, (n, p) in enumerate(sizes):
+        if which is not None and i not in which:
+            continue
+        key = np.array([SEED_BASE, workload * 1000 + replicate * 1000 * 1000 + i], dtype=np.uint64)
+        X, ldx = _alloc_x(n, p, "f32", 0.0)
+        _fill_normal_f32(X, n, key)
+        gi = np.random.Generator(np.random.Philox(key=key))
+        beta = np.zeros(p)
+        kk = min(k, p)
+        idx = gi.choice(p, size=kk, replace=False)
+        beta[idx] = np.where(gi.random(kk) < 0.5, -1.0, 1.0)
+        signal = X[idx, :n].astype(np.float64).T @ beta[idx]
+        var_sig = float(np.var(signal))
+        sigma = np.sqrt(var_sig / snr) if var_sig > 0 else 1.0
+        y = signal + sigma * gi.standard_normal(n)
+        out.append(Problem(f"many_{i}_{n}x{p}_f32", X, y, n, p, ldx, "f32", beta, 1.0, 0.05, 100, 1e-7,
+                           {"k": kk, "snr": snr, "sigma": sigma}))
+    return out
+
+
 def batched_residuals(bp: BatchedProblem, replicate: int = 0):
     """Residual-shaped test vectors for the batched z pass: right-hand side
     b = r * (nfolds + 1) + f is N(0,1) on fit f's rows and 0 elsewhere.

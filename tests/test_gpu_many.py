@@ -48,3 +48,28 @@ def test_fit_many_reports_per_problem_status():
         assert res[1]["nnz"] == 0 and res[0]["nnz"] > 0
     finally:
         ctx.close()
+
+
+def test_fit_many_at_full_sizes_matches_oracle_on_a_sample():
+    """Three problems of the many-problems workload at its real sizes (n up to
+    2000, p up to 50,000; here 1387 x 26,290, 1747 x 21,641 and 1418 x 46,976),
+    solved together through bl_fit_many, each against the oracle on all host
+    cores."""
+    import os
+    pick = [3, 17, 42]
+    probs = synth.many_problems(nprob=64, which=pick)
+    assert max(q.n * q.p for q in probs) > 10_000_000
+    ctx = bl.Context(0)
+    used = oracle.set_threads(len(os.sched_getaffinity(0)))
+    try:
+        dev = [(torch.from_numpy(q.X).to(DEV), q.n, torch.from_numpy(q.y).to(DEV)) for q in probs]
+        res = bl.bl_fit_many(ctx, dev, alpha=1.0, ratio=0.05, nlambda=100, eps=1e-7, cd_mode=bl.BL_CD_BLOCKED,
+                             concurrency=3)
+        torch.cuda.synchronize()
+        for q, r in zip(probs, res):
+            assert r["status"] == bl.BL_OK
+            o = oracle.fit_path(q.dense_f64(), q.y, 1.0, ratio=0.05, nlambda=100, eps=1e-7)
+            compare_paths(q, r, o, 1e-5, allow_exempt=2, label=f"many {q.n}x{q.p}")
+    finally:
+        oracle.set_threads(1)
+        ctx.close()
