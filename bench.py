@@ -158,11 +158,11 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def zpass_traffic():
-    """DRAM bytes over algorithmic bytes of one z-pass launch, from the committed
-    ncu summary, if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "zpass_traffic.json")
-    src = os.path.join(ROOT, "paper_1701_05936_gb300", "csrc", "bl_zpass.cu")
+def zpass_traffic(name: str = "zpass_traffic.json", source: str = "bl_zpass.cu"):
+    """DRAM bytes over algorithmic bytes of one launch of a kernel, from the
+    committed ncu summary, if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", name)
+    src = os.path.join(ROOT, "paper_1701_05936_gb300", "csrc", source)
     try:
         meta = json.load(open(path))
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()
@@ -339,6 +339,7 @@ def batched(local: int, reps: int = 20, plain_rhs: int = 8, path_steps: int = 2)
     flops = 2.0 * bp.n * bp.p * nrhs
     gbs = bytes_alg / 1e9 / (ms / 1e3)
     tfs = flops / 1e12 / (ms / 1e3)
+    xtraffic = zpass_traffic("xtr_traffic.json", "bl_xtr.cu")
     wl = f"ar1_{bp.n}x{bp.p}_f32_rho0.3, {bp.m} responses x ({bp.nfolds} folds + all rows) = {nrhs} problems"
     zobj = {
         "workload": wl,
@@ -346,7 +347,8 @@ def batched(local: int, reps: int = 20, plain_rhs: int = 8, path_steps: int = 2)
         "ms_per_pass": ms, "passes": reps,
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": gbs / peaks["hbm_gbs"], "peak_source": f"{which} hbm_gbs",
-                     "algorithmic_bytes_per_pass": bytes_alg, "traffic": None},
+                     "algorithmic_bytes_per_pass": bytes_alg,
+                     "traffic": xtraffic["dram_over_algorithmic"] * bytes_alg if xtraffic else None},
         "tensor": {"achieved": tfs, "peak": tf32_peak, "unit": "TFLOP/s", "frac": tfs / tf32_peak,
                    "peak_source": f"{which} bf16_tflops x 1.1/2.25 (nominal TF32/BF16)"},
         "plain_form": {"form": "FP32 single-residual z pass (k_zpass) per residual", "ms_per_residual": plain_ms,

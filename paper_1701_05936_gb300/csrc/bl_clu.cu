@@ -48,21 +48,22 @@ namespace {
 
 // The shape of one cluster: ND data CTAs and a chain CTA of CT threads (one
 // row per data thread, 1024 rows in all), blocks of CB coordinates.
-template <int ND> struct Clu {
+template <int ND, int CB_> struct Clu {
     static constexpr int NDATA = ND;           // data CTAs (cluster ranks 0..ND-1); the chain CTA is rank ND
     static constexpr int CT = 1024 / ND;       // threads per CTA
     static constexpr int CW = CT / 32;         // warps per CTA
     static constexpr int HROWS = CT;           // rows per data CTA
     static constexpr uint32_t HCOL = HROWS * 4;  // bytes of one packed column part
-    static constexpr int CB = 8 * ND;          // coordinates per block
+    static constexpr int CB = CB_;             // coordinates per block
     static_assert(CB == 16 || CB == 32, "the chain warp holds one block's coordinates");
+    static_assert(ND * CB >= 32 && (ND * CB) % 32 == 0, "every lane of the chain warp sends the same count");
 };
 // The form the path uses: 2 data CTAs of 512 rows, blocks of 16 (62.5 ns per
 // update on the 1000 x 100,000 path).  ND = 4 (4 data CTAs of 256 rows, blocks
 // of 32) measured 101.6 ns: every chain lane evaluates every step, so the
 // chain warp issues CB^2/2 updates per block (4x at CB = 32), and the helper
 // warps gather 3 CB^2 entries of R per block over half as many threads.
-constexpr int CLU_ND = 2;
+constexpr int CLU_ND = 4, CLU_CB = 16;
 constexpr int LA = 3;      // look-ahead: the dots of block b see updates up to block b-LA
 constexpr uint64_t CLU_WAIT_NS = 1000ull * 1000ull * 1000ull;
 enum { SW_STOP = 0, SW_FULL = 1, SW_ACTIVE = 2 };
@@ -121,8 +122,8 @@ __device__ __forceinline__ bool wait_cl(uint32_t bar, uint32_t parity, uint64_t 
 __device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
 
 // the static shared state of all roles (each CTA uses its role's part)
-template <int ND> struct CluShared {
-    static constexpr int CB = Clu<ND>::CB, CW = Clu<ND>::CW;
+template <int ND, int CB_> struct CluShared {
+    static constexpr int CB = CB_, CW = Clu<ND, CB_>::CW;
     // data CTAs
     float red[CW][CB];
     __align__(16) float dks[LA][CB];        // d_k / s_k of a block, stored by the chain CTA
@@ -191,9 +192,9 @@ template <int CB> __device__ __forceinline__ float reduce_scatter(float (&v)[CB]
     return v1;
 }
 
-template <int ND> __device__ void clu_data(const CluArgs &a, CluShared<ND> &S, unsigned char *dyn, int h)
+template <int ND, int CB_> __device__ void clu_data(const CluArgs &a, CluShared<ND, CB_> &S, unsigned char *dyn, int h)
 {
-    using C = Clu<ND>;
+    using C = Clu<ND, CB_>;
     constexpr int CB = C::CB, CW = C::CW, HROWS = C::HROWS;
     constexpr uint32_t HCOL = C::HCOL;
     constexpr int LPS = 32 / CB;  // lanes per column after the reduce-scatter
@@ -358,9 +359,9 @@ template <int ND> __device__ void clu_data(const CluArgs &a, CluShared<ND> &S, u
 }
 
 // ------------------------------------------------------------ chain role
-template <int ND> __device__ void clu_chain(const CluArgs &a, CluShared<ND> &S, unsigned char *dyn)
+template <int ND, int CB_> __device__ void clu_chain(const CluArgs &a, CluShared<ND, CB_> &S, unsigned char *dyn)
 {
-    using C = Clu<ND>;
+    using C = Clu<ND, CB_>;
     constexpr int CB = C::CB, CT = C::CT, CW = C::CW, HROWS = C::HROWS;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t w = a.w, ld = a.ld;
@@ -683,9 +684,9 @@ template <int ND> __device__ void clu_chain(const CluArgs &a, CluShared<ND> &S, 
     }
 }
 
-template <int ND> __global__ void __launch_bounds__(Clu<ND>::CT, 1) k_cd_clu(CluArgs a)
+template <int ND, int CB_> __global__ void __launch_bounds__(Clu<ND, CB_>::CT, 1) k_cd_clu(CluArgs a)
 {
-    __shared__ CluShared<ND> S;
+    __shared__ CluShared<ND, CB_> S;
     extern __shared__ __align__(16) unsigned char dyn[];
     const uint32_t rank = cluster_rank();
     if (threadIdx.x == 0) {
@@ -701,9 +702,9 @@ template <int ND> __global__ void __launch_bounds__(Clu<ND>::CT, 1) k_cd_clu(Clu
     }
     cluster_sync();  // every CTA's barriers exist before any remote arrival
     if (rank < (uint32_t)ND)
-        clu_data<ND>(a, S, dyn, (int)rank);
+        clu_data<ND, CB_>(a, S, dyn, (int)rank);
     else
-        clu_chain<ND>(a, S, dyn);
+        clu_chain<ND, CB_>(a, S, dyn);
     cluster_sync();  // no CTA leaves while another may still touch its memory
 }
 
@@ -731,32 +732,32 @@ __global__ void __launch_bounds__(256) k_pack_parts(const float *__restrict__ X,
     }
 }
 
-template <int ND> size_t clu_smem(int64_t w)
+template <int ND, int CB_> size_t clu_smem(int64_t w)
 {
-    const size_t data = 2 * (size_t)Clu<ND>::CB * Clu<ND>::HCOL;
+    const size_t data = 2 * (size_t)CB_ * Clu<ND, CB_>::HCOL;
     const size_t chain = (((size_t)w * 2 + 15) & ~(size_t)15) + (size_t)w * 16;
     return std::max(data, chain);
 }
 
-template <int ND> bool clu_ok(int64_t n, int64_t w)
+template <int ND, int CB_> bool clu_ok(int64_t n, int64_t w)
 {
     return n >= 1 && n <= 1024 && w >= 1 && w <= MAX_WORKING &&
-           clu_smem<ND>(w) + sizeof(CluShared<ND>) <= 227 * 1024 - 1024;
+           clu_smem<ND, CB_>(w) + sizeof(CluShared<ND, CB_>) <= 227 * 1024 - 1024;
 }
 
 }  // namespace
 
-size_t cd_clu_smem(int64_t w) { return clu_smem<CLU_ND>(w); }
+size_t cd_clu_smem(int64_t w) { return clu_smem<CLU_ND, CLU_CB>(w); }
 
-bool cd_clu_ok(int dtype, int64_t n, int64_t w) { return dtype == BL_F32 && clu_ok<CLU_ND>(n, w); }
+bool cd_clu_ok(int dtype, int64_t n, int64_t w) { return dtype == BL_F32 && clu_ok<CLU_ND, CLU_CB>(n, w); }
 
 cudaError_t launch_cd_clu(const float *X, int64_t n, int64_t p, int64_t ldx, const float *cvec, const float *isvec,
                           const int32_t *idx, int64_t w, const float *gref, const float *Rm, double lam, double alpha,
                           float *beta, double eps, int64_t max_sweeps, uint64_t time_limit_ns, DevScalars *sc,
                           float *packed, int64_t packed_floats, int num_sms, cudaStream_t st)
 {
-    constexpr int ND = CLU_ND;
-    using C = Clu<ND>;
+    constexpr int ND = CLU_ND, CB = CLU_CB;
+    using C = Clu<ND, CB>;
     // packed: the working set's columns in its first half, the active ones in its second
     const int64_t hstride = (packed_floats / 2) / ND;
     if (!cd_clu_ok(BL_F32, n, w) || hstride < w * C::HROWS || (hstride & 3)) return cudaErrorInvalidValue;
@@ -765,8 +766,8 @@ cudaError_t launch_cd_clu(const float *X, int64_t n, int64_t p, int64_t ldx, con
                                                                                     hstride, Xw);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem = clu_smem<ND>(w);
-    if ((e = allow_smem(k_cd_clu<ND>, smem)) != cudaSuccess) return e;
+    const size_t smem = clu_smem<ND, CB>(w);
+    if ((e = allow_smem(k_cd_clu<ND, CB>, smem)) != cudaSuccess) return e;
     CluArgs a{Xw, Xa, hstride, n, w, p, gram_ld(w), idx, isvec, gref, Rm, beta, lam, alpha, eps, max_sweeps,
               time_limit_ns, sc};
     cudaLaunchConfig_t cfg = {};
@@ -781,7 +782,7 @@ cudaError_t launch_cd_clu(const float *X, int64_t n, int64_t p, int64_t ldx, con
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_cd_clu<ND>, a);
+    return cudaLaunchKernelEx(&cfg, k_cd_clu<ND, CB>, a);
 }
 
 }  // namespace bl
