@@ -59,11 +59,12 @@ template <int ND, int CB_> struct Clu {
     static_assert(ND * CB >= 32 && (ND * CB) % 32 == 0, "every lane of the chain warp sends the same count");
 };
 // The form the path uses: 2 data CTAs of 512 rows, blocks of 16 (62.5 ns per
-// update on the 1000 x 100,000 path).  ND = 4 (4 data CTAs of 256 rows, blocks
-// of 32) measured 101.6 ns: every chain lane evaluates every step, so the
-// chain warp issues CB^2/2 updates per block (4x at CB = 32), and the helper
-// warps gather 3 CB^2 entries of R per block over half as many threads.
-constexpr int CLU_ND = 4, CLU_CB = 16;
+// update on the 1000 x 100,000 path).  Measured and not kept: 4 data CTAs of
+// 256 rows with blocks of 32 (101.6 ns: every chain lane evaluates every step,
+// so the chain warp issues CB^2/2 updates per block, and the helper warps
+// gather 3 CB^2 entries of R per block over half as many threads) and with
+// blocks of 16 (63.4 ns: the chain CTA, not the data CTAs, sets the pace).
+constexpr int CLU_ND = 2, CLU_CB = 16;
 constexpr int LA = 3;      // look-ahead: the dots of block b see updates up to block b-LA
 constexpr uint64_t CLU_WAIT_NS = 1000ull * 1000ull * 1000ull;
 enum { SW_STOP = 0, SW_FULL = 1, SW_ACTIVE = 2 };
