@@ -222,8 +222,10 @@ __global__ void __launch_bounds__(256)
 // fit's rows only: thread t owns row chunks t, t + 256, ... and a row outside
 // the fit (or past n) contributes x - c = 0, so dr stays 0 there.  The next
 // coordinate's column chunks are prefetched into registers.
+// Up to 2048 rows (RPT <= 2) two CTAs share an SM, so that a batch of more
+// problems than SMs (176 on 152) runs in one wave.
 template <int RPT>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(256, (RPT <= 2) ? 2 : 1)
     k_bcd(const float *__restrict__ X, int64_t n, int64_t ldx, int64_t p, int F, const int8_t *__restrict__ fold,
           const double *__restrict__ nfit, const float *__restrict__ c32, const float *__restrict__ is32,
           const int32_t *__restrict__ idx_all, const int64_t *__restrict__ w_all, int64_t cap, int64_t lds,
