@@ -121,10 +121,6 @@ __device__ __forceinline__ bool wait_cl(uint32_t bar, uint32_t parity, uint64_t 
     return true;
 }
 __device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
-__device__ __forceinline__ void mbar_arrive_cta(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
 
 // the static shared state of all roles (each CTA uses its role's part)
 template <int ND, int CB_> struct CluShared {
@@ -144,10 +140,6 @@ template <int ND, int CB_> struct CluShared {
     int opos[2][CB];                        // block b's operands (warp 1 for warp 0), at [b & 1]
     float ob[2][CB], ois[2][CB], og[2][CB], ox2[2][CB];
     __align__(8) uint64_t pF[LA];
-    // hand-offs between the chain CTA's roles, per block g (slot g % 3, operand buffer g % 2):
-    // R entries stored (helpers) and consumed (warp 0), operands stored (warp 1) and
-    // consumed (warp 0), steps stored (warp 0) for warp 1's b-2 term
-    __align__(8) uint64_t qRdy[3], qFre[3], opRdy[2], opFre[2], dpRdy[2];
     int dkind, dlen, dsame;                 // the sweep descriptor the data CTAs read
     // all
     int flag, fail;
@@ -454,9 +446,10 @@ template <int ND, int CB_> __device__ void clu_chain(const CluArgs &a, CluShared
     };
     // Warp 1: block blk's operands for warp 0 (position, b, 1/s, g_ref) and the
     // update of block blk-2, which its dots do not see, sum_m d_m R_km
-    auto prep = [&](int64_t blk, int qs, int o) {
+    auto prep = [&](int64_t blk, int qs) {
         const int64_t t0 = blk * CB;
         const int cnt = (int)((len - t0 < CB) ? len - t0 : CB);
+        const int o = (int)(blk & 1);
         if (lane < CB) {
             int pos = 0;
             float b = 0.f, is = 0.f, gv = 0.f, x2 = 0.f;
@@ -466,7 +459,7 @@ template <int ND, int CB_> __device__ void clu_chain(const CluArgs &a, CluShared
                 is = is_s[pos];
                 gv = g_s[pos];
                 if (blk >= 2) {
-                    const float *dp = S.dph[o];  // block blk-2's steps (the same buffer parity)
+                    const float *dp = S.dph[blk & 1];  // block blk-2's steps
 #pragma unroll
                     for (int m = 0; m < CB; ++m) x2 = fmaf(dp[m], S.QX2[qs][m * CB + lane], x2);
                 }
@@ -509,76 +502,37 @@ template <int ND, int CB_> __device__ void clu_chain(const CluArgs &a, CluShared
         if (!ok || kind == SW_STOP) break;
         const int64_t nblk = (len + CB - 1) / CB;
         if (!same) q0_ok = false;
-        // Block g of the launch (this sweep's block blk = g - g0) uses exchange and
-        // R slot g % 3 (exchange parity (g / 3) & 1) and operand buffer g % 2.  The
-        // roles run at their own pace, linked only by the hand-off barriers: the
-        // helpers fill R slot g once block g - 3 has left it, warp 1 prepares block
-        // g's operands once its R entries are in and block g - 2 has left the
-        // buffer, and warp 0 runs block g once its operands and the R entries of g
-        // and g + 1 are in.  Every wait is bounded; a role that gives up raises
-        // fail, and the others give up on the hand-offs it no longer makes.
-        const uint32_t g0 = g;
-        const bool use_q0 = q0_ok;  // this sweep's block 0 takes its R entries from QT0
+        // the block's slot (exchange and R entries alike: three of each) and the
+        // parity of its exchange phase, kept as counters: slot = g % 3, parity = (g / 3) & 1
+        int q0 = (int)(g % 3u);
+        uint32_t par = (g / 3u) & 1u;
+        if (helper && nblk > 0) {
+            if (q0_ok) {
+                for (int e = hid; e < CB * CB; e += HELP) S.QT[q0][e] = S.QT0[e];
+            } else {
+                load_q(0, q0, kind == SW_ACTIVE);
+            }
+            if (nblk > 1) load_q(1, (q0 + 1) % 3, false);
+        }
+        if (wid == 1 && nblk > 0) prep(0, q0);
         // block 0's partials: armed now, each later block's right after the wait before it
-        if (tid == 0 && nblk > 0) mbar_expect_tx(smem_u32(&S.pF[g0 % 3u]), ND * CB * 4);
+        if (tid == 0 && nblk > 0) mbar_expect_tx(smem_u32(&S.pF[q0]), ND * CB * 4);
         q0_ok = kind == SW_ACTIVE;
         bool moved = false, newnz = false;  // lanes of warp 0
         float x1acc = 0.f;  // lane CB + i (CB = 16) or i (CB = 32) of warp 0: coordinate i of the next
                             // block's correction for this block's steps
         __syncthreads();
-        if (helper) {
-            for (int64_t blk = 0; blk < nblk; ++blk) {
-                const uint32_t gb = g0 + (uint32_t)blk;
-                const int sq = (int)(gb % 3u);
-                bool got = true;
-                if (gb >= 3u) got = mbar_wait_bounded(smem_u32(&S.qFre[sq]), ((gb / 3u) - 1u) & 1u, CLU_WAIT_NS);
-                if (!__all_sync(0xffffffffu, got)) {
-                    S.fail = 1;
-                    break;
-                }
-                if (blk == 0 && use_q0) {
-                    for (int e = hid; e < CB * CB; e += HELP) S.QT[sq][e] = S.QT0[e];
-                } else {
-                    load_q(blk, sq, blk == 0 && kind == SW_ACTIVE);
-                }
-                mbar_arrive_cta(smem_u32(&S.qRdy[sq]));
-                if (__any_sync(0xffffffffu, S.fail != 0)) break;
-            }
-        } else if (wid == 1) {
-            for (int64_t blk = 0; blk < nblk; ++blk) {
-                const uint32_t gb = g0 + (uint32_t)blk;
-                const int sq = (int)(gb % 3u), ob = (int)(gb & 1u);
-                bool got = mbar_wait_bounded(smem_u32(&S.qRdy[sq]), (gb / 3u) & 1u, CLU_WAIT_NS);
-                if (gb >= 2u) {
-                    got = got && mbar_wait_bounded(smem_u32(&S.opFre[ob]), ((gb >> 1) - 1u) & 1u, CLU_WAIT_NS);
-                    got = got && mbar_wait_bounded(smem_u32(&S.dpRdy[ob]), ((gb >> 1) - 1u) & 1u, CLU_WAIT_NS);
-                }
-                if (!__all_sync(0xffffffffu, got)) {
-                    S.fail = 1;
-                    break;
-                }
-                prep(blk, sq, ob);
-                mbar_arrive_cta(smem_u32(&S.opRdy[ob]));
-                if (__any_sync(0xffffffffu, S.fail != 0)) break;
-            }
-        } else if (wid == 0) {
-            for (int64_t blk = 0; blk < nblk; ++blk) {
-                const uint32_t gb = g0 + (uint32_t)blk;
-                const int q0 = (int)(gb % 3u), q1 = (int)((gb + 1u) % 3u);
-                const uint32_t ps = (uint32_t)q0, par = (gb / 3u) & 1u;
-                const int cnt = (int)((len - blk * CB < CB) ? len - blk * CB : CB);
-                bool got = mbar_wait_bounded(smem_u32(&S.opRdy[gb & 1u]), (gb >> 1) & 1u, CLU_WAIT_NS);
-                got = got && mbar_wait_bounded(smem_u32(&S.qRdy[q0]), (gb / 3u) & 1u, CLU_WAIT_NS);
-                if (blk + 1 < nblk)
-                    got = got && mbar_wait_bounded(smem_u32(&S.qRdy[q1]), ((gb + 1u) / 3u) & 1u, CLU_WAIT_NS);
-                if (!__all_sync(0xffffffffu, got)) {
-                    S.fail = 1;
-                    break;
-                }
+        for (int64_t blk = 0; blk < nblk; ++blk, ++g) {
+            const int q1 = (q0 == 2) ? 0 : q0 + 1, q2 = (q1 == 2) ? 0 : q1 + 1;
+            const uint32_t ps = (uint32_t)q0;
+            const int cnt = (int)((len - blk * CB < CB) ? len - blk * CB : CB);
+            if (helper && blk + 2 < nblk) load_q(blk + 2, q2, false);
+            if (wid == 1 && blk + 1 < nblk) prep(blk + 1, q1);
+            if (wid == 0) {
                 // operands (from warp 1) and the updates of blocks b-1 (accumulated by
                 // lanes 16-31 during the last chain) and b-2 (from warp 1), which
                 // the dots did not see
-                const int o = (int)(gb & 1u);
+                const int o = (int)(blk & 1);
                 const float x1 = (CB == 32) ? x1acc : __shfl_down_sync(0xffffffffu, x1acc, CB & 31);
                 const bool mine = lane < cnt;  // lanes >= CB have cnt <= CB <= lane
                 int my_pos = 0;
@@ -642,23 +596,19 @@ template <int ND, int CB_> __device__ void clu_chain(const CluArgs &a, CluShared
                         newnz |= (my_b == 0.f && fabsf(nb) >= tol);
                         beta_s[my_pos] = nb;
                     }
-                    S.dph[gb & 1u][lane] = dv;
+                    S.dph[blk & 1][lane] = dv;
                 }
                 dsv = __shfl_sync(0xffffffffu, dsv, lane & (CB - 1));
 #pragma unroll
                 for (int q = 0; q < SPL; ++q)
                     st_async_f32(peer_dks[q] + (ps * CB + (uint32_t)(lane & (CB - 1))) * 4, dsv, peer_dsF[q] + ps * 8);
                 updates += (unsigned long long)cnt;
-            
-                __syncwarp();
-                mbar_arrive_cta(smem_u32(&S.dpRdy[gb & 1u]));
-                mbar_arrive_cta(smem_u32(&S.opFre[gb & 1u]));
-                mbar_arrive_cta(smem_u32(&S.qFre[q0]));
-                if (__any_sync(0xffffffffu, S.fail != 0)) break;
             }
+            __syncthreads();  // R entries two blocks ahead and the next block's operands are in place
+            if (S.fail) break;
+            if (q0 == 2) par ^= 1u;
+            q0 = q1;
         }
-        g += (uint32_t)nblk;
-        __syncthreads();  // every role is done with the sweep
         // end of the sweep: decide the next one
         if (wid == 0) {
             const bool am = __any_sync(0xffffffffu, moved), an = __any_sync(0xffffffffu, newnz);
@@ -749,17 +699,6 @@ template <int ND, int CB_> __global__ void __launch_bounds__(Clu<ND, CB_>::CT, 1
             mbar_init(smem_u32(&S.pF[s]), 1);
         }
         mbar_init(smem_u32(&S.desc), 1);
-        constexpr int CW = Clu<ND, CB_>::CW;
-        constexpr int HELP = 32 * (CW - 2 - (CW / 4 - 1));  // the chain CTA's helper threads
-        for (int q = 0; q < 3; ++q) {
-            mbar_init(smem_u32(&S.qRdy[q]), HELP);
-            mbar_init(smem_u32(&S.qFre[q]), 32);
-        }
-        for (int q = 0; q < 2; ++q) {
-            mbar_init(smem_u32(&S.opRdy[q]), 32);
-            mbar_init(smem_u32(&S.opFre[q]), 32);
-            mbar_init(smem_u32(&S.dpRdy[q]), 32);
-        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     cluster_sync();  // every CTA's barriers exist before any remote arrival
