@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-many", action="store_true", help="skip the many-problems object")
     ap.add_argument("--no-genotype", action="store_true",
                     help="skip the full-size genotype (int8, 5000 x 500,000) path object")
+    ap.add_argument("--no-out-of-core", action="store_true",
+                    help="skip the path with X in host memory (read over NVLink-C2C)")
     ap.add_argument("--no-rules", action="store_true", help="skip the screening-rule comparison (SSR, SEDPP, BEDPP)")
     ap.add_argument("--plain-steps", type=int, default=2,
                     help="steps of the plain form (residual-update CD) timed for comparison; 0 = skip")
@@ -623,6 +625,35 @@ def genotype_path(local: int, steps: int = 2, oracle_lambdas: int = 8):
             "status": res["status"]}
 
 
+def out_of_core(ctx, X, y, prob, kw, res_device, steps: int = 2):
+    """The headline path with X in page-locked host memory (Grace LPDDR), read by
+    the same kernels over NVLink-C2C through its unified address: the path time,
+    the z pass's achieved GB/s from host memory, and the coefficient difference
+    from the device-resident path (0: the same kernels and arithmetic)."""
+    import torch
+    from paper_1701_05936_gb300 import bl
+    Xh = X.cpu().pin_memory()
+    r = bl.bl_fit_path(ctx, Xh, prob.n, y, **kw)
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(steps):
+        r = bl.bl_fit_path(ctx, Xh, prob.n, y, **kw)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    t = ctx.timing()
+    ctx.set_timing(False)
+    zp = t["zpass"]
+    diff = float((bl.path_dense(r, prob.p) - bl.path_dense(res_device, prob.p)).abs().max())
+    return {"form": "X in page-locked host memory, read over NVLink-C2C by the same kernels",
+            "value": 1e3 / ms, "unit": "paths/s", "ms_per_path": ms, "steps": steps,
+            "zpass_ms_per_path": zp["ms"] / steps,
+            "zpass_gbs_from_host": zp["bytes"] / (zp["ms"] / 1e3) / 1e9 if zp["ms"] > 0 else None,
+            "max_abs_coef_diff_vs_device_resident": diff, "status": r["status"]}
+
+
 def config(prob):
     return {"workload": WORKLOAD_NAME if prob.p == 100_000 else f"ar1_{prob.n}x{prob.p}_f32_small",
             "n": prob.n, "p": prob.p, "ldx": prob.ldx, "nlambda": prob.nlambda, "lambda_min_ratio": prob.ratio,
@@ -775,6 +806,8 @@ def run_ours(args):
         line["precision_form"] = precision_form(ctx, X, y, prob, kw, res, tim["zpass"]["ms"] / args.steps)
     if solo and not args.no_rules:
         line["screen_rules"] = screen_rules(ctx, X, y, prob, kw, res)
+    if solo and not args.no_out_of_core:
+        line["out_of_core"] = out_of_core(ctx, X, y, prob, kw, res)
     if solo and not args.no_batched:
         line["batched_zpass"], line["batched_path"] = batched(local)
     if solo and not args.no_learned:

@@ -29,7 +29,12 @@
  *   j starts at element j*ldx.  dtype is a bl_dtype.  Requirements (else
  *   BL_ERR_ARG before any launch): n >= 1, p >= 1, ldx >= n,
  *   ldx*sizeof(elem) a multiple of 16 bytes, X 16-byte aligned.  The rows
- *   n..ldx-1 of each column are never read for arithmetic.
+ *   n..ldx-1 of each column are never read for arithmetic.  For bl_fit_path
+ *   with FP32 data, n <= 1024 and BL_CD_BLOCKED, and for bl_standardize,
+ *   bl_lambda_max, bl_bedpp_init and bl_kkt_check, X may instead be
+ *   page-locked host memory (cudaHostAlloc; read through its unified address,
+ *   over NVLink-C2C on Grace systems); pageable host memory is not addressable
+ *   by the kernels and must not be passed.
  *   Indices are 64-bit, so n*ldx may exceed 2^31.
  * - Per-feature vectors are length p, per-observation vectors length n.
  */
@@ -522,7 +527,8 @@ typedef struct {
  * problem; problems may differ in n, p and dtype).  `concurrency` host workers
  * (0: min(nprob, 16), at most 64), each with its own context and non-blocking
  * CUDA stream on ctx's device and a workspace sized for the largest problem,
- * take problems from a shared queue, so the paths' kernels overlap on the GPU
+ * take problems from a shared queue (largest n * p first), so the paths'
+ * kernels overlap on the GPU
  * (each coordinate descent runs on one SM; z passes interleave).  opt applies to
  * every problem.  Returns BL_OK when every problem returned BL_OK, else the first
  * problem's error in queue order (every problem's own status is in its

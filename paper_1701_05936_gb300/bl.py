@@ -211,6 +211,10 @@ def design_args(X: torch.Tensor, n: int):
         raise BLError(BL_ERR_ARG, "X must be a 2-D (p, ldx) float64/float32/int8 tensor")
     if X.stride(1) != 1:
         raise BLError(BL_ERR_ARG, "X rows (design columns) must be contiguous")
+    if not X.is_cuda and not X.is_pinned():
+        # the kernels reach host memory only through a page-locked allocation's
+        # unified address; pageable memory is not addressable from the GPU
+        raise BLError(BL_ERR_ARG, "a host design must be in page-locked memory (Tensor.pin_memory())")
     return [C.c_void_p(X.data_ptr()), _DTYPE[X.dtype], int(n), int(X.shape[0]), int(X.stride(0))]
 
 
@@ -328,7 +332,7 @@ def bl_fit_path(ctx, X, n, y, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, lambd
     proposer: device FP32 parameters for screen=BL_SCREEN_LEARNED; capture > 0
     returns up to that many proposer candidates (prop_feat, prop_idx,
     prop_label, prop_count)."""
-    dev = X.device
+    dev = X.device if X.is_cuda else torch.device("cuda", ctx.device)  # outputs on the ctx's GPU
     p = int(X.shape[0])
     K = int(nlambda if lambdas is None else len(lambdas))
     if nnz_capacity is None:
@@ -360,8 +364,8 @@ def bl_fit_path(ctx, X, n, y, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, lambd
         path.prop_label = res["prop_label"].data_ptr()
         path.prop_cap = int(capture)
     if warm_beta is not None and (warm_beta.dtype != torch.float64 or warm_beta.numel() != X.shape[0]
-                                  or not warm_beta.is_contiguous() or warm_beta.device != X.device):
-        raise BLError(BL_ERR_ARG, "warm_beta must be a contiguous float64 (p,) tensor on X's device")
+                                  or not warm_beta.is_contiguous() or warm_beta.device != dev):
+        raise BLError(BL_ERR_ARG, "warm_beta must be a contiguous float64 (p,) tensor on the ctx's GPU")
     opt = bl_options(float(alpha), float(eps), float(ratio), int(max_sweeps), int(screen), int(cd_mode),
                      None if proposer is None else proposer.data_ptr(), float(proposer_tau), int(xprec), 0,
                      int(timeout_ns), None if warm_beta is None else warm_beta.data_ptr(), float(warm_lambda))

@@ -1018,14 +1018,21 @@ extern "C" int bl_fit_many(bl_ctx *ctx, bl_problem *probs, int nprob, const bl_o
             return fail(ctx, st, "could not create the worker contexts");
         }
     }
+    // the queue runs the largest problems (n * p) first, so that no large path is
+    // left to run alone at the end
+    std::vector<int> order((size_t)nprob);
+    for (int i = 0; i < nprob; ++i) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return (double)probs[x].n * (double)probs[x].p > (double)probs[y].n * (double)probs[y].p;
+    });
     std::atomic<int> next{0};
     auto work = [&](int t) {
         cudaSetDevice(ctx->device);
         bl_ctx *c = wk[(size_t)t];
         for (;;) {
-            const int i = next.fetch_add(1);
-            if (i >= nprob) break;
-            bl_problem &q = probs[i];
+            const int k = next.fetch_add(1);
+            if (k >= nprob) break;
+            bl_problem &q = probs[order[(size_t)k]];
             q.status = bl_fit_path(c, q.X, q.dtype, q.n, q.p, q.ldx, q.y, opt, q.lambdas, q.nlambda, q.out);
         }
     };
