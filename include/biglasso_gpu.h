@@ -190,8 +190,9 @@ typedef struct {
  * 2 bedpp_init, 3 screen, 4 compact, 5 cd, 6 residual, 7 zpass, 8 record,
  * 9 gref (the FP64 reference gradients each CD launch starts from),
  * 10 xtr (the batched z pass of bl_xtr_batched), 11 kkt (the batched path's
- * KKT check). */
-#define BL_NUM_KINDS 12
+ * KKT check), 12 gram (the working set's correlation matrix that the blocked
+ * and covariance CD forms read). */
+#define BL_NUM_KINDS 13
 typedef struct {
     int64_t launches[BL_NUM_KINDS];
     double ms[BL_NUM_KINDS];         /* summed device time */

@@ -30,7 +30,7 @@ BL_MLP_NPARAM = 4609
 BL_CD_RESIDUAL, BL_CD_COVARIANCE, BL_CD_BLOCKED = 0, 1, 2
 BL_XPREC_NATIVE, BL_XPREC_BF16 = 0, 1
 KINDS = ["standardize", "lambda_max", "bedpp_init", "screen", "compact", "cd", "residual", "zpass", "record",
-         "gref", "xtr", "kkt"]
+         "gref", "xtr", "kkt", "gram"]
 
 _STATUS = {0: "BL_OK", -1: "BL_ERR_ARG", -2: "BL_ERR_CUDA", -3: "BL_ERR_OOM", -4: "BL_ERR_NOT_CONVERGED",
            -5: "BL_ERR_TIMEOUT", -6: "BL_ERR_UNSUPPORTED", -7: "BL_ERR_CAPACITY"}

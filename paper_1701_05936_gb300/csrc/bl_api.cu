@@ -38,6 +38,7 @@ struct Workspace {
     void *beta;
     uint8_t *keep, *safe, *working, *scan;
     int32_t *idx;
+    int32_t *gpos, *gidx, *gop, *gnew;  // the stored working set of the correlation matrix (bl_gram.cu)
     double *yc, *xcs, *partial, *part_val, *r64;
     long long *part_idx;
     void *r, *gref;
@@ -57,8 +58,10 @@ struct bl_ctx {
     std::vector<TimedLaunch> launches;
     std::vector<cudaEvent_t> pool;
     bl_timing totals{};
-    void *gram = nullptr;      // correlation matrix of the working set (covariance-form CD)
-    size_t gram_bytes = 0;
+    void *gram = nullptr;      // correlation matrix of the working set (blocked and covariance CD)
+    void *gram2 = nullptr;     // the next one, assembled from gram (the two swap after each build)
+    size_t gram_bytes = 0;     // of each
+    int64_t gram_w = 0;        // features in gram (0: none stored)
     void *xtr = nullptr;       // batched z pass: per-fit epilogue vectors, sum r, row counts
     size_t xtr_bytes = 0;
     void *hist = nullptr;      // learned proposer: z at the three previous lambdas
@@ -123,8 +126,9 @@ int ensure_ws(bl_ctx *ctx, int64_t n, int64_t p)
     const size_t n8 = align256((size_t)N * 8);
     const size_t idxb = align256((size_t)MAX_WORKING * 4);
     const size_t grefb = align256((size_t)MAX_WORKING * 8);
+    const size_t gsetb = align256(((size_t)MAX_WORKING + 1) * 4);
     const size_t total = 6 * p8 + 4 * p4 + p8 + 4 * p1 + idxb + grefb + 4 * n8 + (size_t)RESID_GROUPS * n8 +
-                         2 * align256(1024 * 8) + align256(sizeof(DevScalars));
+                         2 * align256(1024 * 8) + align256(sizeof(DevScalars)) + p4 + 3 * gsetb;
     if (w.base) {
         cudaStreamSynchronize(ctx->stream);
         cudaFree(w.base);
@@ -168,10 +172,32 @@ int ensure_ws(bl_ctx *ctx, int64_t n, int64_t p)
     w.part_val = (double *)take(align256(1024 * 8));
     w.part_idx = (long long *)take(align256(1024 * 8));
     w.sc = (DevScalars *)take(align256(sizeof(DevScalars)));
+    w.gpos = (int32_t *)take(p4);
+    w.gidx = (int32_t *)take(gsetb);
+    w.gop = (int32_t *)take(gsetb);
+    w.gnew = (int32_t *)take(gsetb);
+    ctx->gram_w = 0;
     w.base = base;
     w.size = total;
     w.n = N;
     w.p = P;
+    return BL_OK;
+}
+
+// The two correlation-matrix buffers, `need` bytes each; a new pair holds no
+// stored working set.
+int ensure_gram(bl_ctx *ctx, size_t need)
+{
+    if (ctx->gram_bytes >= need) return BL_OK;
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->gram) cudaFree(ctx->gram);
+    if (ctx->gram2) cudaFree(ctx->gram2);
+    ctx->gram = ctx->gram2 = nullptr;
+    ctx->gram_bytes = 0;
+    ctx->gram_w = 0;
+    CK(cudaMalloc(&ctx->gram, need));
+    CK(cudaMalloc(&ctx->gram2, need));
+    ctx->gram_bytes = need;
     return BL_OK;
 }
 
@@ -247,6 +273,20 @@ void fold_timing(bl_ctx *ctx)
     ctx->launches.clear();
 }
 
+// The working set's correlation matrix into ctx->gram: assembled from the
+// stored one (the last build of this path) and the entering features' rows.
+int build_gram(bl_ctx *ctx, int dtype, const void *X, int64_t n, int64_t ldx, const void *cvec, const void *isvec,
+               const Workspace &w, int64_t wh)
+{
+    const int slot = tbegin(ctx, 12);
+    LAUNCH(3, launch_gram_inc(dtype, X, n, ldx, cvec, isvec, w.idx, wh, ctx->gram, ctx->gram_w, w.gpos, w.gidx,
+                              w.gop, w.gnew, ctx->gram2, ctx->num_sms, ctx->stream));
+    tend(ctx, slot, 0.0);
+    std::swap(ctx->gram, ctx->gram2);
+    ctx->gram_w = wh;
+    return BL_OK;
+}
+
 int sync_sc(bl_ctx *ctx)
 {
     CK(cudaMemcpyAsync(ctx->sc_host, ctx->ws.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, ctx->stream));
@@ -310,6 +350,7 @@ extern "C" int bl_ctx_destroy(bl_ctx *ctx)
     for (auto e : ctx->pool) cudaEventDestroy(e);
     if (ctx->ws.base) cudaFree(ctx->ws.base);
     if (ctx->gram) cudaFree(ctx->gram);
+    if (ctx->gram2) cudaFree(ctx->gram2);
     if (ctx->xtr) cudaFree(ctx->xtr);
     if (ctx->hist) cudaFree(ctx->hist);
     if (ctx->packed) cudaFree(ctx->packed);
@@ -335,14 +376,7 @@ extern "C" int bl_reserve(bl_ctx *ctx, int dtype, int64_t n, int64_t p, const bl
     if ((opt->cd_mode == BL_CD_BLOCKED && cd_blk_ok(dtype, n)) || opt->cd_mode == BL_CD_COVARIANCE) {
         const int64_t cap = f64 ? MAX_WORKING_F64 : MAX_WORKING;
         const size_t need = (size_t)cap * (size_t)cap * (f64 ? 8 : 4);
-        if (ctx->gram_bytes < need) {
-            CK(cudaStreamSynchronize(ctx->stream));
-            if (ctx->gram) cudaFree(ctx->gram);
-            ctx->gram = nullptr;
-            ctx->gram_bytes = 0;
-            CK(cudaMalloc(&ctx->gram, need));
-            ctx->gram_bytes = need;
-        }
+        if ((st = ensure_gram(ctx, need))) return st;
     }
     if (opt->cd_mode == BL_CD_BLOCKED && dtype == BL_F32 && n <= 1024 && !ctx->packed) {
         CK(cudaMalloc(&ctx->packed, 2 * (size_t)MAX_WORKING * 4096));
@@ -368,7 +402,7 @@ extern "C" int bl_reserve(bl_ctx *ctx, int dtype, int64_t n, int64_t p, const bl
 extern "C" int bl_ctx_workspace_bytes(const bl_ctx *ctx, int64_t *bytes)
 {
     if (!ctx || !bytes) return BL_ERR_ARG;
-    *bytes = (int64_t)(ctx->ws.size + ctx->gram_bytes + ctx->packed_bytes + ctx->xtr_bytes + ctx->hist_bytes +
+    *bytes = (int64_t)(ctx->ws.size + 2 * ctx->gram_bytes + ctx->packed_bytes + ctx->xtr_bytes + ctx->hist_bytes +
                        ctx->xbf_bytes + ctx->rlist_bytes);
     return BL_OK;
 }
@@ -1003,11 +1037,7 @@ extern "C" int bl_fit_many(bl_ctx *ctx, bl_problem *probs, int nprob, const bl_o
         cudaError_t e = cudaStreamCreateWithFlags(&ws[(size_t)t], cudaStreamNonBlocking);
         int st = (e == cudaSuccess) ? bl_ctx_create(&wk[(size_t)t], ctx->device, ws[(size_t)t]) : BL_ERR_CUDA;
         if (st == BL_OK) st = ensure_ws(wk[(size_t)t], nmax, pmax);
-        if (st == BL_OK && gneed) {
-            e = cudaMalloc(&wk[(size_t)t]->gram, gneed);
-            if (e == cudaSuccess) wk[(size_t)t]->gram_bytes = gneed;
-            else st = (e == cudaErrorMemoryAllocation) ? BL_ERR_OOM : BL_ERR_CUDA;
-        }
+        if (st == BL_OK && gneed) st = ensure_gram(wk[(size_t)t], gneed);
         if (st == BL_OK && opt->cd_mode == BL_CD_BLOCKED && any_f32) {  // the SM-cluster form's packed columns
             e = cudaMalloc(&wk[(size_t)t]->packed, 2 * (size_t)MAX_WORKING * 4096);
             if (e == cudaSuccess) wk[(size_t)t]->packed_bytes = 2 * (size_t)MAX_WORKING * 4096;
@@ -1434,14 +1464,8 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
     if (gram_mode || blk_mode) {
         const int64_t cap = max_w_for(dtype);
         const size_t need = (size_t)cap * (size_t)cap * (beta_f64 ? 8 : 4);
-        if (ctx->gram_bytes < need) {
-            CK(cudaStreamSynchronize(s));
-            if (ctx->gram) cudaFree(ctx->gram);
-            ctx->gram = nullptr;
-            ctx->gram_bytes = 0;
-            CK(cudaMalloc(&ctx->gram, need));
-            ctx->gram_bytes = need;
-        }
+        if ((st = ensure_gram(ctx, need))) return st;
+        ctx->gram_w = 0;  // a new standardization: nothing stored carries over
     }
     const void *cvec = beta_f64 ? (const void *)w.center : (const void *)w.c32;
     const void *isvec = beta_f64 ? (const void *)w.inv_scale : (const void *)w.is32;
@@ -1615,7 +1639,7 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
                 CK(cudaStreamSynchronize(s));
                 if (wh > wcap) return fail(ctx, BL_ERR_UNSUPPORTED, "working set exceeds the CD kernel's limit");
                 if (gram_mode) {
-                    LAUNCH(1, launch_gram(dtype, X, n, ldx, cvec, isvec, w.idx, wh, w.sc, ctx->gram, ctx->num_sms, s));
+                    if ((st = build_gram(ctx, dtype, X, n, ldx, cvec, isvec, w, wh))) return st;
                     LAUNCH(1, launch_cd_gram(dtype, ctx->gram, n, p, isvec, w.idx, wh, w.gref, lam, alpha, w.beta, eps,
                                              opt->max_sweeps, tlim, w.sc, s));
                 } else if (cd_clu_ok(dtype, n, wh)) {  // chain on one SM, row halves on two more (bl_clu.cu)
@@ -1623,13 +1647,13 @@ extern "C" int bl_fit_path(bl_ctx *ctx, const void *X, int dtype, int64_t n, int
                         CK(cudaMalloc(&ctx->packed, 2 * (size_t)MAX_WORKING * 4096));
                         ctx->packed_bytes = 2 * (size_t)MAX_WORKING * 4096;
                     }
-                    LAUNCH(1, launch_gram(dtype, X, n, ldx, cvec, isvec, w.idx, wh, w.sc, ctx->gram, ctx->num_sms, s));
+                    if ((st = build_gram(ctx, dtype, X, n, ldx, cvec, isvec, w, wh))) return st;
                     LAUNCH(2, launch_cd_clu((const float *)X, n, p, ldx, (const float *)cvec, (const float *)isvec,
                                             w.idx, wh, (const float *)w.gref, (const float *)ctx->gram, lam, alpha,
                                             (float *)w.beta, eps, opt->max_sweeps, tlim, w.sc,
                                             ctx->packed, (int64_t)(ctx->packed_bytes / 4), ctx->num_sms, s));
                 } else if (cd_blk_fits(dtype, n, wh)) {
-                    LAUNCH(1, launch_gram(dtype, X, n, ldx, cvec, isvec, w.idx, wh, w.sc, ctx->gram, ctx->num_sms, s));
+                    if ((st = build_gram(ctx, dtype, X, n, ldx, cvec, isvec, w, wh))) return st;
                     LAUNCH(1, launch_cd_blk(dtype, X, n, p, ldx, cvec, isvec, w.idx, wh, w.gref, ctx->gram, lam, alpha,
                                             w.beta, nullptr, eps, opt->max_sweeps, tlim, w.sc, s));
                 } else {  // working set too large for the block stages: coordinate-at-a-time form

@@ -17,117 +17,221 @@
 
 namespace bl {
 
-// ------------------------------------------------------------ R = Xt_W'Xt_W/n
-// Persistent tiled kernel: 64 x 64 tiles of R, 256 threads, 4 x 4 outputs per
-// thread, 32-row slabs of the two column blocks staged in shared memory and
-// centred on the fly (x_ij - c_j); the epilogue scales by 1/(n s_a s_b).
-// Tiles cover ld x ld with ld = gram_ld(w); entries outside w are written 0.
+// ------------------------------------------ R carried from one CD call to the next
+// Along the path the working set changes by a few features per lambda, so the
+// new working set's R is assembled from the stored one: the entries between
+// features of both sets are copied and only the rows and columns of the
+// entering features are computed.  gpos[j] is the position of feature j in the
+// stored matrix whenever gpos[j] < w_old and gidx[gpos[j]] == j; an entry that
+// fails the test is stale, so gpos is never cleared.
+
+// One CTA: op[t] = stored position of feature idx[t], or -1 when it enters;
+// gnew[0 .. m) = the entering positions, ascending, and gnew[MAX_WORKING] = m.
+__global__ void __launch_bounds__(1024)
+    k_gram_map(const int32_t *__restrict__ idx, int64_t w, const int32_t *__restrict__ gpos,
+               const int32_t *__restrict__ gidx, int64_t w_old, int32_t *__restrict__ op, int32_t *__restrict__ gnew)
+{
+    __shared__ int32_t wsum[32];
+    __shared__ int32_t base;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int64_t t0 = 0; t0 < w; t0 += blockDim.x) {
+        const int64_t t = t0 + threadIdx.x;
+        int32_t q = -1;
+        if (t < w) {
+            const int32_t j = idx[t];
+            const int32_t c = gpos[j];
+            if (c >= 0 && c < w_old && gidx[c] == j) q = c;
+            op[t] = q;
+        }
+        const bool enters = t < w && q < 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, enters);
+        if (lane == 0) wsum[wid] = __popc(bal);
+        __syncthreads();
+        if (wid == 0) {
+            int v = (lane < nw) ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            wsum[lane] = v;  // inclusive
+        }
+        __syncthreads();
+        if (enters) gnew[base + (wid ? wsum[wid - 1] : 0) + __popc(bal & ((1u << lane) - 1u))] = (int32_t)t;
+        __syncthreads();
+        if (threadIdx.x == 0) base += wsum[nw - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) gnew[MAX_WORKING] = base;
+}
+
+// R's rows a < ld: entries between two stored features copied from Rold,
+// padding (a or b >= w) set to 0, the rest left to k_gram_rows.  Also records
+// the new working set as the stored one (gpos, gidx); k_gram_map has read them.
+template <typename A>
+__global__ void __launch_bounds__(256)
+    k_gram_gather(const A *__restrict__ Rold, int64_t ld_old, const int32_t *__restrict__ op,
+                  const int32_t *__restrict__ idx, int64_t w, A *__restrict__ Rm, int32_t *__restrict__ gpos,
+                  int32_t *__restrict__ gidx)
+{
+    const int64_t ld = gram_ld(w);
+    for (int64_t a = blockIdx.x; a < ld; a += gridDim.x) {
+        const int32_t oa = (a < w) ? op[a] : -1;
+        A *row = Rm + a * ld;
+        if (a >= w) {
+            for (int64_t b = threadIdx.x; b < ld; b += blockDim.x) row[b] = (A)0;
+            continue;
+        }
+        for (int64_t b = threadIdx.x; b < ld; b += blockDim.x) {
+            if (b >= w) {
+                row[b] = (A)0;
+            } else if (oa >= 0) {
+                const int32_t ob = op[b];
+                if (ob >= 0) row[b] = Rold[(int64_t)oa * ld_old + ob];
+            }
+        }
+        if (threadIdx.x == 0) {
+            const int32_t j = idx[a];
+            gpos[j] = (int32_t)a;
+            gidx[a] = j;
+        }
+    }
+}
+
+// Sum of v[e] over the warp's lanes for NV entries, as a butterfly that halves
+// the entries each lane carries at every step (NV - 2 NV/32 shuffles instead of
+// 5 NV); lane l ends with the sums of entries (NV/32) l .. (NV/32) l + NV/32 - 1
+// in v[0 .. NV/32).  Every entry is summed in the same tree.
+template <int NV, typename A> __device__ __forceinline__ void warp_sum_scatter(A (&v)[NV], int lane)
+{
+#pragma unroll
+    for (int s = 16, len = NV / 2; s >= 1; s >>= 1, len >>= 1) {
+        const bool up = (lane & s) != 0;
+#pragma unroll
+        for (int k = 0; k < len; ++k) {
+            const A send = up ? v[k] : v[k + len];
+            const A keep = up ? v[k + len] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+}
+
+// The rows and columns of R for the entering positions gnew[0 .. m): one work
+// item is FG entering features x CG consecutive positions b, over all n rows.
+// Thread (warp q, lane l) takes rows 32 (q + 8 i) + l, accumulating FG x CG
+// products of the centred values; the lanes' sums are combined by
+// warp_sum_scatter and the 8 warps' in order.  R(a, b) is written as
+// acc s_a s_b / n for both (a, b) and (b, a), so a pair of entering features,
+// met in two items, gets the same value from both.
 template <typename T>
 __global__ void __launch_bounds__(256)
-    k_gram(const T *__restrict__ X, int64_t n, int64_t ldx, const typename elem<T>::acc *__restrict__ cvec,
-           const typename elem<T>::acc *__restrict__ isvec, const int32_t *__restrict__ idx, int64_t w_host,
-           int64_t cap, const DevScalars *__restrict__ scw, typename elem<T>::acc *__restrict__ Rm)
+    k_gram_rows(const T *__restrict__ X, int64_t n, int64_t ldx, const typename elem<T>::acc *__restrict__ cvec,
+                const typename elem<T>::acc *__restrict__ isvec, const int32_t *__restrict__ idx, int64_t w,
+                const int32_t *__restrict__ gnew, typename elem<T>::acc *__restrict__ Rm)
 {
     using A = typename elem<T>::acc;
-    constexpr int TB = 64, KB = 32;
-    __shared__ A As[KB][TB + 1];
-    __shared__ A Bs[KB][TB + 1];
-    __shared__ int32_t ia[TB], ib[TB];
-    __shared__ A ca[TB], cb[TB], sa[TB], sb[TB];
-    int64_t w = (w_host >= 0) ? w_host : (int64_t)scw->w;
-    if (w > cap) w = cap;
+    constexpr int CG = 4, FG = (sizeof(A) == 8) ? 8 : 16, NV = FG * CG, PER = NV / 32, NWARP = 8;
+    __shared__ A red[NWARP][NV];
+    __shared__ int32_t ja[FG], pa[FG], jb[CG];
+    __shared__ A ca[FG], sa[FG], cb[CG], sb[CG];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t m = gnew[MAX_WORKING];
     const int64_t ld = gram_ld(w);
-    const int64_t T_ = (ld + TB - 1) / TB;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t ncg = (w + CG - 1) / CG, items = ncg * ((m + FG - 1) / FG);
     const A inv_n = (A)(1.0 / (double)n);
-    for (int64_t tile = blockIdx.x; tile < T_ * T_; tile += gridDim.x) {
-        const int64_t a0 = (tile / T_) * TB, b0 = (tile % T_) * TB;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int64_t f0 = (it / ncg) * FG, b0 = (it % ncg) * CG;
         __syncthreads();
-        if (threadIdx.x < TB) {
-            const int64_t a = a0 + threadIdx.x;
-            const int32_t j = (a < w) ? idx[a] : -1;
-            ia[threadIdx.x] = j;
+        if (threadIdx.x < FG) {
+            const int64_t u = f0 + threadIdx.x;
+            const int32_t pos = (u < m) ? gnew[u] : -1;
+            const int32_t j = (pos >= 0) ? idx[pos] : -1;
+            pa[threadIdx.x] = pos;
+            ja[threadIdx.x] = j;
             ca[threadIdx.x] = (j >= 0) ? cvec[j] : (A)0;
             sa[threadIdx.x] = (j >= 0) ? isvec[j] : (A)0;
-        } else if (threadIdx.x < 2 * TB) {
-            const int t = threadIdx.x - TB;
-            const int64_t b = b0 + t;
-            const int32_t j = (b < w) ? idx[b] : -1;
-            ib[t] = j;
-            cb[t] = (j >= 0) ? cvec[j] : (A)0;
-            sb[t] = (j >= 0) ? isvec[j] : (A)0;
+        } else if (threadIdx.x >= 32 && threadIdx.x < 32 + CG) {
+            const int v = threadIdx.x - 32;
+            const int32_t j = (b0 + v < w) ? idx[b0 + v] : -1;
+            jb[v] = j;
+            cb[v] = (j >= 0) ? cvec[j] : (A)0;
+            sb[v] = (j >= 0) ? isvec[j] : (A)0;
         }
         __syncthreads();
-        A acc[4][4];
+        int32_t jav[FG], jbv[CG];
+        A cav[FG], cbv[CG];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int f = 0; f < FG; ++f) jav[f] = ja[f], cav[f] = ca[f];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = (A)0;
-        for (int64_t i0 = 0; i0 < n; i0 += KB) {
-            // each thread stages 8 entries of each slab: column c = e / KB, row k = e % KB
+        for (int v = 0; v < CG; ++v) jbv[v] = jb[v], cbv[v] = cb[v];
+        A acc[NV];
 #pragma unroll
-            for (int m = 0; m < (KB * TB) / 256; ++m) {
-                const int e = threadIdx.x + 256 * m;
-                const int c = e / KB, k = e % KB;
-                const int64_t i = i0 + k;
-                const int32_t ja = ia[c], jb = ib[c];
-                As[k][c] = (ja >= 0 && i < n) ? (A)X[(int64_t)ja * ldx + i] - ca[c] : (A)0;
-                Bs[k][c] = (jb >= 0 && i < n) ? (A)X[(int64_t)jb * ldx + i] - cb[c] : (A)0;
+        for (int e = 0; e < NV; ++e) acc[e] = (A)0;
+        for (int64_t i = (int64_t)wid * 32 + lane; i < n; i += NWARP * 32) {
+            A xb[CG];
+#pragma unroll
+            for (int v = 0; v < CG; ++v) xb[v] = (jbv[v] >= 0) ? (A)X[(int64_t)jbv[v] * ldx + i] - cbv[v] : (A)0;
+#pragma unroll
+            for (int f = 0; f < FG; ++f) {
+                if (jav[f] < 0) continue;  // uniform across the CTA
+                const A xa = (A)X[(int64_t)jav[f] * ldx + i] - cav[f];
+#pragma unroll
+                for (int v = 0; v < CG; ++v) acc[f * CG + v] = fma(xa, xb[v], acc[f * CG + v]);
             }
-            __syncthreads();
-#pragma unroll 8
-            for (int k = 0; k < KB; ++k) {
-                A av[4], bv[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) av[u] = As[k][ty * 4 + u];
-#pragma unroll
-                for (int v = 0; v < 4; ++v) bv[v] = Bs[k][tx * 4 + v];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
-            }
-            __syncthreads();
         }
+        warp_sum_scatter<NV>(acc, lane);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t a = a0 + ty * 4 + u;
-            if (a >= ld) continue;
+        for (int k = 0; k < PER; ++k) red[wid][PER * lane + k] = acc[k];
+        __syncthreads();
+        if (threadIdx.x < NV) {
+            const int e = threadIdx.x, f = e / CG, v = e % CG;
+            A sum = red[0][e];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const int64_t b = b0 + tx * 4 + v;
-                if (b >= ld) continue;
-                const bool in = a < w && b < w;
-                Rm[a * ld + b] = in ? acc[u][v] * sa[ty * 4 + u] * sb[tx * 4 + v] * inv_n : (A)0;
+            for (int q = 1; q < NWARP; ++q) sum += red[q][e];
+            const int32_t a = pa[f];
+            const int64_t b = b0 + v;
+            if (a >= 0 && b < w) {
+                Rm[(int64_t)a * ld + b] = sum * sa[f] * sb[v] * inv_n;
+                Rm[b * ld + a] = sum * sb[v] * sa[f] * inv_n;
             }
         }
     }
 }
 
 template <typename T>
-static cudaError_t gram_t(const T *X, int64_t n, int64_t ldx, const void *cvec, const void *isvec, const int32_t *idx,
-                          int64_t w_host, int64_t cap, const DevScalars *scw, void *Rm, int num_sms, cudaStream_t st)
+static cudaError_t gram_inc_t(const T *X, int64_t n, int64_t ldx, const void *cvec, const void *isvec,
+                              const int32_t *idx, int64_t w, const void *Rold, int64_t w_old, int32_t *gpos,
+                              int32_t *gidx, int32_t *gop, int32_t *gnew, void *Rm, int num_sms, cudaStream_t st)
 {
     using A = typename elem<T>::acc;
-    int64_t blocks = (int64_t)num_sms * 2;
-    if (w_host >= 0) {
-        const int64_t tiles = (gram_ld(w_host) + 63) / 64;
-        if (tiles * tiles < blocks) blocks = tiles * tiles;
-        if (blocks < 1) return cudaSuccess;
-    }
-    k_gram<T><<<(int)blocks, 256, 0, st>>>(X, n, ldx, (const A *)cvec, (const A *)isvec, idx, w_host, cap, scw,
-                                           (A *)Rm);
+    if (w < 1) return cudaSuccess;
+    k_gram_map<<<1, 1024, 0, st>>>(idx, w, gpos, gidx, w_old, gop, gnew);
+    const int64_t ld = gram_ld(w);
+    k_gram_gather<A><<<(int)std::min<int64_t>(ld, (int64_t)num_sms * 4), 256, 0, st>>>(
+        (const A *)Rold, gram_ld(w_old), gop, idx, w, (A *)Rm, gpos, gidx);
+    constexpr int CG = 4, FG = (sizeof(A) == 8) ? 8 : 16;
+    const int64_t most = ((w + CG - 1) / CG) * ((w + FG - 1) / FG);  // every position entering
+    k_gram_rows<T><<<(int)std::min<int64_t>(most, (int64_t)num_sms * 2), 256, 0, st>>>(
+        X, n, ldx, (const A *)cvec, (const A *)isvec, idx, w, gnew, (A *)Rm);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gram(int dtype, const void *X, int64_t n, int64_t ldx, const void *cvec, const void *isvec,
-                        const int32_t *idx, int64_t w_host, const DevScalars *scw, void *Rm, int num_sms,
-                        cudaStream_t st)
+cudaError_t launch_gram_inc(int dtype, const void *X, int64_t n, int64_t ldx, const void *cvec, const void *isvec,
+                            const int32_t *idx, int64_t w, const void *Rold, int64_t w_old, int32_t *gpos,
+                            int32_t *gidx, int32_t *gop, int32_t *gnew, void *Rm, int num_sms, cudaStream_t st)
 {
     switch (dtype) {
-    case 0: return gram_t((const double *)X, n, ldx, cvec, isvec, idx, w_host, MAX_WORKING_F64, scw, Rm, num_sms, st);
-    case 1: return gram_t((const float *)X, n, ldx, cvec, isvec, idx, w_host, MAX_WORKING, scw, Rm, num_sms, st);
-    case 3: return gram_t((const int8_t *)X, n, ldx, cvec, isvec, idx, w_host, MAX_WORKING, scw, Rm, num_sms, st);
+    case 0:
+        return gram_inc_t((const double *)X, n, ldx, cvec, isvec, idx, w, Rold, w_old, gpos, gidx, gop, gnew, Rm,
+                          num_sms, st);
+    case 1:
+        return gram_inc_t((const float *)X, n, ldx, cvec, isvec, idx, w, Rold, w_old, gpos, gidx, gop, gnew, Rm,
+                          num_sms, st);
+    case 3:
+        return gram_inc_t((const int8_t *)X, n, ldx, cvec, isvec, idx, w, Rold, w_old, gpos, gidx, gop, gnew, Rm,
+                          num_sms, st);
     default: return cudaErrorInvalidValue;
     }
 }

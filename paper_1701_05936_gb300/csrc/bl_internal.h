@@ -145,10 +145,14 @@ cudaError_t launch_cd_widx(int dtype, const void *X, int64_t n, int64_t p, int64
                            uint64_t time_limit_ns, DevScalars *sc, cudaStream_t st);
 
 // R = Xt_W'Xt_W/n for the working set (W-ordered, leading dimension
-// round_up(w, 4), arithmetic type of the design).
-cudaError_t launch_gram(int dtype, const void *X, int64_t n, int64_t ldx, const void *cvec, const void *isvec,
-                        const int32_t *idx, int64_t w_host, const DevScalars *scw, void *Rm, int num_sms,
-                        cudaStream_t st);
+// round_up(w, 4), arithmetic type of the design, padding 0).
+// R of the working set idx[0 .. w) into Rm, from Rold (the stored working set's R,
+// w_old features, recorded in gpos/gidx) and the rows of the entering features;
+// then records idx as the stored set.  w_old = 0: every feature enters.  gop
+// and gnew: MAX_WORKING and MAX_WORKING + 1 ints of scratch.  Three kernels.
+cudaError_t launch_gram_inc(int dtype, const void *X, int64_t n, int64_t ldx, const void *cvec, const void *isvec,
+                            const int32_t *idx, int64_t w, const void *Rold, int64_t w_old, int32_t *gpos,
+                            int32_t *gidx, int32_t *gop, int32_t *gnew, void *Rm, int num_sms, cudaStream_t st);
 
 // Covariance-form CD over the w (host-known) working-set entries from R and
 // the reference gradients.
