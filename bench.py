@@ -454,13 +454,17 @@ def learned(local: int):
 
 
 def many(local: int, nprob: int = 256, concurrency: int = 16):
-    """Independent problems at once (bl_fit_many) at the many-problems workload's
-    sizes: nprob lasso paths with n ~ U{100..2000}, p ~ U{1000..50,000}, iid
-    N(0,1) FP32, 10 nonzero +-1, SNR 3, 100 lambdas to 0.05 lambda_max, alpha 1
-    (about 27 GB of designs, all resident in HBM).  Timed with CUDA events on
-    the ctx stream around the call (the call synchronizes its worker streams
-    before it returns).  Beside the plain form: the same problems one after
-    another through bl_fit_path, timed on a sample and scaled."""
+    """Independent problems at the many-problems workload's sizes: nprob lasso
+    paths with n ~ U{100..2000}, p ~ U{1000..50,000}, iid N(0,1) FP32, 10 nonzero
+    +-1, SNR 3, 100 lambdas to 0.05 lambda_max, alpha 1 (about 27 GB of designs,
+    all resident in HBM).  The chosen form is one persistent launch
+    (bl_fit_many_persistent), its launch shape picked by the autotuner on a
+    sample of the problems; beside it the worker form (bl_fit_many: host worker
+    threads, one stream and one bl_fit_path each) and the plain form (the
+    problems one after another through bl_fit_path, timed on a sample and
+    scaled).  Each is timed with CUDA events on the ctx stream around the call
+    (the calls synchronize before they return)."""
+    import numpy as np
     import torch
     from paper_1701_05936_gb300 import bl, synth
     dev = torch.device("cuda", local)
@@ -468,39 +472,74 @@ def many(local: int, nprob: int = 256, concurrency: int = 16):
     probs = synth.many_problems(nprob)
     gen_s = time.perf_counter() - t0
     dv = [(torch.from_numpy(q.X).to(dev), q.n, torch.from_numpy(q.y).to(dev)) for q in probs]
-    kw = dict(alpha=1.0, ratio=0.05, nlambda=100, eps=1e-7, cd_mode=bl.BL_CD_BLOCKED)
+    kw = dict(alpha=1.0, ratio=0.05, nlambda=100, eps=1e-7)
     ctx = bl.Context(local)
-    bl.bl_fit_many(ctx, dv[:concurrency], concurrency=concurrency, **kw)   # warm-up
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(ctx.stream)
-    res = bl.bl_fit_many(ctx, dv, concurrency=concurrency, **kw)
-    e1.record(ctx.stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        out = fn()
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    # the autotuner on every 8th problem, then the persistent launch over all of them
+    sample = dv[::8]
+    tune_ms, chosen = bl.bl_many_autotune(ctx, sample, **kw)
+    ctx.set_timing(True)
+    res, ms = timed(lambda: bl.bl_fit_many_persistent(ctx, dv, **kw))
+    updates = ctx.timing()["cd_updates"]
+    ctx.set_timing(False)
+    phases = bl.bl_many_phase_ms(ctx)
+    rows = bl.bl_many_problem_ms(ctx, nprob)
+    pms_each = np.array([r["total"] for r in rows])
+    slow = [int(i) for i in np.argsort(-pms_each)[:4]]
     ok = sum(r["status"] == bl.BL_OK for r in res)
     scanned = sum(float(r["cols_scanned"].sum()) * q.n * 4 for r, q in zip(res, probs))
-    # plain: one after another, on a sample of problems, scaled to all
-    sample = list(range(0, nprob, max(1, nprob // 16)))
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    p0.record(ctx.stream)
-    for i in sample:
-        X, n, y = dv[i]
-        bl.bl_fit_path(ctx, X, n, y, **kw)
-    p1.record(ctx.stream)
+    # the worker form and the difference between the two forms on a sample of problems
+    kww = dict(kw, cd_mode=bl.BL_CD_BLOCKED)
+    bl.bl_fit_many(ctx, dv[:concurrency], concurrency=concurrency, **kww)   # warm-up
     torch.cuda.synchronize()
-    plain_ms = p0.elapsed_time(p1) * sum(q.n * q.p for q in probs) / sum(probs[i].n * probs[i].p for i in sample)
+    resw, wms = timed(lambda: bl.bl_fit_many(ctx, dv, concurrency=concurrency, **kww))
+    diff = 0.0
+    for i in range(0, nprob, max(1, nprob // 8)):
+        diff = max(diff, float((bl.path_dense(res[i], probs[i].p) - bl.path_dense(resw[i], probs[i].p)).abs().max()))
+    # plain: one after another, on a sample of problems, scaled to all
+    psample = list(range(0, nprob, max(1, nprob // 16)))
+
+    def plain():
+        for i in psample:
+            X, n, y = dv[i]
+            bl.bl_fit_path(ctx, X, n, y, cd_mode=bl.BL_CD_BLOCKED, **kw)
+    _, pms = timed(plain)
+    plain_ms = pms * sum(q.n * q.p for q in probs) / sum(probs[i].n * probs[i].p for i in psample)
     ctx.close()
     total_bytes = sum(4.0 * q.n * q.p for q in probs)
+    peak = measured_peaks()[0]["hbm_gbs"]
     return {"workload": f"{nprob} problems, n ~ U{{100..2000}}, p ~ U{{1000..50000}}, iid N(0,1) FP32, 10 nonzero "
-                        f"+-1, SNR 3, 100 lambdas to 0.05 lambda_max, alpha 1", "concurrency": concurrency,
+                        f"+-1, SNR 3, 100 lambdas to 0.05 lambda_max, alpha 1",
+            "form": "one persistent launch (a one-node CUDA graph): each CTA runs a whole path, problems from a "
+                    "device queue, largest first",
             "value": nprob / (ms / 1e3), "unit": "problems/s", "ms": ms, "problems_ok": ok,
+            "cta_ms_by_phase": phases, "cd_updates": updates,
+            "problem_cta_ms": {"max": float(pms_each.max()), "median": float(np.median(pms_each)),
+                               "sum": float(pms_each.sum()),
+                               "slowest": [dict(shape=f"{probs[i].n}x{probs[i].p}",
+                                                sweeps=int(res[i]["sweeps"].sum()),
+                                                **{k: round(v, 1) for k, v in rows[i].items()}) for i in slow]},
+            "cd_ns_per_update_per_cta": 1e6 * phases["cd"] / max(1, updates),
+            "autotune": {"sample_problems": len(sample), "ms_per_shape": tune_ms,
+                         "shapes": bl.bl_many_configs(), "chosen": chosen},
             "design_bytes": total_bytes, "z_pass_bytes": scanned,
             "z_pass_gbs_whole_call": scanned / (ms / 1e3) / 1e9,
-            "note": "CUDA events on the ctx stream around the call; host worker threads drive per-problem streams",
+            "z_pass_frac_of_peak_whole_call": scanned / (ms / 1e3) / 1e9 / peak,
             "host_generation_s": gen_s,
+            "worker_form": {"form": "bl_fit_many: 16 host worker threads, each a stream and bl_fit_path "
+                                    "(blocked CD on a 3-SM cluster)", "ms": wms,
+                            "value": nprob / (wms / 1e3), "chosen_over_worker": wms / ms,
+                            "max_abs_coef_diff_on_8_problems": diff},
             "plain_form": {"form": "bl_fit_path one problem after another (sample scaled by n*p)",
-                           "ms_for_all": plain_ms, "sampled_problems": len(sample),
+                           "ms_for_all": plain_ms, "sampled_problems": len(psample),
                            "chosen_over_plain": plain_ms / ms}}
 
 

@@ -537,6 +537,59 @@ typedef struct {
  * BL_ERR_ARG before any launch for NULL pointers or nprob < 1.  Synchronizes. */
 int bl_fit_many(bl_ctx *ctx, bl_problem *probs, int nprob, const bl_options *opt, int concurrency);
 
+/* Many independent paths in ONE persistent kernel launch (issued as a one-node
+ * CUDA graph on the ctx stream).  The same path as bl_fit_path for each problem
+ * (Sec. 1, Sec. 2.2, Sec. 3.1.1: screening, the KKT loop of cyclic coordinate
+ * descent with residual updates, the record step), but every step of a
+ * problem's path runs inside one CTA, which takes problems from a device queue
+ * (largest p (n + 1024) first): no host round trip per lambda, and the z passes of
+ * about 150 problems stream at once.  Coordinate descent is the residual form
+ * (the blocked forms of opt->cd_mode are not used here).
+ * Covered: FP32 designs with n <= 2048 rows, screen BL_SCREEN_NONE, _SSR or
+ * _SSR_BEDPP, xprec BL_XPREC_NATIVE.  Every other problem, and any problem
+ * whose working set outgrows the launch shape's shared-memory capacity, is
+ * solved afterwards by bl_fit_many's worker form, so every problem gets its
+ * path.  config: a launch shape index (0 .. bl_many_num_configs() - 1), or -1
+ * for the one bl_many_autotune chose on this ctx (a default before that).
+ * Device scratch (about 68 bytes per feature and 16 per row of every problem)
+ * is held by the ctx and only grows.  Returns BL_OK when every problem
+ * succeeded, else the status of the first failing problem in index order
+ * (each problem's status is in bl_problem.status).  BL_ERR_ARG before any
+ * launch for NULL pointers, nprob < 1, a warm start, or bad options.
+ * Synchronizes. */
+int bl_fit_many_persistent(bl_ctx *ctx, bl_problem *probs, int nprob, const bl_options *opt, int config);
+
+/* Number of launch shapes of bl_fit_many_persistent (threads per CTA, CTAs per
+ * SM, loads in flight per lane of the z pass). */
+int bl_many_num_configs(void);
+
+/* Description of launch shape `config` ("" when out of range); a static string. */
+const char *bl_many_config_name(int config);
+
+/* CTA time, in milliseconds summed over the CTAs, that the last persistent
+ * launch on this ctx spent in each phase: [0] setup (y centring, standardization
+ * with x~'y, lambda_max), [1] BEDPP init, [2] screening, [3] working-set
+ * compaction, [4] FP64 reference gradients, [5] coordinate descent, [6] FP64
+ * residual, [7] z pass with the KKT test, [8] record.  The first count (at
+ * most 9) entries are written. */
+int bl_many_phase_ms(const bl_ctx *ctx, double *ms, int count);
+
+/* CTA time, in milliseconds, of each problem the last persistent launch on this
+ * ctx solved (problems in index order, those passed to the worker form left
+ * out): 11 values per problem, its whole time, its time in each phase of
+ * bl_many_phase_ms, and its number of coordinate updates.  Writes at most count values; returns the number
+ * written (or BL_ERR_ARG). */
+int bl_many_problem_ms(const bl_ctx *ctx, double *ms, int count);
+
+/* Autotuner of bl_fit_many_persistent: runs the persistent launch over the given
+ * problems (a sample of the workload; their outputs are written as by
+ * bl_fit_many_persistent, fallback problems excepted) once per launch shape,
+ * times each launch with CUDA events, and keeps the fastest for later calls on
+ * this ctx with config = -1.  ms (nullable, bl_many_num_configs() entries): the
+ * time of each shape; chosen (nullable): the index kept.  BL_ERR_UNSUPPORTED when
+ * opt's rule is not covered or no sample problem fits the persistent form. */
+int bl_many_autotune(bl_ctx *ctx, bl_problem *probs, int nprob, const bl_options *opt, double *ms, int *chosen);
+
 /* Largest working set that bl_cd_active_noalloc accepts. */
 #define BL_NOALLOC_MAX_WORK 4096
 

@@ -18,6 +18,7 @@ import re
 import threading
 from typing import Optional
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -123,6 +124,12 @@ def lib():
                                         C.POINTER(bl_path)],
                 "bl_mlp_predict": [_vp, _vp, _vp, _i64, _vp],
                 "bl_fit_many": [_vp, C.POINTER(bl_problem), _int, C.POINTER(bl_options), _int],
+                "bl_fit_many_persistent": [_vp, C.POINTER(bl_problem), _int, C.POINTER(bl_options), _int],
+                "bl_many_autotune": [_vp, C.POINTER(bl_problem), _int, C.POINTER(bl_options),
+                                     C.POINTER(C.c_double), C.POINTER(C.c_int)],
+                "bl_many_num_configs": [],
+                "bl_many_phase_ms": [_vp, C.POINTER(C.c_double), _int],
+                "bl_many_problem_ms": [_vp, C.POINTER(C.c_double), _int],
                 "bl_mlp_loss_grad": [_vp, _vp, _vp, _vp, _i64, _vp, C.POINTER(_dbl)],
                 "bl_mlp_train": [_vp, _vp, _vp, _i64, _vp, _int, _i64, _dbl, C.c_uint64, C.POINTER(_dbl)],
                 "bl_mlp_save": [_vp, C.c_char_p],
@@ -136,6 +143,8 @@ def lib():
             L.bl_last_error.restype = C.c_char_p
             L.bl_version.argtypes = []
             L.bl_version.restype = C.c_char_p
+            L.bl_many_config_name.argtypes = [_int]
+            L.bl_many_config_name.restype = C.c_char_p
             _lib = L
     return _lib
 
@@ -380,15 +389,12 @@ def bl_fit_path(ctx, X, n, y, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, lambd
     return res
 
 
-def bl_fit_many(ctx, problems, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, screen=BL_SCREEN_SSR_BEDPP,
-                cd_mode=BL_CD_RESIDUAL, max_sweeps=100_000, concurrency=0):
-    """Independent paths at once.  problems: a list of (X (p, ldx) device, n, y
-    (n,) FP64 device).  Returns one bl_fit_path-shaped dict per problem, each
-    with its own status."""
+def _many_array(problems, nlambda, lambdas=None):
+    """bl_problem records (and the output tensors they point at) for a list of
+    (X (p, ldx) device, n, y (n,) FP64 device) problems."""
     nprob = len(problems)
     arr = (bl_problem * nprob)()
-    keep = []
-    res = []
+    keep, res = [], []
     o = torch.zeros
     for i, (X, n, y) in enumerate(problems):
         dev = X.device
@@ -414,21 +420,103 @@ def bl_fit_many(ctx, problems, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, scre
         arr[i].nlambda = K
         arr[i].n, arr[i].p, arr[i].ldx = n_, p_, ldx
         arr[i].y = y.data_ptr()
+        if lambdas is not None:
+            lh = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))
+            keep.append(lh)
+            arr[i].lambdas = lh.ctypes.data
         arr[i].out = C.cast(C.pointer(path), C.c_void_p)
         keep.append(path)
         r.update(host)
         res.append(r)
+    return arr, keep, res
+
+
+def _many_results(arr, keep, res):
+    paths = [k for k in keep if isinstance(k, bl_path)]
+    for i, r in enumerate(res):
+        pth = paths[i]
+        r.update(status=arr[i].status, nnz=pth.nnz_needed, lambda_max=pth.lambda_max, jstar=pth.jstar,
+                 ybar=pth.ybar)
+    return res
+
+
+def bl_fit_many(ctx, problems, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, screen=BL_SCREEN_SSR_BEDPP,
+                cd_mode=BL_CD_RESIDUAL, max_sweeps=100_000, concurrency=0):
+    """Independent paths at once.  problems: a list of (X (p, ldx) device, n, y
+    (n,) FP64 device).  Returns one bl_fit_path-shaped dict per problem, each
+    with its own status."""
+    nprob = len(problems)
+    arr, keep, res = _many_array(problems, nlambda)
     opt = bl_options(float(alpha), float(eps), float(ratio), int(max_sweeps), int(screen), int(cd_mode))
     st = lib().bl_fit_many(ctx.h, arr, nprob, C.byref(opt), int(concurrency))
     if st not in (BL_OK, BL_ERR_NOT_CONVERGED):
         bad = [i for i in range(nprob) if arr[i].status not in (BL_OK, BL_ERR_NOT_CONVERGED)]
         if not bad:
             ctx.check(st)
-    for i in range(nprob):
-        pth = keep[i]
-        res[i].update(status=arr[i].status, nnz=pth.nnz_needed, lambda_max=pth.lambda_max, jstar=pth.jstar,
-                      ybar=pth.ybar)
-    return res
+    return _many_results(arr, keep, res)
+
+
+def bl_fit_many_persistent(ctx, problems, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7,
+                           screen=BL_SCREEN_SSR_BEDPP, cd_mode=BL_CD_RESIDUAL, max_sweeps=100_000, config=-1,
+                           timeout_ns=0, lambdas=None):
+    """The same paths as bl_fit_many from one persistent kernel launch (problems
+    outside its coverage are solved by the worker form).  config: launch shape
+    index, -1 for the autotuned one."""
+    nprob = len(problems)
+    arr, keep, res = _many_array(problems, nlambda, lambdas)
+    opt = bl_options(float(alpha), float(eps), float(ratio), int(max_sweeps), int(screen), int(cd_mode))
+    opt.timeout_ns = int(timeout_ns)
+    st = lib().bl_fit_many_persistent(ctx.h, arr, nprob, C.byref(opt), int(config))
+    if st not in (BL_OK, BL_ERR_NOT_CONVERGED):
+        bad = [i for i in range(nprob) if arr[i].status not in (BL_OK, BL_ERR_NOT_CONVERGED)]
+        if not bad:
+            ctx.check(st)
+    return _many_results(arr, keep, res)
+
+
+def bl_many_configs():
+    """Descriptions of the persistent form's launch shapes."""
+    L = lib()
+    return [L.bl_many_config_name(c).decode() for c in range(L.bl_many_num_configs())]
+
+
+MANY_PHASES = ["setup", "bedpp_init", "screen", "working_set", "gref", "cd", "residual", "zpass", "record"]
+
+
+def bl_many_phase_ms(ctx):
+    """CTA milliseconds by phase of the last persistent launch on ctx."""
+    out = (C.c_double * len(MANY_PHASES))()
+    ctx.check(lib().bl_many_phase_ms(ctx.h, out, len(MANY_PHASES)))
+    return dict(zip(MANY_PHASES, [float(v) for v in out]))
+
+
+def bl_many_problem_ms(ctx, count):
+    """Per problem of the last persistent launch on ctx (at most count problems):
+    a dict with its CTA milliseconds ("total") and its milliseconds by phase."""
+    per = 2 + len(MANY_PHASES)
+    out = (C.c_double * max(1, count * per))()
+    k = lib().bl_many_problem_ms(ctx.h, out, int(count * per))
+    if k < 0:
+        ctx.check(k)
+    rows = []
+    for i in range(k // per):
+        v = [float(out[i * per + x]) for x in range(per)]
+        rows.append(dict(total=v[0], updates=int(v[-1]), **dict(zip(MANY_PHASES, v[1:-1]))))
+    return rows
+
+
+def bl_many_autotune(ctx, problems, alpha=1.0, ratio=0.1, nlambda=100, eps=1e-7, screen=BL_SCREEN_SSR_BEDPP,
+                     max_sweeps=100_000):
+    """Time every launch shape of the persistent form on these problems and keep
+    the fastest on ctx.  Returns (ms per shape, chosen index)."""
+    nprob = len(problems)
+    arr, keep, res = _many_array(problems, nlambda)
+    opt = bl_options(float(alpha), float(eps), float(ratio), int(max_sweeps), int(screen), BL_CD_RESIDUAL)
+    nc = lib().bl_many_num_configs()
+    ms = (C.c_double * nc)()
+    chosen = C.c_int(-1)
+    ctx.check(lib().bl_many_autotune(ctx.h, arr, nprob, C.byref(opt), ms, C.byref(chosen)))
+    return [float(v) for v in ms], int(chosen.value)
 
 
 def bl_mlp_predict(ctx, w, F):

@@ -73,6 +73,11 @@ struct bl_ctx {
     int32_t *rlist = nullptr;
     size_t rlist_bytes = 0;
     int64_t recheck_cols = 0;
+    void *many = nullptr;      // bl_fit_many_persistent: descriptors, results and per-problem scratch
+    size_t many_bytes = 0;
+    int many_cfg = -1;         // launch shape chosen by bl_many_autotune (-1: not tuned)
+    double many_phase_ms[MANY_PHASES] = {};  // CTA time by phase of the last persistent launch
+    std::vector<double> many_prob_ms;        // per problem of that launch: CTA ms, then ms by phase
     int64_t kernels = 0;
     int64_t cd_updates = 0;
 };
@@ -356,6 +361,7 @@ extern "C" int bl_ctx_destroy(bl_ctx *ctx)
     if (ctx->packed) cudaFree(ctx->packed);
     if (ctx->xbf) cudaFree(ctx->xbf);
     if (ctx->rlist) cudaFree(ctx->rlist);
+    if (ctx->many) cudaFree(ctx->many);
     if (ctx->sc_host) cudaFreeHost(ctx->sc_host);
     delete ctx;
     return BL_OK;
@@ -1077,6 +1083,332 @@ extern "C" int bl_fit_many(bl_ctx *ctx, bl_problem *probs, int nprob, const bl_o
     cleanup();
     for (int i = 0; i < nprob; ++i)
         if (probs[i].status != BL_OK) return fail(ctx, probs[i].status, "a problem failed (see bl_problem.status)");
+    return BL_OK;
+}
+
+// ------------------------------------------------ many problems, one launch
+namespace {
+
+constexpr int MANY_DEFAULT_CFG = 1;
+
+// Whether the persistent form takes problem q under opt (the rest go to the
+// worker form of bl_fit_many).
+bool many_eligible(const bl_problem &q, const bl_options *opt)
+{
+    if (!q.X || !q.y || !q.out || q.nlambda < 1 || q.dtype != BL_F32) return false;
+    if (q.n < 1 || q.n > MANY_NMAX || q.p < 1 || q.p > 2147483647LL || q.ldx < q.n) return false;
+    if ((q.ldx * 4) % 16 != 0 || ((uintptr_t)q.X) % 16 != 0) return false;
+    const bl_path *o = q.out;
+    if (!o->lambdas || !o->col_ptr || !o->intercept || !o->loss || o->nnz_capacity < 0 ||
+        (o->nnz_capacity > 0 && (!o->row_idx || !o->val)))
+        return false;
+    if (q.lambdas) {
+        for (int k = 0; k < q.nlambda; ++k) {
+            if (!(q.lambdas[k] > 0.0)) return false;
+            if (k > 0 && !(q.lambdas[k] < q.lambdas[k - 1])) return false;
+        }
+    } else if (q.nlambda > 1 && !(opt->lambda_min_ratio > 0.0 && opt->lambda_min_ratio < 1.0)) {
+        return false;
+    }
+    return true;
+}
+
+// One persistent launch over the eligible problems `sel` with launch shape
+// cfg.  Problems whose working set outgrew the shape's capacity are appended
+// to `redo`.  *ms (nullable): device time of the launch.
+int many_run(bl_ctx *ctx, bl_problem *probs, const std::vector<int> &sel, const bl_options *opt, int cfg,
+             std::vector<int> &redo, float *ms)
+{
+    const int m = (int)sel.size();
+    if (m == 0) return BL_OK;
+    cudaStream_t s = ctx->stream;
+    const int wcap = many_wcap(cfg);
+    // layout: [descriptors | order | queue, updates | user lambdas] [stats | scal | status] [scratch...]
+    size_t nlam_in = 0, nstat = 0;
+    for (int q : sel) {
+        if (probs[q].lambdas) nlam_in += (size_t)probs[q].nlambda;
+        nstat += (size_t)MANY_STATS * (size_t)probs[q].nlambda;
+    }
+    const size_t off_order = align256((size_t)m * sizeof(ManyProblem));
+    const size_t off_q = off_order + align256((size_t)m * 4);
+    const size_t off_lam = off_q + 256;
+    const size_t head = off_lam + align256(nlam_in * 8);
+    const size_t off_scal = align256(nstat * 8);
+    const size_t off_stat = off_scal + align256((size_t)m * MANY_SCAL * 8);
+    const size_t res = off_stat + align256((size_t)m * 4);
+    size_t scratch = 0;
+    for (int q : sel) {
+        const size_t p = (size_t)probs[q].p, n = (size_t)probs[q].n;
+        scratch += 6 * align256(p * 8) + 5 * align256(p * 4) + 3 * align256(p) + 2 * align256(n * 8);
+    }
+    const size_t total = head + res + scratch;
+    if (ctx->many_bytes < total) {
+        CK(cudaStreamSynchronize(s));
+        if (ctx->many) cudaFree(ctx->many);
+        ctx->many = nullptr;
+        ctx->many_bytes = 0;
+        CK(cudaMalloc(&ctx->many, total));
+        ctx->many_bytes = total;
+    }
+    char *base = (char *)ctx->many;
+    char *rbase = base + head;
+    char *sp = rbase + res;
+    std::vector<char> himg(head, 0);
+    ManyProblem *D = reinterpret_cast<ManyProblem *>(himg.data());
+    double *lam_h = reinterpret_cast<double *>(himg.data() + off_lam);
+    size_t lam_pos = 0, stat_pos = 0;
+    auto take = [&](size_t bytes) {
+        char *r = sp;
+        sp += align256(bytes);
+        return r;
+    };
+    for (int t = 0; t < m; ++t) {
+        const bl_problem &q = probs[sel[(size_t)t]];
+        ManyProblem &d = D[t];
+        const size_t p = (size_t)q.p, n = (size_t)q.n;
+        d.X = (const float *)q.X;
+        d.n = q.n;
+        d.p = q.p;
+        d.ldx = q.ldx;
+        d.y = q.y;
+        d.K = q.nlambda;
+        d.lam_in = nullptr;
+        if (q.lambdas) {
+            std::memcpy(lam_h + lam_pos, q.lambdas, (size_t)q.nlambda * 8);
+            d.lam_in = reinterpret_cast<const double *>(base + off_lam) + lam_pos;
+            lam_pos += (size_t)q.nlambda;
+        }
+        d.lambdas = q.out->lambdas;
+        d.col_ptr = q.out->col_ptr;
+        d.row_idx = q.out->row_idx;
+        d.val = q.out->val;
+        d.val_orig = q.out->val_orig;
+        d.cap = q.out->nnz_capacity;
+        d.intercept = q.out->intercept;
+        d.loss = q.out->loss;
+        d.stats = reinterpret_cast<int64_t *>(rbase) + stat_pos;
+        stat_pos += (size_t)MANY_STATS * (size_t)q.nlambda;
+        d.scal = reinterpret_cast<double *>(rbase + off_scal) + MANY_SCAL * (size_t)t;
+        d.status = reinterpret_cast<int32_t *>(rbase + off_stat) + t;
+        d.center = (double *)take(p * 8);
+        d.scale = (double *)take(p * 8);
+        d.inv_scale = (double *)take(p * 8);
+        d.xnorm = (double *)take(p * 8);
+        d.xty = (double *)take(p * 8);
+        d.xtxs = (double *)take(p * 8);
+        d.c32 = (float *)take(p * 4);
+        d.is32 = (float *)take(p * 4);
+        d.z = (float *)take(p * 4);
+        d.beta = (float *)take(p * 4);
+        d.keep = (uint8_t *)take(p);
+        d.safe = (uint8_t *)take(p);
+        d.working = (uint8_t *)take(p);
+        d.slist = (int32_t *)take(p * 4);
+        d.yc = (double *)take(n * 8);
+        d.xcs = (double *)take(n * 8);
+    }
+    // queue order: the costliest first, so that no long path is left to run alone
+    // at the end.  A CTA's time per lambda grows with p (n + 1024): the bytes of
+    // the z pass plus a per-column cost (screen, z-pass epilogue) of about 1024 rows
+    std::vector<int> ord((size_t)m);
+    for (int t = 0; t < m; ++t) ord[(size_t)t] = t;
+    auto cost = [&](int t) {
+        const bl_problem &q = probs[sel[(size_t)t]];
+        return (double)q.p * ((double)q.n + 1024.0);
+    };
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    std::memcpy(himg.data() + off_order, ord.data(), (size_t)m * 4);  // queue counter and updates stay 0
+    CK(cudaMemcpyAsync(base, himg.data(), head, cudaMemcpyHostToDevice, s));
+    ManyArgs a{};
+    a.probs = reinterpret_cast<const ManyProblem *>(base);
+    a.order = reinterpret_cast<const int32_t *>(base + off_order);
+    a.nprob = m;
+    a.queue = reinterpret_cast<unsigned int *>(base + off_q);
+    a.updates = reinterpret_cast<unsigned long long *>(base + off_q + 128);
+    a.phase_ns = reinterpret_cast<unsigned long long *>(base + off_q + 136);
+    a.alpha = opt->alpha;
+    a.eps = opt->eps;
+    a.ratio = opt->lambda_min_ratio;
+    a.max_sweeps = opt->max_sweeps;
+    a.time_limit_ns = opt->timeout_ns > 0 ? (uint64_t)opt->timeout_ns : CD_TIME_LIMIT_NS;
+    a.screen = opt->screen;
+    a.wcap = wcap;
+    CK(many_prepare(cfg, wcap));
+    // the launch as a one-node CUDA graph, recorded on a private stream (the ctx
+    // stream may be the legacy default stream, which cannot be captured) and
+    // replayed on the ctx stream
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cs = nullptr;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        const cudaError_t le = launch_many(cfg, a, ctx->num_sms, cs);
+        e = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = le;
+    }
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(ctx, e, "persistent many-problem launch (capture)");
+    }
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    cudaEvent_t e0 = get_event(ctx), e1 = get_event(ctx);
+    cudaEventRecord(e0, s);
+    e = cudaGraphLaunch(exec, s);
+    cudaEventRecord(e1, s);
+    ctx->kernels += 1;
+    std::vector<char> rimg(res + 8 * (1 + MANY_PHASES));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rimg.data(), rbase, res, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(rimg.data() + res, base + off_q + 128, 8 * (1 + MANY_PHASES), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaGraphExecDestroy(exec);
+    float t_ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&t_ms, e0, e1);
+    ctx->pool.push_back(e0);
+    ctx->pool.push_back(e1);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "persistent many-problem launch");
+    if (ms) *ms = t_ms;
+    unsigned long long upd = 0, phs[MANY_PHASES];
+    std::memcpy(&upd, rimg.data() + res, 8);
+    std::memcpy(phs, rimg.data() + res + 8, 8 * MANY_PHASES);
+    for (int x = 0; x < MANY_PHASES; ++x) ctx->many_phase_ms[x] = (double)phs[x] * 1e-6;
+    ctx->many_prob_ms.clear();
+    ctx->cd_updates += (int64_t)upd;
+    const int64_t *stats_h = reinterpret_cast<const int64_t *>(rimg.data());
+    const double *scal_h = reinterpret_cast<const double *>(rimg.data() + off_scal);
+    const int32_t *st_h = reinterpret_cast<const int32_t *>(rimg.data() + off_stat);
+    size_t sp2 = 0;
+    for (int t = 0; t < m; ++t) {
+        bl_problem &q = probs[sel[(size_t)t]];
+        bl_path *o = q.out;
+        const int K = q.nlambda;
+        const int32_t bits = st_h[t];
+        const int64_t *stt = stats_h + sp2;
+        sp2 += (size_t)MANY_STATS * (size_t)K;
+        if (bits & ST_WORKING_TOO_BIG) {
+            redo.push_back(sel[(size_t)t]);
+            continue;
+        }
+        const double *sc = scal_h + MANY_SCAL * (size_t)t;
+        o->lambda_max = sc[0];
+        o->ybar = sc[1];
+        o->jstar = (int64_t)sc[2];
+        o->nnz_needed = (int64_t)sc[3];
+        for (int x = 0; x < 2 + MANY_PHASES; ++x) ctx->many_prob_ms.push_back(sc[4 + x]);
+        o->prop_count = 0;
+        int64_t *dst[MANY_STATS] = {o->sweeps, o->n_safe, o->n_strong, o->kkt_rounds, o->cols_scanned, o->n_active};
+        for (int c = 0; c < MANY_STATS; ++c)
+            if (dst[c])
+                for (int k = 0; k < K; ++k) dst[c][k] = stt[(size_t)c * K + k];
+        if (bits & ST_TIMEOUT) q.status = BL_ERR_TIMEOUT;
+        else if ((bits & ST_CAPACITY) || o->nnz_needed > o->nnz_capacity) q.status = BL_ERR_CAPACITY;
+        else if (bits & (ST_NOT_CONVERGED | ST_KKT_CAP)) q.status = BL_ERR_NOT_CONVERGED;
+        else q.status = BL_OK;
+    }
+    return BL_OK;
+}
+
+int many_check(bl_ctx *ctx, bl_problem *probs, int nprob, const bl_options *opt)
+{
+    if (!ctx) return BL_ERR_ARG;
+    if (!probs || !opt || nprob < 1) return fail(ctx, BL_ERR_ARG, "NULL argument or nprob < 1");
+    if (opt->warm_beta) return fail(ctx, BL_ERR_ARG, "warm_beta resumes one path: use bl_fit_path");
+    if (!(opt->alpha > 0.0 && opt->alpha <= 1.0)) return fail(ctx, BL_ERR_ARG, "alpha must be in (0, 1]");
+    if (!(opt->eps > 0.0)) return fail(ctx, BL_ERR_ARG, "eps must be > 0");
+    if (opt->max_sweeps < 1) return fail(ctx, BL_ERR_ARG, "max_sweeps must be >= 1");
+    if (opt->timeout_ns < 0) return fail(ctx, BL_ERR_ARG, "timeout_ns < 0");
+    for (int i = 0; i < nprob; ++i)
+        if (!probs[i].out || !probs[i].X || !probs[i].y || probs[i].nlambda < 1)
+            return fail(ctx, BL_ERR_ARG, "every problem needs X, y, out and nlambda >= 1");
+    return BL_OK;
+}
+
+bool many_rule_ok(const bl_options *opt)
+{
+    return (opt->screen == BL_SCREEN_NONE || opt->screen == BL_SCREEN_SSR || opt->screen == BL_SCREEN_SSR_BEDPP) &&
+           opt->xprec == BL_XPREC_NATIVE;
+}
+
+}  // namespace
+
+extern "C" int bl_many_num_configs(void) { return many_num_configs(); }
+
+extern "C" int bl_many_phase_ms(const bl_ctx *ctx, double *ms, int count)
+{
+    if (!ctx || !ms || count < 0) return BL_ERR_ARG;
+    for (int x = 0; x < count && x < MANY_PHASES; ++x) ms[x] = ctx->many_phase_ms[x];
+    return BL_OK;
+}
+
+extern "C" int bl_many_problem_ms(const bl_ctx *ctx, double *ms, int count)
+{
+    if (!ctx || !ms || count < 0) return BL_ERR_ARG;
+    const int k = std::min<int>(count, (int)ctx->many_prob_ms.size());
+    for (int i = 0; i < k; ++i) ms[i] = ctx->many_prob_ms[(size_t)i];
+    return k;
+}
+
+extern "C" const char *bl_many_config_name(int config) { return many_config_name(config); }
+
+extern "C" int bl_fit_many_persistent(bl_ctx *ctx, bl_problem *probs, int nprob, const bl_options *opt, int config)
+{
+    int st = many_check(ctx, probs, nprob, opt);
+    if (st) return st;
+    if (config >= many_num_configs()) return fail(ctx, BL_ERR_ARG, "unknown launch configuration");
+    ctx->err.clear();
+    CK(cudaSetDevice(ctx->device));
+    const int cfg = config >= 0 ? config : (ctx->many_cfg >= 0 ? ctx->many_cfg : MANY_DEFAULT_CFG);
+    std::vector<int> sel, redo;
+    for (int i = 0; i < nprob; ++i) {
+        probs[i].status = BL_OK;
+        if (many_rule_ok(opt) && many_eligible(probs[i], opt)) sel.push_back(i);
+        else redo.push_back(i);
+    }
+    if ((st = many_run(ctx, probs, sel, opt, cfg, redo, nullptr))) return st;
+    if (!redo.empty()) {  // the rest through the worker form (the solver of bl_fit_path)
+        std::sort(redo.begin(), redo.end());
+        std::vector<bl_problem> sub;
+        for (int i : redo) sub.push_back(probs[i]);
+        const std::string keep_err = ctx->err;
+        bl_fit_many(ctx, sub.data(), (int)sub.size(), opt, 0);
+        for (size_t t = 0; t < redo.size(); ++t) probs[redo[t]].status = sub[t].status;
+        if (ctx->err.empty()) ctx->err = keep_err;
+    }
+    for (int i = 0; i < nprob; ++i)
+        if (probs[i].status != BL_OK) return fail(ctx, probs[i].status, "a problem failed (see bl_problem.status)");
+    return BL_OK;
+}
+
+extern "C" int bl_many_autotune(bl_ctx *ctx, bl_problem *probs, int nprob, const bl_options *opt, double *ms,
+                                int *chosen)
+{
+    int st = many_check(ctx, probs, nprob, opt);
+    if (st) return st;
+    if (!many_rule_ok(opt)) return fail(ctx, BL_ERR_UNSUPPORTED, "the persistent form covers SSR and SSR-BEDPP");
+    ctx->err.clear();
+    CK(cudaSetDevice(ctx->device));
+    std::vector<int> sel;
+    for (int i = 0; i < nprob; ++i)
+        if (many_eligible(probs[i], opt)) sel.push_back(i);
+    if (sel.empty()) return fail(ctx, BL_ERR_UNSUPPORTED, "no problem of the sample fits the persistent form");
+    int best = -1;
+    float best_ms = 0.f;
+    for (int c = 0; c < many_num_configs(); ++c) {
+        std::vector<int> redo;
+        float t = 0.f;
+        if ((st = many_run(ctx, probs, sel, opt, c, redo, &t))) return st;
+        if (ms) ms[c] = t;
+        if (best < 0 || t < best_ms) {
+            best = c;
+            best_ms = t;
+        }
+    }
+    ctx->many_cfg = best;
+    if (chosen) *chosen = best;
     return BL_OK;
 }
 

@@ -306,4 +306,61 @@ struct RecordArgs {
 };
 cudaError_t launch_record(const RecordArgs &a, DevScalars *sc, cudaStream_t st);
 
+// ---- many problems in one persistent launch (bl_many.cu)
+constexpr int64_t MANY_NMAX = 2048;  // rows of a problem the persistent form holds on chip
+constexpr int MANY_STATS = 6;        // per-lambda counters: sweeps, n_safe, n_strong, kkt_rounds, cols_scanned, nonzeros
+constexpr int ST_KKT_CAP = 32;       // the KKT loop reached its round cap (the problem stops)
+// CTA time of the persistent form by phase: setup (y centring, standardization,
+// lambda_max), BEDPP init, screen, working set, reference gradients, CD,
+// residual, z pass, record
+constexpr int MANY_PHASES = 9;
+constexpr int MANY_SCAL = 6 + MANY_PHASES;  // and the problem's ms by phase, its CD updates
+// One problem: the design, the response and the outputs of bl_fit_path, plus
+// device scratch (p- and n-sized arrays) that only this problem's CTA touches.
+struct ManyProblem {
+    const float *X;
+    int64_t n, p, ldx;
+    const double *y;
+    const double *lam_in;  // device [K], or null: the grid lambda_max * ratio^(k/(K-1))
+    int32_t K;
+    int32_t pad;
+    double *lambdas;
+    int64_t *col_ptr;
+    int32_t *row_idx;
+    double *val, *val_orig;
+    int64_t cap;
+    double *intercept, *loss;
+    int64_t *stats;    // [MANY_STATS * K], counter c of lambda k at c * K + k
+    double *scal;      // [MANY_SCAL]: lambda_max, ybar, jstar, nonzeros of the path, ms on the CTA, ms by phase
+    int32_t *status;   // ST_* bits
+    double *center, *scale, *inv_scale, *xnorm, *xty, *xtxs;  // [p]
+    float *c32, *is32, *z, *beta;                               // [p]
+    uint8_t *keep, *safe, *working;                             // [p]
+    int32_t *slist;                                             // [p]: the columns the z passes read
+    double *yc, *xcs;                                           // [n]
+};
+struct ManyArgs {
+    const ManyProblem *probs;
+    const int32_t *order;    // queue order (problem indices)
+    int nprob;
+    unsigned int *queue;     // next queue position (0 at launch)
+    double alpha, eps, ratio;
+    int64_t max_sweeps;
+    uint64_t time_limit_ns;  // per coordinate-descent phase
+    int screen;              // BL_SCREEN_NONE, _SSR or _SSR_BEDPP
+    int wcap;                // largest working set (shared-memory arrays)
+    unsigned long long *updates;
+    unsigned long long *phase_ns;  // [MANY_PHASES], summed over CTAs
+};
+// Candidate launch shapes of the persistent kernel (the autotuner's choices).
+int many_num_configs();
+const char *many_config_name(int c);
+// Dynamic shared memory at working-set capacity wcap; the largest wcap that
+// configuration c's occupancy leaves room for.
+size_t many_smem(int wcap);
+int many_wcap(int c);
+// Set the kernel's shared-memory limit (before any stream capture), then launch.
+cudaError_t many_prepare(int c, int wcap);
+cudaError_t launch_many(int c, const ManyArgs &a, int num_sms, cudaStream_t st);
+
 }  // namespace bl
