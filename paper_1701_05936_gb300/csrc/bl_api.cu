@@ -1089,7 +1089,7 @@ extern "C" int bl_fit_many(bl_ctx *ctx, bl_problem *probs, int nprob, const bl_o
 // ------------------------------------------------ many problems, one launch
 namespace {
 
-constexpr int MANY_DEFAULT_CFG = 1;
+constexpr int MANY_DEFAULT_CFG = 2;
 
 // Whether the persistent form takes problem q under opt (the rest go to the
 // worker form of bl_fit_many).
@@ -1139,7 +1139,7 @@ int many_run(bl_ctx *ctx, bl_problem *probs, const std::vector<int> &sel, const 
     size_t scratch = 0;
     for (int q : sel) {
         const size_t p = (size_t)probs[q].p, n = (size_t)probs[q].n;
-        scratch += 6 * align256(p * 8) + 5 * align256(p * 4) + 3 * align256(p) + 2 * align256(n * 8);
+        scratch += 6 * align256(p * 8) + 5 * align256(p * 4) + 3 * align256(p) + align256(n * 8);
     }
     const size_t total = head + res + scratch;
     if (ctx->many_bytes < total) {
@@ -1205,7 +1205,6 @@ int many_run(bl_ctx *ctx, bl_problem *probs, const std::vector<int> &sel, const 
         d.working = (uint8_t *)take(p);
         d.slist = (int32_t *)take(p * 4);
         d.yc = (double *)take(n * 8);
-        d.xcs = (double *)take(n * 8);
     }
     // queue order: the costliest first, so that no long path is left to run alone
     // at the end.  A CTA's time per lambda grows with p (n + 1024): the bytes of

@@ -337,7 +337,7 @@ struct ManyProblem {
     float *c32, *is32, *z, *beta;                               // [p]
     uint8_t *keep, *safe, *working;                             // [p]
     int32_t *slist;                                             // [p]: the columns the z passes read
-    double *yc, *xcs;                                           // [n]
+    double *yc;                                                 // [n]
 };
 struct ManyArgs {
     const ManyProblem *probs;

@@ -301,14 +301,15 @@ __device__ __noinline__ void many_zpass(const ManyProblem &P, int64_t n, int64_t
     const uint32_t cbytes = (uint32_t)(((uint64_t)n * 4 + 15) & ~(uint64_t)15);
     const int64_t zstep = (int64_t)NW * CPW;
     if (li == 0 && wid * CPW + gi + zstep < nscan)
-        prefetch_l2(X + (int64_t)P.slist[wid * CPW + gi + zstep] * ldx, cbytes);
+        for (int k = 1; k < 3; ++k)
+            if (wid * CPW + gi + k * zstep < nscan) prefetch_l2(X + (int64_t)P.slist[wid * CPW + gi + k * zstep] * ldx, cbytes);
     for (int64_t m0 = (int64_t)wid * CPW; m0 < nscan; m0 += zstep) {
         const int64_t m = m0 + gi;
         const bool act = m < nscan;
         const int64_t j = act ? (int64_t)P.slist[m] : 0;
         // this group's column two iterations ahead into L2; the epilogue's
         // operands now, so that their latency overlaps the column's loads
-        if (li == 0 && m + 2 * zstep < nscan) prefetch_l2(X + (int64_t)P.slist[m + 2 * zstep] * ldx, cbytes);
+        if (li == 0 && m + 3 * zstep < nscan) prefetch_l2(X + (int64_t)P.slist[m + 3 * zstep] * ldx, cbytes);
         double isj = 0.0, cj = 0.0, xnj = 0.0;
         bool kkt_j = false;
         if (act) {
@@ -429,6 +430,7 @@ __global__ void __launch_bounds__(NT, MINB) k_many_path(ManyArgs a)
         for (int64_t i = tid; i < n; i += NT) {
             const double v = P.y[i] - ybar;
             P.yc[i] = v;
+            r64_s[i] = v;  // (the standardization pass reads yc from shared memory)
             s1 += v;
             s2 += v * v;
         }
@@ -456,7 +458,7 @@ __global__ void __launch_bounds__(NT, MINB) k_many_path(ManyArgs a)
                         ps += d;
                         pss = fmaf(d, d, pss);
                         varies |= (d != 0.f);
-                        sdy = fma((double)e - x0d, P.yc[i], sdy);
+                        sdy = fma((double)e - x0d, r64_s[i], sdy);
                     }
                 }
                 sd += (double)ps;
@@ -524,9 +526,10 @@ __global__ void __launch_bounds__(NT, MINB) k_many_path(ManyArgs a)
             const float *cs = X + jstar * ldx;
             const double cstar = P.center[jstar];
             double sx = 0.0;
+            __syncthreads();  // (every warp is done with yc in r64_s)
             for (int64_t i = tid; i < n; i += NT) {
                 const double v = (double)__ldg(cs + i) - cstar;
-                P.xcs[i] = v;
+                r64_s[i] = v;
                 sx += v;
             }
             const double sum_xcs = bsum<NW>(sx, dbuf);
@@ -539,12 +542,13 @@ __global__ void __launch_bounds__(NT, MINB) k_many_path(ManyArgs a)
                 const float *col = X + j * ldx;
                 const double x0 = (double)__ldg(col);
                 double acc = 0.0;
-                for (int64_t i = lane; i < n; i += 32) acc = fma((double)__ldg(col + i) - x0, P.xcs[i], acc);
+                for (int64_t i = lane; i < n; i += 32) acc = fma((double)__ldg(col + i) - x0, r64_s[i], acc);
                 acc = warp_sum(acc);
                 if (lane == 0) P.xtxs[j] = (acc + (x0 - P.center[j]) * sum_xcs) / (P.scale[j] * sst);
             }
             sstar = (P.xty[jstar] >= 0.0) ? 1.0 : -1.0;
         }
+        __syncthreads();  // (r64_s is rewritten below)
 
         // ---- state at lambda_max: b = 0, r = yc, z = x~'yc / n
         for (int64_t j = tid; j < p; j += NT) P.z[j] = P.keep[j] ? (float)(P.xty[j] * (1.0 / (double)n)) : 0.f;
@@ -822,9 +826,9 @@ struct Cfg {
 // every shape leaves 128 registers per thread (threads x CTAs per SM = 512)
 constexpr Cfg CFGS[] = {
     {128, 8, 4, "128 threads, 4 CTAs per SM, 8 loads in flight per lane"},
-    {256, 4, 2, "256 threads, 2 CTAs per SM, 4 loads in flight per lane"},
     {256, 8, 2, "256 threads, 2 CTAs per SM, 8 loads in flight per lane"},
     {512, 8, 1, "512 threads, 1 CTA per SM, 8 loads in flight per lane"},
+    {512, 16, 1, "512 threads, 1 CTA per SM, 16 loads in flight per lane"},
 };
 constexpr int NCFG = (int)(sizeof(CFGS) / sizeof(CFGS[0]));
 
@@ -863,9 +867,9 @@ cudaError_t many_prepare(int c, int wcap)
     const size_t smem = many_smem(wcap);
     switch (c) {
     case 0: return prep_cfg<128, 8, 4>(smem);
-    case 1: return prep_cfg<256, 4, 2>(smem);
-    case 2: return prep_cfg<256, 8, 2>(smem);
-    case 3: return prep_cfg<512, 8, 1>(smem);
+    case 1: return prep_cfg<256, 8, 2>(smem);
+    case 2: return prep_cfg<512, 8, 1>(smem);
+    case 3: return prep_cfg<512, 16, 1>(smem);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -875,9 +879,9 @@ cudaError_t launch_many(int c, const ManyArgs &a, int num_sms, cudaStream_t st)
     const size_t smem = many_smem(a.wcap);
     switch (c) {
     case 0: return run_cfg<128, 8, 4>(a, num_sms, smem, st);
-    case 1: return run_cfg<256, 4, 2>(a, num_sms, smem, st);
-    case 2: return run_cfg<256, 8, 2>(a, num_sms, smem, st);
-    case 3: return run_cfg<512, 8, 1>(a, num_sms, smem, st);
+    case 1: return run_cfg<256, 8, 2>(a, num_sms, smem, st);
+    case 2: return run_cfg<512, 8, 1>(a, num_sms, smem, st);
+    case 3: return run_cfg<512, 16, 1>(a, num_sms, smem, st);
     default: return cudaErrorInvalidValue;
     }
 }
