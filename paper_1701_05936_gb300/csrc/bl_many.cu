@@ -300,24 +300,25 @@ __device__ __noinline__ void many_zpass(const ManyProblem &P, int64_t n, int64_t
     const float4 *r4 = reinterpret_cast<const float4 *>(r_s);
     const uint32_t cbytes = (uint32_t)(((uint64_t)n * 4 + 15) & ~(uint64_t)15);
     const int64_t zstep = (int64_t)NW * CPW;
-    if (li == 0 && wid * CPW + gi + zstep < nscan)
-        for (int k = 1; k < 3; ++k)
-            if (wid * CPW + gi + k * zstep < nscan) prefetch_l2(X + (int64_t)P.slist[wid * CPW + gi + k * zstep] * ldx, cbytes);
+    // The group's next column indices ride in registers, loaded from the scan
+    // list one to three iterations before their use, so that neither a
+    // column's loads nor the L2 prefetch of a later column waits for a list
+    // load: jc = this iteration's column, jn the next, jnn the one after.
+    const int64_t m_first = (int64_t)wid * CPW + gi;
+    auto at = [&](int64_t m) -> int32_t { return (m < nscan) ? P.slist[m] : -1; };
+    int32_t jc = at(m_first), jn = at(m_first + zstep), jnn = at(m_first + 2 * zstep);
+    if (li == 0 && jn >= 0) prefetch_l2(X + (int64_t)jn * ldx, cbytes);
+    float bacc = 0.f;  // this lane's column of the current epilogue batch
+    int32_t bj = -1;
+    int it = 0;
     for (int64_t m0 = (int64_t)wid * CPW; m0 < nscan; m0 += zstep) {
         const int64_t m = m0 + gi;
         const bool act = m < nscan;
-        const int64_t j = act ? (int64_t)P.slist[m] : 0;
-        // this group's column two iterations ahead into L2; the epilogue's
-        // operands now, so that their latency overlaps the column's loads
-        if (li == 0 && m + 3 * zstep < nscan) prefetch_l2(X + (int64_t)P.slist[m + 3 * zstep] * ldx, cbytes);
-        double isj = 0.0, cj = 0.0, xnj = 0.0;
-        bool kkt_j = false;
-        if (act) {
-            isj = P.inv_scale[j];
-            cj = P.center[j];
-            xnj = P.xnorm[j];
-            kkt_j = P.safe[j] && !P.working[j];
-        }
+        const int64_t j = act ? (int64_t)jc : 0;
+        // the column two iterations ahead into L2 (its index came in the last
+        // iteration) and the index for the next prefetch
+        if (li == 0 && jnn >= 0) prefetch_l2(X + (int64_t)jnn * ldx, cbytes);
+        const int32_t j3 = at(m + 3 * zstep);
         const float *col = X + j * ldx;
         const float4 *colv = reinterpret_cast<const float4 *>(col);
         float acc = 0.f;
@@ -345,21 +346,37 @@ __device__ __noinline__ void many_zpass(const ManyProblem &P, int64_t n, int64_t
                 for (int64_t i = nfull * 4; i < n; ++i) acc = fmaf(__ldg(col + i), r_s[i], acc);
         }
         for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (act && li == 0) {
-            cols += 1.0;
-            const double f = inv_nd * isj;
-            const double zj = ((double)acc - cj * sum_r) * f;
-            P.z[j] = (float)zj;
-            if (kkt_j) {
-                // |fl(x'r) - x'r| <= gam ||x_j|| ||r|| (Cauchy-Schwarz)
-                const double tau = gam * xnj * rnorm * f * (1.0 + 1e-6) +
-                                   4e-16 * (fabs(cj * sum_r) * f + fabs(zj));
-                if (fabs(zj) > thr_k - tau) {
-                    P.working[j] = 1;
-                    viol += 1.0;
+        if (act && li == 0) cols += 1.0;
+        // every lane of the group holds the sum: lane `slot` keeps it, and the
+        // group's lanes run the FP64 epilogue of G columns together (one FP64
+        // instruction stream per G columns instead of one per column)
+        const int slot = it % G;
+        if (li == slot) {
+            bacc = acc;
+            bj = act ? (int32_t)j : -1;
+        }
+        ++it;
+        if (slot == G - 1 || m0 + zstep >= nscan) {
+            if (bj >= 0) {
+                const double isj = P.inv_scale[bj], cj = P.center[bj];
+                const double f = inv_nd * isj;
+                const double zj = ((double)bacc - cj * sum_r) * f;
+                P.z[bj] = (float)zj;
+                if (P.safe[bj] && !P.working[bj]) {
+                    // |fl(x'r) - x'r| <= gam ||x_j|| ||r|| (Cauchy-Schwarz)
+                    const double tau = gam * P.xnorm[bj] * rnorm * f * (1.0 + 1e-6) +
+                                       4e-16 * (fabs(cj * sum_r) * f + fabs(zj));
+                    if (fabs(zj) > thr_k - tau) {
+                        P.working[bj] = 1;
+                        viol += 1.0;
+                    }
                 }
             }
+            bj = -1;
         }
+        jc = jn;
+        jn = jnn;
+        jnn = j3;
     }
 }
 
