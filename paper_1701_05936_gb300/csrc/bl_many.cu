@@ -78,6 +78,30 @@ __device__ __forceinline__ void prefetch_l2(const float *col, uint32_t bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(col), "r"(bytes) : "memory");
 }
 
+// Compensated dot product in FP32 (Dot2 of Ogita, Rump and Oishi, 2005): the
+// product's rounding error comes from one fused multiply-add (a*b = p + e
+// exactly), the sum's from Knuth's TwoSum (s + p = t + q exactly), and the
+// errors gather in c.  The result s + c, added in FP64, is as accurate as the
+// dot product carried out in twice the working precision; the rounding-mode
+// intrinsics keep the compiler from fusing the steps.  A second factor held as
+// hi + lo (an FP64 value split into two floats) adds x*lo to c directly.
+__device__ __forceinline__ void dot2_add(float &s, float &c, float x, float hi, float lo)
+{
+    const float p = __fmul_rn(x, hi);
+    const float e = fmaf(x, hi, -p);
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s = t;
+    c = fmaf(x, lo, __fadd_rn(c, __fadd_rn(q, e)));
+}
+
+__device__ __forceinline__ void split2(double v, float &hi, float &lo)
+{
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
 __device__ __forceinline__ void amax_merge2(double &v, long long &i, double v2, long long i2)
 {
     if (i2 >= 0 && (i < 0 || v2 > v || (v2 == v && i2 < i))) {
@@ -139,7 +163,7 @@ __device__ __noinline__ void many_cd(const float *__restrict__ X, int64_t ldx, i
     constexpr int CD_D = (16 / RPT < 2) ? 2 : 16 / RPT;
     constexpr int CD_PF = 12;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int32_t *idx_s = reinterpret_cast<const int32_t *>(smem + MANY_NMAX * 12);
+    const int32_t *idx_s = reinterpret_cast<const int32_t *>(smem + MANY_NMAX * 16);
     const float *c_s = reinterpret_cast<const float *>(idx_s + wcap);
     const float *is_s = c_s + wcap;
     const float *g_s = is_s + wcap;
@@ -390,8 +414,9 @@ __global__ void __launch_bounds__(NT, MINB) k_many_path(ManyArgs a)
     static_assert(RPT * NT == MANY_NMAX, "rows per thread");
     extern __shared__ __align__(16) unsigned char smem[];
     double *r64_s = reinterpret_cast<double *>(smem);             // FP64 residual
-    float *r_s = reinterpret_cast<float *>(r64_s + MANY_NMAX);    // its FP32 rounding (0 past n)
-    int32_t *idx_s = reinterpret_cast<int32_t *>(r_s + MANY_NMAX);
+    float *r_s = reinterpret_cast<float *>(r64_s + MANY_NMAX);    // its FP32 rounding (0 past n): the hi part
+    float *rlo_s = r_s + MANY_NMAX;                               // and the lo part, r64 - hi
+    int32_t *idx_s = reinterpret_cast<int32_t *>(rlo_s + MANY_NMAX);
     float *c_s = reinterpret_cast<float *>(idx_s + a.wcap);
     float *is_s = c_s + a.wcap;
     float *g_s = is_s + a.wcap;
@@ -447,7 +472,7 @@ __global__ void __launch_bounds__(NT, MINB) k_many_path(ManyArgs a)
         for (int64_t i = tid; i < n; i += NT) {
             const double v = P.y[i] - ybar;
             P.yc[i] = v;
-            r64_s[i] = v;  // (the standardization pass reads yc from shared memory)
+            split2(v, r_s[i], rlo_s[i]);  // (the standardization pass reads yc from shared memory)
             s1 += v;
             s2 += v * v;
         }
@@ -457,12 +482,14 @@ __global__ void __launch_bounds__(NT, MINB) k_many_path(ManyArgs a)
         // ---- standardization and x~'y: one warp per column.  With d = x - x_0j
         // (a constant column gives exactly 0), FP32 sums of d and d^2 over 8 rows
         // per lane are added in FP64; c = x_0 + sum d / n, s^2 = sum d^2 / n - (sum
-        // d / n)^2 (population sd); x~_j'yc = (sum (x - x_0) yc + (x_0 - c) sum yc) / s.
+        // d / n)^2 (population sd); x~_j'yc = (sum x yc - c sum yc) / s, the sum
+        // x yc by Dot2 against yc = hi + lo.
         for (int64_t j = wid; j < p; j += NW) {
             const float *col = X + j * ldx;
             const float x0 = __ldg(col);
             const double x0d = (double)x0;
-            double sd = 0.0, sdd = 0.0, sdy = 0.0;
+            double sd = 0.0, sdd = 0.0;
+            float ys = 0.f, yc2 = 0.f;
             bool varies = false;
             for (int64_t i0 = lane; i0 < n; i0 += 32 * 8) {
                 float ps = 0.f, pss = 0.f;
@@ -475,7 +502,7 @@ __global__ void __launch_bounds__(NT, MINB) k_many_path(ManyArgs a)
                         ps += d;
                         pss = fmaf(d, d, pss);
                         varies |= (d != 0.f);
-                        sdy = fma((double)e - x0d, r64_s[i], sdy);
+                        dot2_add(ys, yc2, e, r_s[i], rlo_s[i]);
                     }
                 }
                 sd += (double)ps;
@@ -483,7 +510,7 @@ __global__ void __launch_bounds__(NT, MINB) k_many_path(ManyArgs a)
             }
             sd = warp_sum(sd);
             sdd = warp_sum(sdd);
-            sdy = warp_sum(sdy);
+            const double sdy = warp_sum((double)ys + (double)yc2);
             varies = __any_sync(0xffffffffu, varies);
             if (lane == 0) {
                 const double md = sd / (double)n;
@@ -501,7 +528,7 @@ __global__ void __launch_bounds__(NT, MINB) k_many_path(ManyArgs a)
                 P.c32[j] = (float)cj;
                 P.is32[j] = (float)isj;
                 P.xnorm[j] = sqrt((double)n * (var + cj * cj));
-                P.xty[j] = kj ? (sdy + (x0d - cj) * sum_yc) / sj : 0.0;
+                P.xty[j] = kj ? (sdy - cj * sum_yc) / sj : 0.0;
                 P.beta[j] = 0.f;
             }
         }
@@ -536,17 +563,18 @@ __global__ void __launch_bounds__(NT, MINB) k_many_path(ManyArgs a)
         }
 
         MANY_PHASE(0)
-        // ---- BEDPP precomputation: xcs = x_* - c_*, x~_j'x~_* (Sec. 3.1.1 (1))
+        // ---- BEDPP precomputation: xcs = x_* - c_*, x~_j'x~_* = (sum x xcs - c
+        // sum xcs) / (s s_*) (Sec. 3.1.1 (1)), the sum by Dot2 against xcs = hi + lo
         const bool use_bedpp = a.screen == BL_SCREEN_SSR_BEDPP && jstar >= 0 && lmax > 0.0;
         double sstar = 1.0;
         if (use_bedpp) {
             const float *cs = X + jstar * ldx;
             const double cstar = P.center[jstar];
             double sx = 0.0;
-            __syncthreads();  // (every warp is done with yc in r64_s)
+            __syncthreads();  // (every warp is done with yc in r_s, rlo_s)
             for (int64_t i = tid; i < n; i += NT) {
                 const double v = (double)__ldg(cs + i) - cstar;
-                r64_s[i] = v;
+                split2(v, r_s[i], rlo_s[i]);
                 sx += v;
             }
             const double sum_xcs = bsum<NW>(sx, dbuf);
@@ -557,11 +585,10 @@ __global__ void __launch_bounds__(NT, MINB) k_many_path(ManyArgs a)
                     continue;
                 }
                 const float *col = X + j * ldx;
-                const double x0 = (double)__ldg(col);
-                double acc = 0.0;
-                for (int64_t i = lane; i < n; i += 32) acc = fma((double)__ldg(col + i) - x0, r64_s[i], acc);
-                acc = warp_sum(acc);
-                if (lane == 0) P.xtxs[j] = (acc + (x0 - P.center[j]) * sum_xcs) / (P.scale[j] * sst);
+                float ps = 0.f, pc = 0.f;
+                for (int64_t i = lane; i < n; i += 32) dot2_add(ps, pc, __ldg(col + i), r_s[i], rlo_s[i]);
+                const double acc = warp_sum((double)ps + (double)pc);  // sum x xcs (Dot2)
+                if (lane == 0) P.xtxs[j] = (acc - P.center[j] * sum_xcs) / (P.scale[j] * sst);
             }
             sstar = (P.xty[jstar] >= 0.0) ? 1.0 : -1.0;
         }
@@ -574,9 +601,11 @@ __global__ void __launch_bounds__(NT, MINB) k_many_path(ManyArgs a)
         for (int q = 0; q < RPT; ++q) {
             const int64_t i = tid + (int64_t)NT * q;
             const double v = (i < n) ? P.yc[i] : 0.0;
-            const float f = (float)v;
+            float f, fl;
+            split2(v, f, fl);
             r64_s[i] = v;
             r_s[i] = f;
+            rlo_s[i] = fl;
             q1 += (double)f;
             q2 += (double)f * (double)f;
             q3 += v * v;
@@ -584,6 +613,7 @@ __global__ void __launch_bounds__(NT, MINB) k_many_path(ManyArgs a)
         double sum_r = bsum<NW>(q1, dbuf);
         double rnorm = sqrt(bsum<NW>(q2, dbuf));
         double rss = bsum<NW>(q3, dbuf);
+        double sum_r64 = sum_yc;  // sum of the FP64 residual
         if (tid == 0) P.col_ptr[0] = 0;
         int64_t base = 0;
         MANY_PHASE(1)
@@ -689,15 +719,15 @@ __global__ void __launch_bounds__(NT, MINB) k_many_path(ManyArgs a)
                     b_s[t] = P.beta[j];
                 }
                 MANY_PHASE(3)
-                // ---- reference gradients g_t = sum_i (x_ij - c_j) r_i, FP64
+                // ---- reference gradients g_t = sum_i (x_ij - c_j) r_i = sum x r - c sum r,
+                // the sum x r by Dot2 against the FP64 residual r = hi + lo
                 for (int64_t t = wid; t < w; t += NW) {
                     const int32_t j = idx_s[t];
                     const float *col = X + (int64_t)j * ldx;
-                    const double cj = P.center[j];
-                    double acc = 0.0;
-                    for (int64_t i = lane; i < n; i += 32) acc = fma((double)__ldg(col + i) - cj, r64_s[i], acc);
-                    acc = warp_sum(acc);
-                    if (lane == 0) g_s[t] = (float)acc;
+                    float ps = 0.f, pc = 0.f;
+                    for (int64_t i = lane; i < n; i += 32) dot2_add(ps, pc, __ldg(col + i), r_s[i], rlo_s[i]);
+                    const double acc = warp_sum((double)ps + (double)pc);
+                    if (lane == 0) g_s[t] = (float)(acc - P.center[j] * sum_r64);
                 }
                 __syncthreads();
                 MANY_PHASE(4)
@@ -713,33 +743,46 @@ __global__ void __launch_bounds__(NT, MINB) k_many_path(ManyArgs a)
                 status |= cd_status;
                 for (int64_t t = tid; t < w; t += NT) P.beta[idx_s[t]] = b_s[t];
 
-                // ---- FP64 residual from b (rows of this thread), its FP32 rounding and sums
-                double u1 = 0.0, u2 = 0.0, u3 = 0.0;
+                // ---- the residual from b (rows of this thread): r = yc - sum_t a_t (x_t -
+                // c_t) = yc + K - sum_t a_t x_t with a_t = b_t / s_t (FP64, held as
+                // hi + lo in g_s / c_s, free after CD) and K = sum_t a_t c_t; the sum
+                // over t by Dot2, the rest in FP64; then its FP32 rounding and sums
+                double kp = 0.0;
+                for (int64_t t = tid; t < w; t += NT) {
+                    const int32_t j = idx_s[t];
+                    const double at = (double)b_s[t] * P.inv_scale[j];
+                    split2(at, g_s[t], c_s[t]);
+                    kp += at * P.center[j];
+                }
+                const double Kc = bsum<NW>(kp, dbuf);  // (its barriers publish g_s, c_s)
+                double u1 = 0.0, u2 = 0.0, u3 = 0.0, u4 = 0.0;
 #pragma unroll
                 for (int q = 0; q < RPT; ++q) {
                     const int64_t i = tid + (int64_t)NT * q;
-                    double acc = 0.0;
+                    float ss = 0.f, sc = 0.f;
                     if (i < n) {
                         for (int64_t t = 0; t < w; ++t) {
-                            const float b = b_s[t];
-                            if (b != 0.f) {
+                            if (b_s[t] != 0.f) {
                                 const int32_t j = idx_s[t];
-                                acc = fma((double)b * P.inv_scale[j], (double)__ldg(X + (int64_t)j * ldx + i) - P.center[j],
-                                          acc);
+                                dot2_add(ss, sc, __ldg(X + (int64_t)j * ldx + i), g_s[t], c_s[t]);
                             }
                         }
                     }
-                    const double v = (i < n) ? P.yc[i] - acc : 0.0;
-                    const float f = (float)v;
+                    const double v = (i < n) ? (P.yc[i] + Kc) - ((double)ss + (double)sc) : 0.0;
+                    float f, fl;
+                    split2(v, f, fl);
                     r64_s[i] = v;
                     r_s[i] = f;
+                    rlo_s[i] = fl;
                     u1 += (double)f;
                     u2 += (double)f * (double)f;
                     u3 += v * v;
+                    u4 += v;
                 }
                 sum_r = bsum<NW>(u1, dbuf);
                 rnorm = sqrt(bsum<NW>(u2, dbuf));
                 rss = bsum<NW>(u3, dbuf);
+                sum_r64 = bsum<NW>(u4, dbuf);
                 MANY_PHASE(6)
                 if (status & ST_TIMEOUT) break;
 
@@ -866,14 +909,14 @@ int many_num_configs() { return NCFG; }
 
 const char *many_config_name(int c) { return (c >= 0 && c < NCFG) ? CFGS[c].name : ""; }
 
-size_t many_smem(int wcap) { return (size_t)MANY_NMAX * (8 + 4) + (size_t)wcap * (4 * 5 + 2); }
+size_t many_smem(int wcap) { return (size_t)MANY_NMAX * (8 + 4 + 4) + (size_t)wcap * (4 * 5 + 2); }
 
 int many_wcap(int c)
 {
     if (c < 0 || c >= NCFG) return 0;
     // dynamic shared memory per CTA: 200 KB shared by the CTAs of an SM (each
     // also holds about 1 KB of static shared memory)
-    const size_t avail = (size_t)200 * 1024 / (size_t)CFGS[c].minb - (size_t)MANY_NMAX * 12;
+    const size_t avail = (size_t)200 * 1024 / (size_t)CFGS[c].minb - (size_t)MANY_NMAX * 16;
     size_t w = avail / 22;
     if (w > (size_t)MAX_WORKING) w = MAX_WORKING;
     return (int)(w & ~(size_t)15);
