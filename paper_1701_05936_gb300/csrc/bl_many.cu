@@ -883,9 +883,9 @@ struct Cfg {
     int nt, u, minb;
     const char *name;
 };
-// every shape leaves 128 registers per thread (threads x CTAs per SM = 512)
+// registers per thread: 128 for 512 threads per SM, 255 for the 256-thread single CTA
 constexpr Cfg CFGS[] = {
-    {128, 8, 4, "128 threads, 4 CTAs per SM, 8 loads in flight per lane"},
+    {256, 16, 1, "256 threads, 1 CTA per SM, 16 loads in flight per lane"},
     {256, 8, 2, "256 threads, 2 CTAs per SM, 8 loads in flight per lane"},
     {512, 8, 1, "512 threads, 1 CTA per SM, 8 loads in flight per lane"},
     {512, 16, 1, "512 threads, 1 CTA per SM, 16 loads in flight per lane"},
@@ -926,7 +926,7 @@ cudaError_t many_prepare(int c, int wcap)
 {
     const size_t smem = many_smem(wcap);
     switch (c) {
-    case 0: return prep_cfg<128, 8, 4>(smem);
+    case 0: return prep_cfg<256, 16, 1>(smem);
     case 1: return prep_cfg<256, 8, 2>(smem);
     case 2: return prep_cfg<512, 8, 1>(smem);
     case 3: return prep_cfg<512, 16, 1>(smem);
@@ -938,7 +938,7 @@ cudaError_t launch_many(int c, const ManyArgs &a, int num_sms, cudaStream_t st)
 {
     const size_t smem = many_smem(a.wcap);
     switch (c) {
-    case 0: return run_cfg<128, 8, 4>(a, num_sms, smem, st);
+    case 0: return run_cfg<256, 16, 1>(a, num_sms, smem, st);
     case 1: return run_cfg<256, 8, 2>(a, num_sms, smem, st);
     case 2: return run_cfg<512, 8, 1>(a, num_sms, smem, st);
     case 3: return run_cfg<512, 16, 1>(a, num_sms, smem, st);

@@ -39,6 +39,15 @@ def test_host_side_argument_checks_need_no_gpu():
     assert L.bl_ctx_destroy(None) == bl.BL_ERR_ARG
     assert L.bl_ctx_create(None, 0, None) == bl.BL_ERR_ARG
     assert L.bl_last_error(None) == b"null context"
+    # the persistent many-problem form: argument checks and its launch-shape table
+    assert L.bl_fit_many_persistent(None, None, 1, None, -1) == bl.BL_ERR_ARG
+    assert L.bl_many_autotune(None, None, 1, None, None, None) == bl.BL_ERR_ARG
+    assert L.bl_many_phase_ms(None, None, 0) == bl.BL_ERR_ARG
+    assert L.bl_many_problem_ms(None, None, 0) == bl.BL_ERR_ARG
+    shapes = bl.bl_many_configs()
+    assert len(shapes) == L.bl_many_num_configs() == 4
+    assert all(s and "threads" in s for s in shapes)
+    assert L.bl_many_config_name(-1) == b"" and L.bl_many_config_name(len(shapes)) == b""
 
 
 def test_struct_layouts_match_the_header(tmp_path):
