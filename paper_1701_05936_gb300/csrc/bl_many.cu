@@ -178,6 +178,8 @@ __device__ __noinline__ void many_cd(const float *__restrict__ X, int64_t ldx, i
     const bool cdw = wid < WC;
     const uint64_t t_start = globaltimer_ns();
     const uint32_t cbytes = (uint32_t)(((uint64_t)n * 4 + 15) & ~(uint64_t)15);
+    // short columns (under 2 KB) stay in L2 between sweeps: no prefetch on warp 0's path
+    const bool pf = n >= 512;
     float dr[RPT];
 #pragma unroll
     for (int q = 0; q < RPT; ++q) dr[q] = 0.f;
@@ -195,7 +197,7 @@ __device__ __noinline__ void many_cd(const float *__restrict__ X, int64_t ldx, i
     };
     auto sweep_w = [&](bool full, int len, bool &moved, bool &newnz) {
         float buf[CD_D][RPT];
-        if (tid == 0)
+        if (pf && tid == 0)
             for (int t = CD_D; t < len && t < CD_PF; ++t) prefetch_l2(X + (int64_t)idx_s[full ? t : act_s[t]] * ldx, cbytes);
 #pragma unroll
         for (int s = 0; s < CD_D; ++s)
@@ -238,7 +240,7 @@ __device__ __noinline__ void many_cd(const float *__restrict__ X, int64_t ldx, i
                     newnz |= (old == 0.f && fabsf(nb) >= tol);
                     ++upd;
                     if (t + CD_D < len) load_col(buf[s], idx_s[full ? t + CD_D : act_s[t + CD_D]]);
-                    if (tid == 0 && t + CD_PF < len)
+                    if (pf && tid == 0 && t + CD_PF < len)
                         prefetch_l2(X + (int64_t)idx_s[full ? t + CD_PF : act_s[t + CD_PF]] * ldx, cbytes);
                 }
             }
