@@ -1479,7 +1479,7 @@ extern "C" int bl_fit_path_batched(bl_ctx *ctx, const void *X, int dtype, int64_
     BatchBufs bb;
     double *cen, *sca, *nfit_d, *ybar, *yc, *r64, *lam_b, *ssr, *rnorm, *xty, *ycs;
     uint8_t *keepF, *inW;
-    float *c32, *is32, *xn32, *r32, *beta, *Z, *gref, *sumr, *cfit, *insfit;
+    float *c32, *is32, *xn32, *r32, *r32lo, *beta, *Z, *gref, *sumr, *cfit, *insfit;
     int32_t *idx, *fit_of;
     int64_t *w, *nnz_total;
     int *status, *active;
@@ -1498,6 +1498,7 @@ extern "C" int bl_fit_path_batched(bl_ctx *ctx, const void *X, int dtype, int64_
     CK(bb.get(&yc, (size_t)B * n));
     CK(bb.get(&r64, (size_t)B * n));
     CK(bb.get(&r32, (size_t)B * ldr));
+    CK(bb.get(&r32lo, (size_t)B * ldr));
     CK(bb.get(&beta, (size_t)B * p));
     CK(bb.get(&Z, (size_t)B * p));
     CK(bb.get(&inW, (size_t)B * p));
@@ -1541,7 +1542,7 @@ extern "C" int bl_fit_path_batched(bl_ctx *ctx, const void *X, int dtype, int64_
     int slot = tbegin(ctx, 0);
     LAUNCH(1, launch_bfit_stats(Xf, n, p, ldx, fold_id, (int)nfolds, nfit_d, cen, sca, keepF, c32, is32, xn32,
                                 ctx->num_sms, s));
-    LAUNCH(1, launch_bcenter_y(Y, ldy, B, F, n, fold_id, nfit_d, ybar, yc, r64, r32, ldr, s));
+    LAUNCH(1, launch_bcenter_y(Y, ldy, B, F, n, fold_id, nfit_d, ybar, yc, r64, r32, r32lo, ldr, s));
     tend(ctx, slot, (double)n * p * 4.0);
     std::vector<double> grid((size_t)m * K);
     std::vector<double> lmax((size_t)m);
@@ -1611,7 +1612,7 @@ extern "C" int bl_fit_path_batched(bl_ctx *ctx, const void *X, int dtype, int64_
             const int64_t lds = std::min<int64_t>(cap, std::max<int64_t>(32, (wmax + 31) / 32 * 32));
             ++rounds;
             slot = tbegin(ctx, 9);
-            LAUNCH(1, launch_bgref(Xf, n, ldx, p, B, F, cen, idx, w, cap, r64, active, gref, ctx->num_sms, s));
+            LAUNCH(1, launch_bgref(Xf, n, ldx, p, B, F, cen, idx, w, cap, r32, r32lo, ldr, active, gref, ctx->num_sms, s));
             tend(ctx, slot, 0.0);
             slot = tbegin(ctx, 5);
             LAUNCH(1, launch_bcd(Xf, n, ldx, p, B, F, fold_id, nfit_d, c32, is32, idx, w, cap, lds, gref, lam_b, alpha, beta,
@@ -1619,8 +1620,8 @@ extern "C" int bl_fit_path_batched(bl_ctx *ctx, const void *X, int dtype, int64_
                                  s));
             tend(ctx, slot, 0.0);
             slot = tbegin(ctx, 6);
-            LAUNCH(1, launch_bresid(Xf, n, ldx, p, B, F, fold_id, cen, sca, idx, w, cap, beta, yc, active, r64, r32, ldr,
-                                    s));
+            LAUNCH(1, launch_bresid(Xf, n, ldx, p, B, F, fold_id, cen, sca, idx, w, cap, beta, yc, active, r64, r32, r32lo,
+                                    ldr, s));
             tend(ctx, slot, 0.0);
             if ((st = zpass())) return st;
             CK(cudaMemsetAsync(nviol, 0, (size_t)B * 8, s));

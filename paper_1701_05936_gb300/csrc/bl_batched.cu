@@ -108,10 +108,12 @@ __global__ void __launch_bounds__(256)
 }
 
 // y of problem b centred on its fit (0 elsewhere): yc, the FP64 residual r64 and
-// its FP32 copy r32 (padding rows of r32 zeroed).
+// its FP32 split r32 + r32lo (r32 = r64 rounded, r32lo = r64 - r32 rounded;
+// padding rows zeroed).
 __global__ void __launch_bounds__(256)
     k_bcenter_y(const double *__restrict__ Y, int64_t ldy, int F, int64_t n, const int8_t *__restrict__ fold,
-                const double *__restrict__ nfit, double *ybar, double *yc, double *r64, float *r32, int64_t ldr)
+                const double *__restrict__ nfit, double *ybar, double *yc, double *r64, float *r32, float *r32lo,
+                int64_t ldr)
 {
     const int b = blockIdx.x, r = b / F, f = b % F;
     const double *y = Y + (int64_t)r * ldy;
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(256)
             yc[(int64_t)b * n + i] = v;
             r64[(int64_t)b * n + i] = v;
         }
-        r32[(int64_t)b * ldr + i] = (float)v;
+        split2(v, r32[(int64_t)b * ldr + i], r32lo[(int64_t)b * ldr + i]);
     }
 }
 
@@ -192,27 +194,33 @@ __global__ void __launch_bounds__(1024)
         }
 }
 
-// ------------------------------------------------ FP64 reference gradients
-// g_bt = sum_i (x_ij - c_fj) r64_bi, j = idx_b[t] (r64 is 0 off the fit).
+// ------------------------------------------------ reference gradients
+// g_bt = sum_i (x_ij - c_fj) r64_bi = sum_i x_ij r64_bi - c_fj sum_i r64_bi, j =
+// idx_b[t] (r64 is 0 off the fit): both sums by Dot2 against the residual's split
+// r32 + r32lo, combined in FP64.
 __global__ void __launch_bounds__(256)
     k_bgref(const float *__restrict__ X, int64_t n, int64_t ldx, int64_t p, int F, const double *__restrict__ cen,
             const int32_t *__restrict__ idx, const int64_t *__restrict__ w, int64_t cap,
-            const double *__restrict__ r64, const int *__restrict__ active, float *gref)
+            const float *__restrict__ r32, const float *__restrict__ r32lo, int64_t ldr, const int *__restrict__ active,
+            float *gref)
 {
     const int b = blockIdx.y, f = b % F;
     if (!active[b]) return;
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const double *r = r64 + (int64_t)b * n;
+    const float *rh = r32 + (int64_t)b * ldr, *rl = r32lo + (int64_t)b * ldr;
     for (int64_t t = gw; t < w[b]; t += nw) {
         const int32_t j = idx[(int64_t)b * cap + t];
         const float *col = X + (int64_t)j * ldx;
-        const double cj = cen[(int64_t)f * p + j];
-        double acc = 0.0;
-        for (int64_t i = lane; i < n; i += 32) acc = fma((double)col[i] - cj, r[i], acc);
-        acc = warp_sum(acc);
-        if (lane == 0) gref[(int64_t)b * cap + t] = (float)acc;
+        float xs = 0.f, xc = 0.f, rs = 0.f, rc = 0.f;
+        for (int64_t i = lane; i < n; i += 32) {
+            const float hi = rh[i], lo = rl[i];
+            dot2_add(xs, xc, col[i], hi, lo);
+            dot2_add(rs, rc, 1.f, hi, lo);
+        }
+        const double sxr = warp_sum((double)xs + (double)xc), sr = warp_sum((double)rs + (double)rc);
+        if (lane == 0) gref[(int64_t)b * cap + t] = (float)(sxr - cen[(int64_t)f * p + j] * sr);
     }
 }
 
@@ -442,19 +450,22 @@ __global__ void __launch_bounds__(256, (RPT <= 2) ? 2 : 1)
     }
 }
 
-// ------------------------------------------------------------ FP64 residual
-// r64_bi = yc_bi - sum_t (x_ij - c_fj) b_bj / s_fj on the fit's rows (0 elsewhere),
-// j = idx_b[t] with b_bj != 0; r32 = r64 rounded.
+// ------------------------------------------------------------ the residual
+// r64_bi = yc_bi - sum_t (x_ij - c_fj) a_bt = yc_bi + sum_t a_bt c_fj - sum_t a_bt x_ij
+// on the fit's rows (0 elsewhere), a_bt = b_bj / s_fj over j = idx_b[t] with
+// b_bj != 0: per chunk of terms, K = sum a c in FP64 (a block sum) and the sum
+// a x by Dot2 against a = hi + lo; then r32 + r32lo = r64 split.
 __global__ void __launch_bounds__(256)
     k_bresid(const float *__restrict__ X, int64_t n, int64_t ldx, int64_t p, int F, const int8_t *__restrict__ fold,
              const double *__restrict__ cen, const double *__restrict__ sca, const int32_t *__restrict__ idx,
              const int64_t *__restrict__ w, int64_t cap, const float *__restrict__ beta, const double *__restrict__ yc,
-             const int *__restrict__ active, double *r64, float *r32, int64_t ldr)
+             const int *__restrict__ active, double *r64, float *r32, float *r32lo, int64_t ldr)
 {
-    // the working set's nonzero terms, 256 at a time: column, c_fj and b_j / s_fj,
-    // each formed once per block (FP64 division is slow on this part)
+    // the working set's nonzero terms, 256 at a time: column and a = b_j / s_fj
+    // split in two floats, each formed once per block (FP64 division is slow here)
     __shared__ int32_t j_s[256];
-    __shared__ double c_s[256], k_s[256];
+    __shared__ float kh_s[256], kl_s[256];
+    __shared__ double kred[8];
     const int b = blockIdx.y, f = b % F;
     if (!active[b]) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -482,20 +493,33 @@ __global__ void __launch_bounds__(256)
             if (q < wid) base += wcnt[q];
             total += wcnt[q];
         }
+        double kc = 0.0;
         if (nz) {
             const unsigned int pos = base + __popc(bal & ((1u << lane) - 1u));
             const int64_t o = (int64_t)f * p + j;
+            const double a = (double)bj / sca[o];
             j_s[pos] = j;
-            c_s[pos] = cen[o];
-            k_s[pos] = (double)bj / sca[o];
+            split2(a, kh_s[pos], kl_s[pos]);
+            kc = a * cen[o];
         }
+        kc = warp_sum(kc);
+        if (lane == 0) kred[wid] = kc;
         __syncthreads();
-        if (live)
-            for (unsigned int e = 0; e < total; ++e)
-                acc = fma(-((double)X[(int64_t)j_s[e] * ldx + i] - c_s[e]), k_s[e], acc);
+        double K = 0.0;
+        for (unsigned int q = 0; q < 8; ++q) K += kred[q];
+        if (live) {
+            float ss = 0.f, sc = 0.f;
+            for (unsigned int e = 0; e < total; ++e) dot2_add(ss, sc, X[(int64_t)j_s[e] * ldx + i], kh_s[e], kl_s[e]);
+            acc += K - ((double)ss + (double)sc);
+        }
     }
     if (i < n) r64[(int64_t)b * n + i] = live ? acc : 0.0;
-    if (i < ldr) r32[(int64_t)b * ldr + i] = live ? (float)acc : 0.f;
+    if (i < ldr) {
+        float hi = 0.f, lo = 0.f;
+        if (live) split2(acc, hi, lo);
+        r32[(int64_t)b * ldr + i] = hi;
+        r32lo[(int64_t)b * ldr + i] = lo;
+    }
 }
 
 // ------------------------------------------------------------------ KKT
@@ -504,7 +528,11 @@ __global__ void __launch_bounds__(256)
 // FP32 accumulation of n terms in any order, FP32 epilogue):
 //   [1.001 (2^-9 + n 2^-24) xn_j rn_b + 4 2^-24 (xn_j rn_b + |c_fj| |sum r_b|)] / (n_f s_fj)
 //   + 2^-23 |z_bj|.
-// A violator joins the working set; nviol_b counts them.
+// The test runs in FP32: the bound and |z| + bound are formed with at most 14
+// roundings of relative size 2^-24 (all terms positive), and the threshold with
+// one, so the test is taken as |z| + bound (1 + 4e-6) > lam alpha (1 - 4e-6),
+// which flags every violator of the exact test (and at most a few more within
+// that margin).  A violator joins the working set; nviol_b counts them.
 __global__ void k_bkkt(int64_t p, int64_t n, int F, const uint8_t *__restrict__ keep, const float *__restrict__ c32,
                        const float *__restrict__ is32, const float *__restrict__ xn32, const double *__restrict__ nfit,
                        const float *__restrict__ Z, int64_t ldz, const double *__restrict__ rnorm,
@@ -512,19 +540,21 @@ __global__ void k_bkkt(int64_t p, int64_t n, int F, const uint8_t *__restrict__ 
                        unsigned long long *nviol)
 {
     const int b = blockIdx.y, f = b % F;
-    const double thr = lam_b[b] * alpha;
     const double u = 5.9604644775390625e-08;  // 2^-24
-    const double g = 1.001 * (0.001953125 + (double)n * u);
-    const double rn = rnorm[b], sr = fabs((double)sumr[b]), inf = 1.0 / nfit[f];
+    // per-problem factors in FP64, rounded up by their slack once
+    const float thr = (float)(lam_b[b] * alpha * (1.0 - 4e-6));
+    const float g = (float)(1.001 * (0.001953125 + (double)n * u) * (1.0 + 1e-6));
+    const float rn = (float)(rnorm[b] * (1.0 + 1e-6)), sr = (float)(fabs((double)sumr[b]) * (1.0 + 1e-6));
+    const float inf = (float)(1.0000002 * 1.0000002 * (1.0 + 1e-6) / nfit[f]);
+    const float u4 = (float)(4.0 * u), u2 = (float)(2.0 * u), slack = 1.000004f;
     unsigned long long cnt = 0;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p; j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = (int64_t)f * p + j;
         if (!keep[o] || inW[(int64_t)b * p + j]) continue;
-        const double z = fabs((double)Z[(int64_t)b * ldz + j]);
-        const double xr = (double)xn32[j] * 1.0000002 * rn;
-        const double bound = (g * xr + 4.0 * u * (xr + fabs((double)c32[o]) * sr)) * (double)is32[o] * 1.0000002 * inf +
-                             2.0 * u * z;
-        if (z > thr - bound) {
+        const float z = fabsf(Z[(int64_t)b * ldz + j]);
+        const float xr = xn32[j] * rn;
+        const float bound = (g * xr + u4 * (xr + fabsf(c32[o]) * sr)) * is32[o] * inf + u2 * z;
+        if (fmaf(bound, slack, z) > thr) {
             inW[(int64_t)b * p + j] = 1;
             ++cnt;
         }
@@ -638,10 +668,10 @@ cudaError_t launch_bfit_stats(const float *X, int64_t n, int64_t p, int64_t ldx,
 }
 
 cudaError_t launch_bcenter_y(const double *Y, int64_t ldy, int B, int F, int64_t n, const int8_t *fold,
-                             const double *nfit, double *ybar, double *yc, double *r64, float *r32, int64_t ldr,
-                             cudaStream_t st)
+                             const double *nfit, double *ybar, double *yc, double *r64, float *r32, float *r32lo,
+                             int64_t ldr, cudaStream_t st)
 {
-    k_bcenter_y<<<B, 256, 0, st>>>(Y, ldy, F, n, fold, nfit, ybar, yc, r64, r32, ldr);
+    k_bcenter_y<<<B, 256, 0, st>>>(Y, ldy, F, n, fold, nfit, ybar, yc, r64, r32, r32lo, ldr);
     return cudaGetLastError();
 }
 
@@ -661,12 +691,12 @@ cudaError_t launch_bcompact(int64_t p, int B, const uint8_t *inW, int32_t *idx, 
 }
 
 cudaError_t launch_bgref(const float *X, int64_t n, int64_t ldx, int64_t p, int B, int F, const double *cen,
-                         const int32_t *idx, const int64_t *w, int64_t cap, const double *r64, const int *active,
-                         float *gref, int num_sms, cudaStream_t st)
+                         const int32_t *idx, const int64_t *w, int64_t cap, const float *r32, const float *r32lo,
+                         int64_t ldr, const int *active, float *gref, int num_sms, cudaStream_t st)
 {
     dim3 g((unsigned)std::max<int64_t>(1, std::min<int64_t>((cap + 7) / 8, ((int64_t)num_sms * 8 + B - 1) / B)),
            (unsigned)B);
-    k_bgref<<<g, 256, 0, st>>>(X, n, ldx, p, F, cen, idx, w, cap, r64, active, gref);
+    k_bgref<<<g, 256, 0, st>>>(X, n, ldx, p, F, cen, idx, w, cap, r32, r32lo, ldr, active, gref);
     return cudaGetLastError();
 }
 
@@ -700,10 +730,10 @@ cudaError_t launch_bcd(const float *X, int64_t n, int64_t ldx, int64_t p, int B,
 cudaError_t launch_bresid(const float *X, int64_t n, int64_t ldx, int64_t p, int B, int F, const int8_t *fold,
                           const double *cen, const double *sca, const int32_t *idx, const int64_t *w, int64_t cap,
                           const float *beta, const double *yc, const int *active, double *r64, float *r32,
-                          int64_t ldr, cudaStream_t st)
+                          float *r32lo, int64_t ldr, cudaStream_t st)
 {
     dim3 g((unsigned)((std::max<int64_t>(n, ldr) + 255) / 256), (unsigned)B);
-    k_bresid<<<g, 256, 0, st>>>(X, n, ldx, p, F, fold, cen, sca, idx, w, cap, beta, yc, active, r64, r32, ldr);
+    k_bresid<<<g, 256, 0, st>>>(X, n, ldx, p, F, fold, cen, sca, idx, w, cap, beta, yc, active, r64, r32, r32lo, ldr);
     return cudaGetLastError();
 }
 

@@ -204,4 +204,28 @@ template <typename A> __device__ __forceinline__ A soft_threshold(A z, A t)
     return z - fmin(fmax(z, -t), t);
 }
 
+// Compensated dot product in FP32 (Dot2 of Ogita, Rump and Oishi, 2005): the
+// product's rounding error comes from one fused multiply-add (a*b = p + e
+// exactly), the sum's from Knuth's TwoSum (s + p = t + q exactly), and the
+// errors gather in c.  The result s + c, added in FP64, is as accurate as the
+// dot product carried out in twice the working precision; the rounding-mode
+// intrinsics keep the compiler from fusing the steps.  A second factor held as
+// hi + lo (an FP64 value split into two floats) adds x*lo to c directly.
+__device__ __forceinline__ void dot2_add(float &s, float &c, float x, float hi, float lo)
+{
+    const float p = __fmul_rn(x, hi);
+    const float e = fmaf(x, hi, -p);
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s = t;
+    c = fmaf(x, lo, __fadd_rn(c, __fadd_rn(q, e)));
+}
+
+__device__ __forceinline__ void split2(double v, float &hi, float &lo)
+{
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
 }  // namespace bl

@@ -203,15 +203,15 @@ cudaError_t launch_bfit_stats(const float *X, int64_t n, int64_t p, int64_t ldx,
                               const double *nfit, double *cen, double *sca, uint8_t *keep, float *c32, float *is32,
                               float *xn32, int num_sms, cudaStream_t st);
 cudaError_t launch_bcenter_y(const double *Y, int64_t ldy, int B, int F, int64_t n, const int8_t *fold,
-                             const double *nfit, double *ybar, double *yc, double *r64, float *r32, int64_t ldr,
-                             cudaStream_t st);
+                             const double *nfit, double *ybar, double *yc, double *r64, float *r32, float *r32lo,
+                             int64_t ldr, cudaStream_t st);
 cudaError_t launch_bstrong(int64_t p, int B, int F, const uint8_t *keep, const float *beta, const float *Z, int64_t ldz,
                            const double *ssr, uint8_t *inW, cudaStream_t st);
 cudaError_t launch_bcompact(int64_t p, int B, const uint8_t *inW, int32_t *idx, int64_t cap, int64_t *w, int *status,
                             const int *active, cudaStream_t st);
 cudaError_t launch_bgref(const float *X, int64_t n, int64_t ldx, int64_t p, int B, int F, const double *cen,
-                         const int32_t *idx, const int64_t *w, int64_t cap, const double *r64, const int *active,
-                         float *gref, int num_sms, cudaStream_t st);
+                         const int32_t *idx, const int64_t *w, int64_t cap, const float *r32, const float *r32lo,
+                         int64_t ldr, const int *active, float *gref, int num_sms, cudaStream_t st);
 size_t bcd_smem(int64_t lds);
 cudaError_t launch_bcd(const float *X, int64_t n, int64_t ldx, int64_t p, int B, int F, const int8_t *fold,
                        const double *nfit, const float *c32, const float *is32, const int32_t *idx, const int64_t *w,
@@ -221,7 +221,7 @@ cudaError_t launch_bcd(const float *X, int64_t n, int64_t ldx, int64_t p, int B,
 cudaError_t launch_bresid(const float *X, int64_t n, int64_t ldx, int64_t p, int B, int F, const int8_t *fold,
                           const double *cen, const double *sca, const int32_t *idx, const int64_t *w, int64_t cap,
                           const float *beta, const double *yc, const int *active, double *r64, float *r32,
-                          int64_t ldr, cudaStream_t st);
+                          float *r32lo, int64_t ldr, cudaStream_t st);
 cudaError_t launch_bkkt(int64_t p, int64_t n, int B, int F, const uint8_t *keep, const float *c32, const float *is32,
                         const float *xn32, const double *nfit, const float *Z, int64_t ldz, const double *rnorm,
                         const float *sumr, const double *lam_b, double alpha, uint8_t *inW, unsigned long long *nviol,

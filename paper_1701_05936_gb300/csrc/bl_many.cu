@@ -78,30 +78,6 @@ __device__ __forceinline__ void prefetch_l2(const float *col, uint32_t bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(col), "r"(bytes) : "memory");
 }
 
-// Compensated dot product in FP32 (Dot2 of Ogita, Rump and Oishi, 2005): the
-// product's rounding error comes from one fused multiply-add (a*b = p + e
-// exactly), the sum's from Knuth's TwoSum (s + p = t + q exactly), and the
-// errors gather in c.  The result s + c, added in FP64, is as accurate as the
-// dot product carried out in twice the working precision; the rounding-mode
-// intrinsics keep the compiler from fusing the steps.  A second factor held as
-// hi + lo (an FP64 value split into two floats) adds x*lo to c directly.
-__device__ __forceinline__ void dot2_add(float &s, float &c, float x, float hi, float lo)
-{
-    const float p = __fmul_rn(x, hi);
-    const float e = fmaf(x, hi, -p);
-    const float t = __fadd_rn(s, p);
-    const float z = __fsub_rn(t, s);
-    const float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
-    s = t;
-    c = fmaf(x, lo, __fadd_rn(c, __fadd_rn(q, e)));
-}
-
-__device__ __forceinline__ void split2(double v, float &hi, float &lo)
-{
-    hi = (float)v;
-    lo = (float)(v - (double)hi);
-}
-
 __device__ __forceinline__ void amax_merge2(double &v, long long &i, double v2, long long i2)
 {
     if (i2 >= 0 && (i < 0 || v2 > v || (v2 == v && i2 < i))) {
