@@ -519,7 +519,7 @@ def many(local: int, nprob: int = 256, concurrency: int = 16):
     return {"workload": f"{nprob} problems, n ~ U{{100..2000}}, p ~ U{{1000..50000}}, iid N(0,1) FP32, 10 nonzero "
                         f"+-1, SNR 3, 100 lambdas to 0.05 lambda_max, alpha 1",
             "form": "one persistent launch (a one-node CUDA graph): each CTA runs a whole path, problems from a "
-                    "device queue, largest first",
+                    "device queue, costliest (p (n + 1024)) first",
             "value": nprob / (ms / 1e3), "unit": "problems/s", "ms": ms, "problems_ok": ok,
             "cta_ms_by_phase": phases, "cd_updates": updates,
             "problem_cta_ms": {"max": float(pms_each.max()), "median": float(np.median(pms_each)),

@@ -10,9 +10,10 @@
 // so the z pass of all B problems is one product X'R (bl_xtr.cu).
 //
 // Per lambda (all problems together): strong rule -> ordered working sets ->
-// FP64 reference gradients -> coordinate descent (one CTA per problem) -> FP64
-// residual -> batched z pass -> KKT check with the TF32 bound; the problems
-// with violators repeat from the gradients; then the path record.
+// reference gradients -> coordinate descent (one CTA per problem) -> residual
+// (kept in FP64; both sums over rows by Dot2 compensated FP32 products) ->
+// batched z pass -> KKT check with the TF32 bound; the problems with violators
+// repeat from the gradients; then the path record.
 #include "biglasso_gpu.h"
 #include "bl_device.cuh"
 #include "bl_internal.h"

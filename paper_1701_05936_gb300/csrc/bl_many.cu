@@ -1,15 +1,18 @@
 // bl_many.cu -- many independent lasso / elastic-net paths in one persistent
-// launch.  Every CTA takes a problem from a device queue (largest first, the
-// order the host gives) and runs that problem's whole path by itself: y
+// launch.  Every CTA takes a problem from a device queue (costliest first, in
+// the order the host gives) and runs that problem's whole path by itself: y
 // centring, standardization with x~'y, lambda_max and the grid, the BEDPP
 // precomputation, and at each lambda the screen, the KKT loop of coordinate
-// descent + FP64 residual + z pass, and the record step.  The steps and their
-// arithmetic are those of bl_fit_path (Sec. 1, Sec. 2.2, Sec. 3.1.1) at the
-// scale of one CTA:
-// * the FP64 residual (n <= MANY_NMAX rows) and its FP32 rounding stay in
+// descent + residual + z pass, and the record step.  The steps are those of
+// bl_fit_path (Sec. 1, Sec. 2.2, Sec. 3.1.1) at the scale of one CTA:
+// * the FP64 residual (n <= MANY_NMAX rows) and its FP32 split hi + lo stay in
 //   shared memory for the whole path;
+// * the sums over rows that bl_fit_path forms with FP64 products (x~'y, x~'x_*,
+//   the reference gradients, the residual) use Dot2 compensated FP32 products
+//   added in FP64 (bl_device.cuh): as accurate to well within the margins that
+//   read them, with far fewer FP64 instructions, which are slow on this part;
 // * coordinate descent is the residual form of bl_cd.cu (the change dr of this
-//   round in registers, the FP64 reference gradients g_ref computed first, one
+//   round in registers, the reference gradients g_ref computed first, one
 //   barrier per coordinate among the warps the rows need, active-set cycling,
 //   the same convergence rule);
 // * the z pass streams each scanned column with 16-byte loads (U per lane in
