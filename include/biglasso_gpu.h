@@ -551,7 +551,7 @@ int bl_fit_many(bl_ctx *ctx, bl_problem *probs, int nprob, const bl_options *opt
  * solved afterwards by bl_fit_many's worker form, so every problem gets its
  * path.  config: a launch shape index (0 .. bl_many_num_configs() - 1), or -1
  * for the one bl_many_autotune chose on this ctx (a default before that).
- * Device scratch (about 68 bytes per feature and 16 per row of every problem)
+ * Device scratch (about 71 bytes per feature and 8 per row of every problem)
  * is held by the ctx and only grows.  Returns BL_OK when every problem
  * succeeded, else the status of the first failing problem in index order
  * (each problem's status is in bl_problem.status).  BL_ERR_ARG before any
